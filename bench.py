@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput benchmark of batched TAPT (arXiv 2509.23043, Algorithm 1) on GB300.
+
+Workload (the batched-TAPT configuration): 256 periodic 3D Edwards-Anderson +-J instances,
+L = 10 (1000 spins), J = +-1 with p = 0.5 from the seed, no field; 32 temperature slots,
+beta geometric 0.1 -> 3.0; Metropolis checkerboard sweeps, one exchange event per sweep
+(M = 1); global proposals every 10 sweeps (from sweep 100) on the 30 hottest slots, drawn
+from device pools of 1024 configurations per slot per instance that PT runs of this library
+produce before timing (untimed); spins bit-packed 32 walkers per uint32; FP64 acceptance of
+exchanges and proposals.
+
+One step = 100 cycles of Algorithm 1 over the whole batch (100 sweeps, 100 energy
+evaluations, 10 proposal events, 100 exchange events) = 8.192e8 spin-flip attempts.
+Metric: spin-flip attempts per ns (one attempt = one free-spin update decision).
+
+  python bench.py [--gpus N --steps K --warmup W]        # our CUDA path
+  python bench.py --impl reference                        # the CPU oracle (reference arm)
+Under torchrun (N > 1) the instances are sharded across ranks (weak scaling: each rank runs
+its own 256 instances); there is no collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "spin-flip attempts/ns; p50/p99 time-to-target of batched served TAPT vs plain PT"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+INT_LANES_PER_SM = 128   # 4 SM sub-partitions x 32 lanes issue one integer op per clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--instances", type=int, default=256)
+    p.add_argument("--L", type=int, default=10)
+    p.add_argument("--R", type=int, default=32)
+    p.add_argument("--sweeps-per-step", type=int, default=100)
+    p.add_argument("--pool-size", type=int, default=1024)
+    p.add_argument("--pool-burnin", type=int, default=2000)
+    p.add_argument("--pool-gap", type=int, default=2)
+    p.add_argument("--threads", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-instances", type=int, default=16)
+    p.add_argument("--cpu-sample-sweeps", type=int, default=60)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------ workload
+def workload(args, first: int, count: int):
+    import instances as I
+    insts = [I.ea_instance(args.L, seed=I.MASTER_SEED, index=first + k) for k in range(count)]
+    betas = [I.geometric_betas(0.1, 3.0, args.R) for _ in range(count)]
+    prop = [[1] * (args.R - 2) + [0, 0] for _ in range(count)]
+    ids = [first + k for k in range(count)]
+    return insts, betas, prop, ids
+
+
+def make_config(args, pool_size):
+    import paper_2509_23043_gb300 as pt
+    return pt.Config(update=pt.METROPOLIS, sweeps_per_cycle=1, propose_every=10,
+                     propose_start=100, pool_size=pool_size, seed=0x7A972509,
+                     threads_per_block=args.threads)
+
+
+def build_pools(args, insts, betas, prop, ids, ctx):
+    """Pools from PT runs of the method itself: a separate batch (other random streams)
+    burns in, then its slot configurations are captured every `gap` sweeps."""
+    import paper_2509_23043_gb300 as pt
+    cfg = pt.Config(seed=0x9001, sweeps_per_cycle=1, threads_per_block=args.threads)
+    gen = pt.create_instances(insts, betas, cfg, instance_ids=[1_000_000 + i for i in ids])
+    pt.run_cycles(gen, args.pool_burnin)
+    for e in range(args.pool_size):
+        pt.run_cycles(gen, args.pool_gap)
+        pt.capture_proposals(ctx, gen, e)
+    pt.destroy(gen)
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([t.strip() for t in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for k, nm in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ roofline model
+def expected_plane_blocks(ctx, args, sample=4):
+    """Algorithmic random-number work of the bit-plane compare: a word of 32 walkers needs
+    plane blocks (4 planes = one Philox call) until each walker with dE > 0 is decided, each
+    plane deciding a walker with probability 1/2. Averaged over the words of a state sample."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    blocks = []
+    for k in range(min(sample, ctx.n)):
+        s, _ = pt.read_state(ctx, k)              # [R][N] slot order
+        inst = I.ea_instance(args.L, index=k)
+        J = np.zeros((args.L ** 3, 6), np.int64)
+        nb = np.zeros((args.L ** 3, 6), np.int64)
+        for e, (a, b, j) in enumerate(zip(inst.edge_i, inst.edge_j, inst.edge_J)):
+            d = e % 3
+            J[a, 2 * d], nb[a, 2 * d] = j, b
+            J[b, 2 * d + 1], nb[b, 2 * d + 1] = j, a
+        unsat = (J[None, :, :] * s[:, :, None] * s[:, nb] < 0).sum(-1)   # [R][N]
+        n_und = (unsat <= 2).sum(0)                                       # walkers per word
+        b = np.zeros_like(n_und, dtype=np.float64)
+        for q in range(8):
+            b += np.where(n_und > 0, 1.0 - (1.0 - 2.0 ** (-4 * q)) ** n_und, 0.0)
+        blocks.append(b.mean())
+    return float(np.mean(blocks))
+
+
+def ops_per_word(e_blocks: float) -> float:
+    # 6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
+    # + 4.5 (energy count in the last colour, half the words) + per plane block:
+    # 40 (Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs)) + 4 x 5 compare
+    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (40 + 20)
+
+
+def load_traffic(source_hash):
+    f = ROOT / "profiles" / "lattice_kernel_traffic.json"
+    if not f.exists():
+        return None
+    try:
+        d = json.loads(f.read_text())
+    except Exception:
+        return None
+    return d if d.get("source_sha256") == source_hash else None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("pt_lattice.cu", "pt_device.cuh", "pt_layout.h"):
+        h.update((ROOT / "paper_2509_23043_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def _oracle_worker(a):
+    L, R, index, sweeps, seed = a
+    sys.path.insert(0, str(ROOT))
+    import instances as I
+    import oracle as O
+    inst = I.ea_instance(L, index=index)
+    betas = I.geometric_betas(0.1, 3.0, R)
+    P = 64
+    o = O.Oracle(inst, betas, instance_id=index, prop_enabled=[1] * (R - 2) + [0, 0],
+                 propose_every=10, propose_start=0, seed=seed, pool_size=P)
+    for r in range(R):
+        o.load_pool(r, I.random_configs(inst.n_spins, P, index=r))
+    t0 = time.perf_counter()
+    o.run_cycles(sweeps)
+    return R * inst.n_spins * sweeps, time.perf_counter() - t0
+
+
+def cpu_oracle(args, n_inst, sweeps, pool=None):
+    import multiprocessing as mp
+    cores = min(os.cpu_count() or 1, n_inst)
+    jobs = [(args.L, args.R, k, sweeps, 0x7A972509) for k in range(n_inst)]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    if own:
+        pool.close()
+        pool.join()
+    attempts = sum(r[0] for r in res)
+    return {"value": attempts / (wall * 1e9), "unit": "attempts/ns", "cores": cores,
+            "kind": "oracle", "wall_s": wall,
+            "sample": f"{n_inst} instances of the workload (L={args.L}, R={args.R}) x {sweeps} "
+                      f"cycles each, one process per instance on {cores} host cores"}
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    n_inst, sweeps = args.cpu_sample_instances, max(10, args.cpu_sample_sweeps // 2)
+    cores = min(os.cpu_count() or 1, n_inst)
+    pool = mp.get_context("spawn").Pool(cores)
+    for _ in range(args.warmup):
+        cpu_oracle(args, cores, 2, pool)
+    tot_att, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle(args, n_inst, sweeps, pool)
+        tot_att += r["value"] * r["wall_s"] * 1e9
+        tot_t += r["wall_s"]
+    pool.close()
+    pool.join()
+    v = tot_att / (tot_t * 1e9)
+    sample = (f"each step: {n_inst} instances of the workload (L={args.L}, R={args.R}) x "
+              f"{sweeps} cycles, one process per instance on {cores} host cores")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "attempts/ns",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/u32 spins, f64 acceptance",
+        "data": "synthetic",
+        "config": {"workload": f"batched TAPT, {args.instances} EA +-J L={args.L} instances, "
+                               f"R={args.R}, 100 sweeps per step (oracle sample)"},
+        "cpu_baseline": {"value": v, "unit": "attempts/ns", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "attempts/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU baseline's process pool starts before the first GPU call
+    cpu_pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        cpu_pool = mp.get_context("spawn").Pool(min(os.cpu_count() or 1, args.cpu_sample_instances))
+    import torch
+    import paper_2509_23043_gb300 as pt
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    B = args.instances
+    first = rank * B
+    insts, betas, prop, ids = workload(args, first, B)
+    cfg = make_config(args, args.pool_size)
+    ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids,
+                              stream=stream.cuda_stream)
+    t_pool = time.perf_counter()
+    build_pools(args, insts, betas, prop, ids, ctx)
+    torch.cuda.synchronize()
+    t_pool = time.perf_counter() - t_pool
+    spc = args.sweeps_per_step
+    attempts_per_step = B * args.R * args.L ** 3 * spc
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        pt.run_cycles(ctx, spc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e_blocks = expected_plane_blocks(ctx, args) if rank == 0 else 0.0
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps (untimed)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = attempts_per_step * world * args.steps / (ms * 1e6)
+
+    # ---------------- end to end through the public API: host pool window in, energies out
+    e2e = None
+    if not args.no_e2e:
+        nw = (args.L ** 3 + 31) // 32
+        slab = B * args.R * nw
+        per_step_entries = spc // cfg.propose_every
+        # pinned host copy of the device pool, so reloading a window changes nothing
+        host_pool = torch.empty((args.pool_size, slab), dtype=torch.int32, pin_memory=True)
+        pt.read_proposals_packed(ctx, host_pool.data_ptr(), 0, args.pool_size)
+        eout = torch.empty(B * args.R, dtype=torch.int32, device="cuda")
+        ehost = torch.empty(B * args.R, dtype=torch.int32, pin_memory=True)
+        c, _ = pt.read_counters(ctx, 0)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            n_prop_done = int(c[2]) + k * per_step_entries
+            c0 = n_prop_done % args.pool_size
+            ev2[k][0].record(stream)
+            first_e, left = c0, per_step_entries
+            while left > 0:
+                take = min(left, args.pool_size - first_e)
+                pt.load_proposals_packed(ctx, host_pool.data_ptr() + first_e * slab * 4, first_e, take)
+                left -= take
+                first_e = 0
+            step()
+            pt.energies_device(ctx, eout.data_ptr())
+            ehost.copy_(eout, non_blocking=True)
+            ev2[k][1].record(stream)
+            torch.cuda.synchronize()
+        ms2 = sum(a.elapsed_time(b) for a, b in ev2)
+        e2e = {"value": attempts_per_step * world * args.steps / (ms2 * 1e6), "unit": "attempts/ns",
+               "h2d_bytes_per_step": per_step_entries * slab * 4,
+               "d2h_bytes_per_step": B * args.R * 4}
+
+    # ---------------- roofline of the dominant kernel (the fused cycle kernel = the whole step)
+    words_per_step = B * args.L ** 3 * ((args.R + 31) // 32) * spc
+    ops = ops_per_word(e_blocks) * words_per_step
+    achieved = ops / (ms_step * 1e-3) / 1e12
+    peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    tr = load_traffic(source_hash())
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                "frac": achieved / peak,
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "kernel": "lattice_kernel", "ops_per_attempt": ops_per_word(e_blocks) / 32,
+                "plane_blocks_per_word": e_blocks,
+                "peak_basis": "152 SMs x 128 int lanes x 2070 MHz (nominal)"}
+
+    cpu = None
+    if cpu_pool is not None:
+        cpu = cpu_oracle(args, args.cpu_sample_instances, args.cpu_sample_sweeps, cpu_pool)
+        cpu_pool.close()
+        cpu_pool.join()
+        cpu.pop("wall_s", None)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 bit-packed spins, int32 energies, f64 acceptance",
+            "data": "synthetic",
+            "config": {"workload": f"batched TAPT: {B} EA +-J instances per GPU, L={args.L} "
+                                   f"(N={args.L ** 3}), R={args.R} beta 0.1->3.0 geometric, "
+                                   f"proposals every 10 sweeps on 30 slots from pools of "
+                                   f"{args.pool_size}, {spc} cycles per step",
+                       "global_batch": B * world, "l2": "flushed between timed steps",
+                       "pool_generation_s": round(t_pool, 2),
+                       "pool": f"PT runs of this library: {args.pool_burnin} burn-in sweeps, "
+                               f"then one capture every {args.pool_gap} sweeps (untimed)",
+                       "threads_per_block": pt.info(ctx)["threads"]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": clk.summary(),
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * pt.h - C ABI of the GB300 (sm_103a) library for parallel tempering with global proposals,
+ * i.e. Transformer-Augmented Parallel Tempering (TAPT), arXiv 2509.23043, Algorithm 1.
+ *
+ * The library runs, for a batch of independent Ising instances, the cycle of Algorithm 1:
+ * M local sweeps of every replica (colour class by colour class), the exact energy of every
+ * replica, the global proposal move on the proposal-enabled replicas, and replica exchange
+ * between neighbouring temperatures with alternating parity. Every step runs in CUDA kernels;
+ * the host code only validates, lays out and launches.
+ *
+ * Conventions (shared by every call)
+ *  - spins m in {-1,+1}; energy E(m) = -sum_edges J m_i m_j - sum_i h_i m_i (Supplementary
+ *    S4, the paper's Ising energy convention); local field I_i = sum_j J_ij m_j + h_i
+ *    (Methods, local Monte Carlo sweeps);
+ *  - replica (temperature) slots r = 0..R-1 run hot -> cold: beta ascending;
+ *  - every output is in slot order, whatever internal relabelling the library uses;
+ *  - all host pointers are owned by the caller and are read (or written) during the call
+ *    only; nothing keeps a reference to them;
+ *  - all device work is ordered on the CUDA stream given at creation (or pt_set_stream);
+ *    calls that return host data synchronise that stream;
+ *  - errors: every call returns a pt_status; pt_last_error() gives a message for the last
+ *    failing call of the calling thread. Nothing is thrown across the ABI. A context is not
+ *    thread safe.
+ */
+#ifndef PT_H
+#define PT_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PT_OK = 0,
+    PT_EINVAL = 1,    /* an argument is out of range or inconsistent */
+    PT_ENOMEM = 2,    /* a device or host allocation failed */
+    PT_ECUDA = 3,     /* a CUDA call failed (message holds its error string) */
+    PT_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    PT_ESTATE = 5,    /* the call is not valid in the context's current state */
+    PT_ENOTSUP = 6    /* valid input that this build does not support (e.g. too large) */
+} pt_status;
+
+typedef struct pt_ctx pt_ctx;   /* opaque; owns all device memory of a batch */
+
+/* One Ising instance: the "Ising energy function E" input of Algorithm 1, with its
+ * temperature ladder {beta_r} and proposal-enabled set R_prop.
+ *  instance_id   caller's identifier; it keys every random stream of the instance, so an
+ *                instance evolves identically whatever batch or position it runs in.
+ *  n_spins       N >= 1.
+ *  lattice_L     > 0: a periodic L^3 lattice (N = L^3, L >= 2); the edges must then be the
+ *                3N bonds in canonical order: for site n = x + L(y + L z), its +x, +y, +z
+ *                bonds, in that order (Methods, benchmark instances: 3D spin glass). The
+ *                lattice is coloured (x+y+z) mod 2 for even L and by a 3-colouring for odd L.
+ *                0: a general graph, coloured by DSATUR (Methods, graph coloring).
+ *  n_edges, edge_i, edge_j, edge_J
+ *                undirected couplings J_ij (int32), one per row; parallel edges are summed
+ *                by the energy; self loops are rejected.
+ *  h             N local fields, or NULL for none.
+ *  clamp         N values: 0 free, +1/-1 clamped to that spin; or NULL. Clamped spins are
+ *                never updated (Supplementary S4, output bits clamped).
+ *  n_replicas    R, 1 <= R <= 128.
+ *  beta          R inverse temperatures, ascending, finite, >= 0.
+ *  prop_enabled  R flags (nonzero = slot receives global proposals, the set R_prop), or
+ *                NULL for none. */
+typedef struct {
+    uint32_t instance_id;
+    int32_t n_spins;
+    int32_t lattice_L;
+    int32_t n_edges;
+    const int32_t *edge_i;
+    const int32_t *edge_j;
+    const int32_t *edge_J;
+    const int32_t *h;
+    const int8_t *clamp;
+    int32_t n_replicas;
+    const double *beta;
+    const uint8_t *prop_enabled;
+} pt_instance_desc;
+
+/* Run parameters, shared by every instance of a context.
+ *  update            0 Metropolis (flip iff dE <= 0 or u < floor(2^32 exp(-beta dE))),
+ *                    1 Gibbs / heat bath (m = +1 iff u < floor(2^32 (1 + tanh(beta I)) / 2)),
+ *                    the paper's rule (Methods, Eq. for the Gibbs update). u is a 32-bit
+ *                    Philox4x32-10 draw; thresholds are computed in FP64, capped at 2^32-1.
+ *  sweeps_per_cycle  M of Algorithm 1 (>= 1).
+ *  propose_every, propose_start, propose_stop
+ *                    proposal schedule of pt_run_cycles: after a cycle that ends at sweep
+ *                    count s, a proposal event happens iff propose_every > 0, s >= start,
+ *                    (stop <= 0 or s <= stop) and (s - start) % propose_every == 0.
+ *                    (Fig. 3: start 100, then every sweep; Fig. S5: stop after 100.)
+ *  pool_size         P, proposal-pool capacity per (instance, slot); 0 = no pools.
+ *  seed              64-bit key of every random stream.
+ *  threads_per_block 0 = automatic choice; else a multiple of 32 in [32, 512] (lattice
+ *                    engine) or [32, 1024] (graph engine).
+ */
+typedef struct {
+    int32_t update;
+    int32_t sweeps_per_cycle;
+    int32_t propose_every;
+    int32_t propose_start;
+    int32_t propose_stop;
+    int32_t pool_size;
+    uint64_t seed;
+    int32_t threads_per_block;
+    int32_t reserved;
+} pt_config;
+
+/* Create a batch of n >= 1 instances (all lattice+Metropolis+J=+-1 without field or clamp,
+ * or all otherwise: one engine per context), allocate its device memory (cudaMallocAsync
+ * on `cuda_stream`, a cudaStream_t or NULL for the legacy stream), draw the random initial
+ * state of every replica (Algorithm 1, "Initialize replica states randomly") and compute
+ * its energies. On success *out owns everything; release it with pt_destroy. */
+pt_status pt_create_instances(pt_ctx **out, const pt_instance_desc *descs, int32_t n,
+                              const pt_config *cfg, void *cuda_stream);
+
+/* Copy `count` configurations (host, int8 +-1, row-major [count][N]) into the proposal pool
+ * of instance `inst`, slot `replica`, at positions first .. first+count-1 (< pool_size).
+ * These are the pre-generated proposals S^T_r at beta_r of Algorithm 1. */
+pt_status pt_load_proposals(pt_ctx *ctx, int32_t inst, int32_t replica, const int8_t *spins,
+                            int32_t count, int32_t first);
+
+/* Bulk load of bit-packed pool entries for every instance and slot: host words laid out
+ * [count][instance][slot][ceil(N_instance/32)] uint32 (bit i%32 of word i/32 set iff spin i
+ * is +1), written to pool positions first .. first+count-1. Stream ordered: the host buffer
+ * must stay valid (ideally pinned) until the stream reaches the copy. */
+pt_status pt_load_proposals_packed(pt_ctx *ctx, const uint32_t *words, int32_t first,
+                                   int32_t count);
+
+/* Inverse of pt_load_proposals_packed: copy pool positions first .. first+count-1 of every
+ * instance and slot to host words in the same layout. Synchronises. */
+pt_status pt_read_proposals_packed(pt_ctx *ctx, uint32_t *words, int32_t first, int32_t count);
+
+/* Copy the current configuration of every slot of every instance of `src` into pool
+ * position `entry` of the same instance and slot of `dst` (same batch shape), on the
+ * device. Used to build pools from long PT runs of the method itself. */
+pt_status pt_capture_proposals(pt_ctx *dst, const pt_ctx *src, int32_t entry);
+
+/* n_sweeps local sweeps of every replica of every instance (Methods: one sweep updates
+ * every free spin once), then the exact energy of every replica ("Compute E(S_r)"). */
+pt_status pt_sweep(pt_ctx *ctx, int32_t n_sweeps);
+
+/* One global-proposal event for every instance: for each r in R_prop, take the next pool
+ * entry S^T_r (cursor advances by one mod P whether or not it is accepted), overwrite its
+ * clamped spins, compute E^T_r exactly, and accept with min[1, exp(beta_r (E_r - E^T_r))]
+ * (Eq. P_accept, evaluated in FP64). Uses the energies of the last sweep. */
+pt_status pt_global_propose(pt_ctx *ctx);
+
+/* One replica-exchange event for every instance: event n (1-based) pairs slots (0,1),(2,3)..
+ * when n is odd and (1,2),(3,4).. when n is even, and swaps the configurations and energies
+ * of a pair with min[1, exp((beta_{r+1}-beta_r)(E_{r+1}-E_r))] (Eq. P_swap, FP64). */
+pt_status pt_exchange(pt_ctx *ctx);
+
+/* n_cycles cycles of Algorithm 1, fused on the device: M sweeps, energies, a proposal event
+ * when the schedule says so, an exchange event. */
+pt_status pt_run_cycles(pt_ctx *ctx, int32_t n_cycles);
+
+/* Energies of every replica: host int32 [sum over instances of R], instance by instance,
+ * slot order. Synchronises. */
+pt_status pt_energies(pt_ctx *ctx, int32_t *out);
+
+/* Same, into caller device memory (stream ordered, no synchronisation). */
+pt_status pt_energies_device(pt_ctx *ctx, int32_t *dev_out);
+
+/* State of one instance: spins int8 [R][N] and energies int32 [R] in slot order (either may
+ * be NULL). Synchronises. */
+pt_status pt_read_state(pt_ctx *ctx, int32_t inst, int8_t *spins, int32_t *E);
+
+/* Walker identity held by each slot (int32 [R]): a configuration keeps its walker id when
+ * an exchange moves it to another slot. Synchronises. */
+pt_status pt_read_walkers(pt_ctx *ctx, int32_t inst, int32_t *walker);
+
+/* Overwrite the state of one instance (checkpoint restore): spins int8 [R][N] in slot
+ * order, the walker id of each slot (a permutation of 0..R-1), the counters
+ * {sweeps, exchange events, proposal events} and the pool cursors int32 [R] (may be NULL).
+ * Energies are recomputed on the device. */
+pt_status pt_write_state(pt_ctx *ctx, int32_t inst, const int8_t *spins,
+                         const int32_t *walker, const int64_t counters[3],
+                         const int32_t *cursors);
+
+/* Counters {sweeps, exchange events, proposal events} of one instance, and its pool cursors
+ * int32 [R] (may be NULL). Synchronises. */
+pt_status pt_read_counters(pt_ctx *ctx, int32_t inst, int64_t counters[3], int32_t *cursors);
+
+/* Acceptance counters of one instance (Figs. S7, S8): swaps accepted/attempted per pair
+ * (slot r with r+1) int64 [R-1], proposals accepted/attempted per slot int64 [R]. Any may be
+ * NULL. Synchronises. */
+pt_status pt_read_stats(pt_ctx *ctx, int32_t inst, int64_t *swap_acc, int64_t *swap_att,
+                        int64_t *prop_acc, int64_t *prop_att);
+
+/* Batch shape: number of instances, engine (0 bit-packed lattice engine, 1 graph engine),
+ * threads per block used, and the instance's R and N (inst may be -1 for batch values only).*/
+pt_status pt_info(const pt_ctx *ctx, int32_t inst, int32_t info[6]);
+
+/* Change the stream of all later calls. */
+pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
+
+/* Release all device memory (stream ordered) and the context. NULL is allowed. */
+pt_status pt_destroy(pt_ctx *ctx);
+
+/* Message of the last failing call on the calling thread ("" if none). */
+const char *pt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,887 @@
+// Host side of the C ABI declared in include/pt.h: validation, per-instance layouts, graph
+// colouring, FP64 threshold tables, device allocation and kernel launches. No step of the
+// method's arithmetic on the spins runs here; it all runs in the kernels of pt_lattice.cu
+// and pt_graph.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pt.h"
+#include "pt_device.cuh"
+#include "pt_layout.h"
+
+namespace pt {
+cudaError_t launch_lattice(const LatInst*, int, int, int, size_t, const RunArgs&, int, cudaStream_t);
+cudaError_t launch_lattice_init(const LatInst*, int, uint64_t, cudaStream_t);
+cudaError_t launch_lattice_capture(const LatInst*, const LatInst*, int, int, cudaStream_t);
+cudaError_t launch_lattice_read(const LatInst*, int, int8_t*, int, cudaStream_t);
+cudaError_t launch_lattice_write(const LatInst*, int, const int8_t*, const int32_t*, int, cudaStream_t);
+cudaError_t launch_graph(const GraphInst*, int, int, size_t, const RunArgs&, int, cudaStream_t);
+cudaError_t launch_graph_init(const GraphInst*, int, uint64_t, cudaStream_t);
+cudaError_t launch_graph_capture(const GraphInst*, const GraphInst*, int, int, cudaStream_t);
+cudaError_t launch_graph_read(const GraphInst*, int, int8_t*, int, cudaStream_t);
+cudaError_t launch_graph_write(const GraphInst*, int, const int8_t*, const int32_t*, int, cudaStream_t);
+cudaError_t launch_gather_energies(const int32_t* const*, const int16_t* const*, const int32_t*,
+                                   int, int32_t*, cudaStream_t);
+}  // namespace pt
+
+using namespace pt;
+
+namespace {
+
+thread_local std::string g_err;
+
+pt_status fail(pt_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Thresholds: floor(2^32 p) capped at 2^32 - 1, p evaluated in FP64 exactly as written.
+uint32_t prob_to_threshold(double p) {
+    const double t = std::floor(std::ldexp(p, 32));
+    if (t >= 4294967295.0) return 4294967295u;
+    if (t <= 0.0) return 0u;
+    return (uint32_t)t;
+}
+uint32_t metropolis_threshold(double beta, int dE) {
+    return prob_to_threshold(std::exp(-beta * (double)dE));
+}
+uint32_t gibbs_threshold(double beta, int I) {
+    return prob_to_threshold(0.5 * (1.0 + std::tanh(beta * (double)I)));
+}
+
+// Device arena: host image assembled chunk by chunk, then one allocation and one copy.
+struct Arena {
+    std::vector<uint8_t> host;
+    size_t add(const void* p, size_t bytes) {
+        const size_t off = (host.size() + 255) & ~size_t(255);
+        host.resize(off + bytes);
+        if (p && bytes) memcpy(host.data() + off, p, bytes);
+        return off;
+    }
+    size_t zeros(size_t bytes) { return add(nullptr, bytes); }
+};
+
+// Colouring of a general graph by DSATUR (Methods, graph coloring): repeatedly colour the
+// uncoloured vertex with the most distinct neighbour colours, ties to the larger number of
+// distinct neighbours, then the lower index; use the smallest colour absent among its
+// neighbours. Runs on the whole interaction graph.
+int dsatur(int N, const std::vector<std::vector<int>>& nbr, std::vector<int>& colour) {
+    colour.assign(N, -1);
+    std::vector<int> deg(N);
+    for (int i = 0; i < N; ++i) deg[i] = (int)nbr[i].size();
+    std::vector<std::vector<char>> seen(N);
+    std::vector<int> sat(N, 0);
+    int ncol = 0;
+    for (int step = 0; step < N; ++step) {
+        int best = -1;
+        for (int i = 0; i < N; ++i) {
+            if (colour[i] >= 0) continue;
+            if (best < 0 || sat[i] > sat[best] || (sat[i] == sat[best] && deg[i] > deg[best])) best = i;
+        }
+        std::vector<char> used(ncol + 1, 0);
+        for (int j : nbr[best])
+            if (colour[j] >= 0) used[colour[j]] = 1;
+        int c = 0;
+        while (c < (int)used.size() && used[c]) ++c;
+        colour[best] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        for (int j : nbr[best]) {
+            if (colour[j] >= 0) continue;
+            if ((int)seen[j].size() <= c) seen[j].resize(c + 1, 0);
+            if (!seen[j][c]) { seen[j][c] = 1; ++sat[j]; }
+        }
+    }
+    return ncol;
+}
+
+int lattice_colour(int n, int L) {
+    const int x = n % L, y = (n / L) % L, z = n / (L * L);
+    if (L % 2 == 0) return (x + y + z) % 2;
+    const int cx = (x == L - 1) ? 2 : x % 2, cy = (y == L - 1) ? 2 : y % 2, cz = (z == L - 1) ? 2 : z % 2;
+    return (cx + cy + cz) % 3;
+}
+
+}  // namespace
+
+struct pt_ctx {
+    int engine = 0;           // 0 lattice, 1 graph
+    int n = 0;
+    pt_config cfg{};
+    cudaStream_t stream = nullptr;
+    int threads = 128;
+    size_t smem = 0;
+    int maxW = 1;
+    int with_pool = 0;
+    int NWmax = 0;
+    int uniformN = -1;        // N when all instances share it, else -1
+    std::vector<int> N, R, W, NW, R4;
+    std::vector<size_t> slab_off;  // words, instance offset inside one pool entry
+    size_t slab = 0;               // words per pool entry (all instances, all slots)
+    uint8_t* arena = nullptr;
+    uint32_t* pool = nullptr;
+    std::vector<LatInst> lat;
+    std::vector<GraphInst> gr;
+    LatInst* d_lat = nullptr;
+    GraphInst* d_gr = nullptr;
+    int32_t* d_eoff = nullptr;          // [n] offsets of each instance in the energy output
+    int32_t** d_Eptr = nullptr;         // [n] per-instance E pointers
+    int16_t** d_wosptr = nullptr;       // [n] per-instance wos pointers
+    int32_t* d_eout = nullptr;          // [sum R] gather buffer
+    int totalR = 0;
+    std::vector<int> eoff;
+};
+
+namespace {
+
+pt_status launch_run(pt_ctx* c, int mode, int nn) {
+    RunArgs a{};
+    a.seed = c->cfg.seed;
+    a.mode = mode;
+    a.n = nn;
+    a.M = c->cfg.sweeps_per_cycle;
+    a.every = c->cfg.propose_every;
+    a.start = c->cfg.propose_start;
+    a.stop = c->cfg.propose_stop;
+    a.update = c->cfg.update;
+    cudaError_t e;
+    if (c->engine == 0)
+        e = launch_lattice(c->d_lat, c->n, c->maxW, c->threads, c->smem, a, c->with_pool, c->stream);
+    else
+        e = launch_graph(c->d_gr, c->n, c->threads, c->smem, a, c->with_pool, c->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+bool is_lattice_desc(const pt_instance_desc& d, const pt_config& cfg) {
+    if (d.lattice_L <= 0 || cfg.update != 0) return false;
+    if (d.h)
+        for (int i = 0; i < d.n_spins; ++i)
+            if (d.h[i] != 0) return false;
+    if (d.clamp)
+        for (int i = 0; i < d.n_spins; ++i)
+            if (d.clamp[i] != 0) return false;
+    for (int e = 0; e < d.n_edges; ++e)
+        if (d.edge_J[e] != 1 && d.edge_J[e] != -1) return false;
+    return true;
+}
+
+pt_status validate(const pt_instance_desc& d, int k) {
+    if (d.n_spins <= 0) return fail(PT_EINVAL, "instance %d: n_spins must be > 0", k);
+    if (d.n_replicas < 1 || d.n_replicas > 128)
+        return fail(PT_EINVAL, "instance %d: n_replicas must be in [1, 128]", k);
+    if (!d.beta) return fail(PT_EINVAL, "instance %d: beta is NULL", k);
+    for (int r = 0; r < d.n_replicas; ++r) {
+        if (!std::isfinite(d.beta[r]) || d.beta[r] < 0.0)
+            return fail(PT_EINVAL, "instance %d: beta[%d] must be finite and >= 0", k, r);
+        if (r > 0 && !(d.beta[r - 1] <= d.beta[r]))
+            return fail(PT_EINVAL, "instance %d: beta must be ascending (hot -> cold)", k);
+    }
+    if (d.n_edges < 0 || (d.n_edges > 0 && (!d.edge_i || !d.edge_j || !d.edge_J)))
+        return fail(PT_EINVAL, "instance %d: bad edge arrays", k);
+    for (int e = 0; e < d.n_edges; ++e) {
+        if (d.edge_i[e] < 0 || d.edge_i[e] >= d.n_spins || d.edge_j[e] < 0 || d.edge_j[e] >= d.n_spins)
+            return fail(PT_EINVAL, "instance %d: edge %d out of range", k, e);
+        if (d.edge_i[e] == d.edge_j[e]) return fail(PT_EINVAL, "instance %d: self loop at edge %d", k, e);
+    }
+    if (d.clamp)
+        for (int i = 0; i < d.n_spins; ++i)
+            if (d.clamp[i] < -1 || d.clamp[i] > 1)
+                return fail(PT_EINVAL, "instance %d: clamp values must be -1, 0 or +1", k);
+    if (d.lattice_L > 0) {
+        const long long L = d.lattice_L;
+        if (L < 2 || L * L * L != d.n_spins)
+            return fail(PT_EINVAL, "instance %d: lattice_L must be >= 2 with n_spins = L^3", k);
+        if (d.n_edges != 3 * d.n_spins)
+            return fail(PT_EINVAL, "instance %d: a lattice needs its 3N bonds", k);
+        for (int n = 0; n < d.n_spins; ++n) {
+            const int x = n % (int)L, y = (n / (int)L) % (int)L, z = n / (int)(L * L);
+            const int nb[3] = {(int)(((x + 1) % L) + L * (y + L * z)), (int)(x + L * (((y + 1) % L) + L * z)),
+                               (int)(x + L * (y + L * ((z + 1) % L)))};
+            for (int dd = 0; dd < 3; ++dd)
+                if (d.edge_i[3 * n + dd] != n || d.edge_j[3 * n + dd] != nb[dd])
+                    return fail(PT_EINVAL, "instance %d: lattice bonds not in canonical order (site %d)", k, n);
+        }
+    }
+    return PT_OK;
+}
+
+// -------------------------------------------------------------------------------- lattice
+pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
+    Arena A;
+    const int n = c->n;
+    std::vector<size_t> o_spins(n), o_sdesc(n), o_cs(n), o_E(n), o_sow(n), o_wos(n), o_thr(n),
+        o_beta(n), o_prop(n), o_cur(n), o_eb(n), o_ctr(n), o_st(n);
+    c->lat.resize(n);
+    size_t maxsmem = 0;
+    int maxitems = 0;
+    for (int k = 0; k < n; ++k) {
+        const pt_instance_desc& d = descs[k];
+        const int L = d.lattice_L, N = d.n_spins, R = d.n_replicas, W = (R + 31) / 32, NW = (N + 31) / 32;
+        c->N[k] = N; c->R[k] = R; c->W[k] = W; c->NW[k] = NW; c->R4[k] = W * 32;
+        if (N > 65535) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 65535", k);
+        LatInst& I = c->lat[k];
+        memset(&I, 0, sizeof I);
+        I.iid = d.instance_id; I.L = L; I.N = N; I.R = R; I.W = W; I.NW = NW;
+        I.ncol = (L % 2 == 0) ? 2 : 3;
+        I.P = c->cfg.pool_size;
+        // colour classes
+        std::vector<int> col(N);
+        for (int i = 0; i < N; ++i) col[i] = lattice_colour(i, L);
+        std::vector<uint16_t> cs;
+        cs.reserve(N);
+        I.col_off[0] = 0;
+        for (int cc = 0; cc < I.ncol; ++cc) {
+            for (int i = 0; i < N; ++i)
+                if (col[i] == cc) cs.push_back((uint16_t)i);
+            I.col_off[cc + 1] = (int)cs.size();
+            maxitems = std::max(maxitems, (I.col_off[cc + 1] - I.col_off[cc]) * W);
+        }
+        for (int cc = I.ncol + 1; cc < 4; ++cc) I.col_off[cc] = (int)cs.size();
+        // site descriptors and bit strings of the bonds (for proposal energies)
+        std::vector<uint32_t> sdesc(N, 0u), eb(6 * (size_t)NW, 0u);
+        const int L2 = L * L;
+        for (int i = 0; i < N; ++i) {
+            const int x = i % L, y = (i / L) % L, z = i / L2;
+            const int xm = (x + L - 1) % L, ym = (y + L - 1) % L, zm = (z + L - 1) % L;
+            const int nbr[6] = {(x + 1) % L + L * (y + L * z), xm + L * (y + L * z),
+                                x + L * ((y + 1) % L + L * z), x + L * (ym + L * z),
+                                x + L * (y + L * ((z + 1) % L)), x + L * (y + L * zm)};
+            // bond owners: +d bond of i is edge 3i+d; -d bond of i is the +d bond of nbr[2d+1]
+            const int Jv[6] = {d.edge_J[3 * i + 0], d.edge_J[3 * nbr[1] + 0], d.edge_J[3 * i + 1],
+                               d.edge_J[3 * nbr[3] + 1], d.edge_J[3 * i + 2], d.edge_J[3 * nbr[5] + 2]};
+            const bool wrap[6] = {x == L - 1, x == 0, y == L - 1, y == 0, z == L - 1, z == 0};
+            uint32_t s = 0;
+            int nlow = 0;
+            for (int dir = 0; dir < 6; ++dir) {
+                if (Jv[dir] < 0) s |= 1u << dir;
+                if (wrap[dir]) s |= 1u << (8 + dir);
+                if (col[nbr[dir]] < col[i]) { s |= 1u << (16 + dir); ++nlow; }
+            }
+            if (nlow == 6) s |= 1u << 24;
+            sdesc[i] = s;
+            for (int dd = 0; dd < 3; ++dd) {
+                if (d.edge_J[3 * i + dd] < 0) eb[(size_t)dd * NW + (i >> 5)] |= 1u << (i & 31);
+                if (wrap[2 * dd]) eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
+            }
+        }
+        std::vector<uint32_t> thr(4 * (size_t)R, 0u);
+        for (int r = 0; r < R; ++r) {
+            thr[4 * r + 0] = metropolis_threshold(d.beta[r], 4);
+            thr[4 * r + 1] = metropolis_threshold(d.beta[r], 8);
+            thr[4 * r + 2] = metropolis_threshold(d.beta[r], 12);
+        }
+        std::vector<int16_t> sow(W * 32, -1), wos(R);
+        for (int r = 0; r < R; ++r) { sow[r] = (int16_t)r; wos[r] = (int16_t)r; }
+        std::vector<uint8_t> prop(R, 0);
+        if (d.prop_enabled)
+            for (int r = 0; r < R; ++r) prop[r] = d.prop_enabled[r] ? 1 : 0;
+        o_spins[k] = A.zeros((size_t)W * N * 4);
+        o_sdesc[k] = A.add(sdesc.data(), sdesc.size() * 4);
+        o_cs[k] = A.add(cs.data(), cs.size() * 2);
+        o_E[k] = A.zeros((size_t)W * 32 * 4);
+        o_sow[k] = A.add(sow.data(), sow.size() * 2);
+        o_wos[k] = A.add(wos.data(), wos.size() * 2);
+        o_thr[k] = A.add(thr.data(), thr.size() * 4);
+        o_beta[k] = A.add(d.beta, (size_t)R * 8);
+        o_prop[k] = A.add(prop.data(), prop.size());
+        o_cur[k] = A.zeros((size_t)R * 4);
+        o_eb[k] = A.add(eb.data(), eb.size() * 4);
+        o_ctr[k] = A.zeros(sizeof(Counters));
+        o_st[k] = A.zeros((size_t)4 * R * 8);
+        c->slab_off[k] = c->slab;
+        c->slab += (size_t)R * NW;
+        c->NWmax = std::max(c->NWmax, NW);
+        c->maxW = std::max(c->maxW, W);
+    }
+    // launch shape: about four words per thread per colour class, at most 42 (counter width)
+    int T = c->cfg.threads_per_block;
+    if (T <= 0) {
+        T = ((maxitems / 4 + 31) / 32) * 32;
+        T = std::max(64, std::min(512, T));
+    }
+    if (T % 32 != 0 || T < 32 || T > 512) return fail(PT_EINVAL, "lattice engine: threads_per_block must be a multiple of 32 in [32, 512]");
+    if ((maxitems + T - 1) / T > 42)
+        return fail(PT_ENOTSUP, "too many words per thread (%d); raise threads_per_block", (maxitems + T - 1) / T);
+    c->threads = T;
+    c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
+    for (int k = 0; k < n; ++k) {
+        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0);
+        maxsmem = std::max(maxsmem, l.total);
+    }
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (maxsmem > (size_t)optin)
+        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, optin);
+    c->smem = maxsmem;
+    if (c->maxW > 2) c->maxW = 4;
+
+    CK(cudaMallocAsync((void**)&c->arena, A.host.size(), c->stream));
+    CK(cudaMemcpyAsync(c->arena, A.host.data(), A.host.size(), cudaMemcpyHostToDevice, c->stream));
+    if (c->with_pool) {
+        const size_t words = c->slab * (size_t)c->cfg.pool_size;
+        CK(cudaMallocAsync((void**)&c->pool, words * 4, c->stream));
+        CK(cudaMemsetAsync(c->pool, 0, words * 4, c->stream));
+    }
+    uint8_t* b = c->arena;
+    for (int k = 0; k < n; ++k) {
+        LatInst& I = c->lat[k];
+        I.spins = (uint32_t*)(b + o_spins[k]);
+        I.sdesc = (const uint32_t*)(b + o_sdesc[k]);
+        I.csites = (const uint16_t*)(b + o_cs[k]);
+        I.E = (int32_t*)(b + o_E[k]);
+        I.sow = (int16_t*)(b + o_sow[k]);
+        I.wos = (int16_t*)(b + o_wos[k]);
+        I.thr = (const uint32_t*)(b + o_thr[k]);
+        I.beta = (const double*)(b + o_beta[k]);
+        I.prop = (const uint8_t*)(b + o_prop[k]);
+        I.cursor = (int32_t*)(b + o_cur[k]);
+        I.ebits = (const uint32_t*)(b + o_eb[k]);
+        I.ctr = (Counters*)(b + o_ctr[k]);
+        I.stats = (unsigned long long*)(b + o_st[k]);
+        I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
+        I.pstride = (long long)c->slab;
+    }
+    CK(cudaMallocAsync((void**)&c->d_lat, sizeof(LatInst) * n, c->stream));
+    CK(cudaMemcpyAsync(c->d_lat, c->lat.data(), sizeof(LatInst) * n, cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = launch_lattice_init(c->d_lat, n, c->cfg.seed, c->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "init: %s", cudaGetErrorString(e));
+    return launch_run(c, kModeEnergy, 0);
+}
+
+// -------------------------------------------------------------------------------- graph
+pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
+    Arena A;
+    const int n = c->n;
+    struct Off { size_t spins, clamp, rowp, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st; };
+    std::vector<Off> o(n);
+    c->gr.resize(n);
+    size_t maxsmem = 0;
+    int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block : 128;
+    if (T % 32 != 0 || T < 32 || T > 1024) return fail(PT_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
+    c->threads = T;
+    c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
+    for (int k = 0; k < n; ++k) {
+        const pt_instance_desc& d = descs[k];
+        const int N = d.n_spins, R = d.n_replicas, R4 = (R + 3) & ~3, NW = (N + 31) / 32, NE = d.n_edges;
+        c->N[k] = N; c->R[k] = R; c->W[k] = (R + 31) / 32; c->NW[k] = NW; c->R4[k] = R4;
+        GraphInst& I = c->gr[k];
+        memset(&I, 0, sizeof I);
+        I.iid = d.instance_id; I.N = N; I.R = R; I.R4 = R4; I.NW = NW; I.NE = NE; I.P = c->cfg.pool_size;
+        // CSR with both directions of every edge
+        std::vector<int32_t> rowp(N + 1, 0), adj(2 * (size_t)NE), adjJ(2 * (size_t)NE), h(N, 0);
+        for (int e = 0; e < NE; ++e) { rowp[d.edge_i[e] + 1]++; rowp[d.edge_j[e] + 1]++; }
+        for (int i = 0; i < N; ++i) rowp[i + 1] += rowp[i];
+        std::vector<int> fill(N, 0);
+        for (int e = 0; e < NE; ++e) {
+            const int a = d.edge_i[e], bb = d.edge_j[e];
+            adj[rowp[a] + fill[a]] = bb; adjJ[rowp[a] + fill[a]] = d.edge_J[e]; fill[a]++;
+            adj[rowp[bb] + fill[bb]] = a; adjJ[rowp[bb] + fill[bb]] = d.edge_J[e]; fill[bb]++;
+        }
+        if (d.h) for (int i = 0; i < N; ++i) h[i] = d.h[i];
+        std::vector<int8_t> clamp(N, 0);
+        if (d.clamp) for (int i = 0; i < N; ++i) clamp[i] = d.clamp[i];
+        // largest |local field|
+        long long Imax = 0;
+        for (int i = 0; i < N; ++i) {
+            long long s = std::llabs((long long)h[i]);
+            for (int a = rowp[i]; a < rowp[i + 1]; ++a) s += std::llabs((long long)adjJ[a]);
+            Imax = std::max(Imax, s);
+        }
+        if (Imax > 4096) return fail(PT_ENOTSUP, "instance %d: local fields up to %lld exceed 4096", k, Imax);
+        I.Imax = (int)Imax;
+        // colouring: lattice colouring when a lattice is given, else DSATUR
+        std::vector<int> col(N);
+        int ncol;
+        if (d.lattice_L > 0) {
+            for (int i = 0; i < N; ++i) col[i] = lattice_colour(i, d.lattice_L);
+            ncol = (d.lattice_L % 2 == 0) ? 2 : 3;
+        } else {
+            std::vector<std::vector<int>> nbr(N);
+            for (int i = 0; i < N; ++i) {
+                for (int a = rowp[i]; a < rowp[i + 1]; ++a) {
+                    const int j = adj[a];
+                    bool dup = false;
+                    for (int x : nbr[i]) if (x == j) { dup = true; break; }
+                    if (!dup) nbr[i].push_back(j);
+                }
+            }
+            ncol = dsatur(N, nbr, col);
+        }
+        if (ncol > 32) return fail(PT_ENOTSUP, "instance %d: colouring needs %d > 32 colours", k, ncol);
+        I.ncol = ncol;
+        std::vector<int32_t> cs;
+        I.col_off[0] = 0;
+        for (int cc = 0; cc < ncol; ++cc) {
+            for (int i = 0; i < N; ++i)
+                if (col[i] == cc && clamp[i] == 0) cs.push_back(i);
+            I.col_off[cc + 1] = (int)cs.size();
+        }
+        I.nfree = (int)cs.size();
+        std::vector<uint32_t> cb(2 * (size_t)NW, 0u);
+        for (int i = 0; i < N; ++i) {
+            if (clamp[i] != 0) cb[i >> 5] |= 1u << (i & 31);
+            if (clamp[i] > 0) cb[NW + (i >> 5)] |= 1u << (i & 31);
+        }
+        const int tw = 2 * I.Imax + 1;
+        std::vector<uint32_t> thr((size_t)R * tw, 0u);
+        for (int r = 0; r < R; ++r)
+            for (int v = -I.Imax; v <= I.Imax; ++v)
+                thr[(size_t)r * tw + v + I.Imax] = (c->cfg.update == 1)
+                    ? gibbs_threshold(d.beta[r], v)
+                    : (v > 0 ? metropolis_threshold(d.beta[r], 2 * v) : 0u);
+        std::vector<int16_t> sow(R4, -1), wos(R);
+        for (int r = 0; r < R; ++r) { sow[r] = (int16_t)r; wos[r] = (int16_t)r; }
+        std::vector<uint8_t> prop(R, 0);
+        if (d.prop_enabled) for (int r = 0; r < R; ++r) prop[r] = d.prop_enabled[r] ? 1 : 0;
+        o[k].spins = A.zeros((size_t)N * R4);
+        o[k].clamp = A.add(clamp.data(), N);
+        o[k].rowp = A.add(rowp.data(), rowp.size() * 4);
+        o[k].adj = A.add(adj.data(), adj.size() * 4);
+        o[k].adjJ = A.add(adjJ.data(), adjJ.size() * 4);
+        o[k].h = A.add(h.data(), h.size() * 4);
+        o[k].cs = A.add(cs.data(), std::max<size_t>(cs.size(), 1) * 4);
+        o[k].ei = A.add(d.edge_i, (size_t)NE * 4);
+        o[k].ej = A.add(d.edge_j, (size_t)NE * 4);
+        o[k].eJ = A.add(d.edge_J, (size_t)NE * 4);
+        o[k].cb = A.add(cb.data(), cb.size() * 4);
+        o[k].E = A.zeros((size_t)R4 * 4);
+        o[k].sow = A.add(sow.data(), sow.size() * 2);
+        o[k].wos = A.add(wos.data(), wos.size() * 2);
+        o[k].thr = A.add(thr.data(), thr.size() * 4);
+        o[k].beta = A.add(d.beta, (size_t)R * 8);
+        o[k].prop = A.add(prop.data(), prop.size());
+        o[k].cur = A.zeros((size_t)R * 4);
+        o[k].ctr = A.zeros(sizeof(Counters));
+        o[k].st = A.zeros((size_t)4 * R * 8);
+        c->slab_off[k] = c->slab;
+        c->slab += (size_t)R * NW;
+        c->NWmax = std::max(c->NWmax, NW);
+        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, T / 32, c->with_pool != 0);
+        maxsmem = std::max(maxsmem, l.total);
+    }
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (maxsmem > (size_t)optin)
+        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, optin);
+    c->smem = maxsmem;
+    CK(cudaMallocAsync((void**)&c->arena, A.host.size(), c->stream));
+    CK(cudaMemcpyAsync(c->arena, A.host.data(), A.host.size(), cudaMemcpyHostToDevice, c->stream));
+    if (c->with_pool) {
+        const size_t words = c->slab * (size_t)c->cfg.pool_size;
+        CK(cudaMallocAsync((void**)&c->pool, words * 4, c->stream));
+        CK(cudaMemsetAsync(c->pool, 0, words * 4, c->stream));
+    }
+    uint8_t* b = c->arena;
+    for (int k = 0; k < n; ++k) {
+        GraphInst& I = c->gr[k];
+        I.spins = (int8_t*)(b + o[k].spins);
+        I.clamp = (const int8_t*)(b + o[k].clamp);
+        I.rowp = (const int32_t*)(b + o[k].rowp);
+        I.adj = (const int32_t*)(b + o[k].adj);
+        I.adjJ = (const int32_t*)(b + o[k].adjJ);
+        I.h = (const int32_t*)(b + o[k].h);
+        I.csites = (const int32_t*)(b + o[k].cs);
+        I.ei = (const int32_t*)(b + o[k].ei);
+        I.ej = (const int32_t*)(b + o[k].ej);
+        I.eJ = (const int32_t*)(b + o[k].eJ);
+        I.cbits = (const uint32_t*)(b + o[k].cb);
+        I.E = (int32_t*)(b + o[k].E);
+        I.sow = (int16_t*)(b + o[k].sow);
+        I.wos = (int16_t*)(b + o[k].wos);
+        I.thr = (const uint32_t*)(b + o[k].thr);
+        I.beta = (const double*)(b + o[k].beta);
+        I.prop = (const uint8_t*)(b + o[k].prop);
+        I.cursor = (int32_t*)(b + o[k].cur);
+        I.ctr = (Counters*)(b + o[k].ctr);
+        I.stats = (unsigned long long*)(b + o[k].st);
+        I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
+        I.pstride = (long long)c->slab;
+    }
+    CK(cudaMallocAsync((void**)&c->d_gr, sizeof(GraphInst) * n, c->stream));
+    CK(cudaMemcpyAsync(c->d_gr, c->gr.data(), sizeof(GraphInst) * n, cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = launch_graph_init(c->d_gr, n, c->cfg.seed, c->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "init: %s", cudaGetErrorString(e));
+    return launch_run(c, kModeEnergy, 0);
+}
+
+void release(pt_ctx* c) {
+    if (!c) return;
+    cudaStream_t s = c->stream;
+    if (c->arena) cudaFreeAsync(c->arena, s);
+    if (c->pool) cudaFreeAsync(c->pool, s);
+    if (c->d_lat) cudaFreeAsync(c->d_lat, s);
+    if (c->d_gr) cudaFreeAsync(c->d_gr, s);
+    if (c->d_eoff) cudaFreeAsync(c->d_eoff, s);
+    if (c->d_Eptr) cudaFreeAsync(c->d_Eptr, s);
+    if (c->d_wosptr) cudaFreeAsync(c->d_wosptr, s);
+    if (c->d_eout) cudaFreeAsync(c->d_eout, s);
+    cudaStreamSynchronize(s);
+    delete c;
+}
+
+pt_status check_inst(const pt_ctx* c, int inst) {
+    if (!c) return fail(PT_EINVAL, "ctx is NULL");
+    if (inst < 0 || inst >= c->n) return fail(PT_EINVAL, "instance %d out of range [0, %d)", inst, c->n);
+    return PT_OK;
+}
+
+Counters* ctr_ptr(const pt_ctx* c, int inst) {
+    return c->engine == 0 ? c->lat[inst].ctr : c->gr[inst].ctr;
+}
+int32_t* cursor_ptr(const pt_ctx* c, int inst) {
+    return c->engine == 0 ? c->lat[inst].cursor : c->gr[inst].cursor;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_last_error(void) { return g_err.c_str(); }
+
+pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32_t n,
+                              const pt_config* cfg, void* cuda_stream) {
+    if (!out || !descs || !cfg) return fail(PT_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1) return fail(PT_EINVAL, "n must be >= 1");
+    if (cfg->update != 0 && cfg->update != 1) return fail(PT_EINVAL, "update must be 0 or 1");
+    if (cfg->sweeps_per_cycle < 1) return fail(PT_EINVAL, "sweeps_per_cycle must be >= 1");
+    if (cfg->pool_size < 0) return fail(PT_EINVAL, "pool_size must be >= 0");
+    if (cfg->propose_every < 0) return fail(PT_EINVAL, "propose_every must be >= 0");
+    for (int k = 0; k < n; ++k) {
+        pt_status s = validate(descs[k], k);
+        if (s != PT_OK) return s;
+    }
+    const bool lat0 = is_lattice_desc(descs[0], *cfg);
+    for (int k = 1; k < n; ++k)
+        if (is_lattice_desc(descs[k], *cfg) != lat0)
+            return fail(PT_EINVAL, "instance %d: a context holds only lattice-engine or only graph-engine instances", k);
+    pt_ctx* c = new (std::nothrow) pt_ctx();
+    if (!c) return fail(PT_ENOMEM, "host allocation failed");
+    c->engine = lat0 ? 0 : 1;
+    c->n = n;
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->N.resize(n); c->R.resize(n); c->W.resize(n); c->NW.resize(n); c->R4.resize(n);
+    c->slab_off.resize(n);
+    pt_status s = lat0 ? build_lattice(c, descs) : build_graph(c, descs);
+    if (s != PT_OK) { release(c); return s; }
+    // energy gather tables
+    c->eoff.resize(n);
+    int tot = 0;
+    std::vector<int32_t*> Ep(n);
+    std::vector<int16_t*> Wp(n);
+    for (int k = 0; k < n; ++k) {
+        c->eoff[k] = tot;
+        tot += c->R[k];
+        Ep[k] = lat0 ? c->lat[k].E : c->gr[k].E;
+        Wp[k] = lat0 ? c->lat[k].wos : c->gr[k].wos;
+    }
+    std::vector<int32_t> eoff_ext(c->eoff);
+    eoff_ext.push_back(tot);
+    c->totalR = tot;
+    int uniform = c->N[0];
+    for (int k = 1; k < n; ++k) if (c->N[k] != uniform) uniform = -1;
+    c->uniformN = uniform;
+    cudaError_t e;
+    if ((e = cudaMallocAsync((void**)&c->d_eoff, (n + 1) * 4, c->stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void**)&c->d_Eptr, n * sizeof(void*), c->stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void**)&c->d_wosptr, n * sizeof(void*), c->stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void**)&c->d_eout, (size_t)tot * 4, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_eoff, eoff_ext.data(), (n + 1) * 4, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_Eptr, Ep.data(), n * sizeof(void*), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_wosptr, Wp.data(), n * sizeof(void*), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        release(c);
+        return fail(PT_ECUDA, "create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return PT_OK;
+}
+
+pt_status pt_destroy(pt_ctx* ctx) {
+    release(ctx);
+    return PT_OK;
+}
+
+pt_status pt_set_stream(pt_ctx* ctx, void* s) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    ctx->stream = (cudaStream_t)s;
+    return PT_OK;
+}
+
+pt_status pt_info(const pt_ctx* ctx, int32_t inst, int32_t info[6]) {
+    if (!ctx || !info) return fail(PT_EINVAL, "NULL argument");
+    info[0] = ctx->n;
+    info[1] = ctx->engine;
+    info[2] = ctx->threads;
+    info[3] = (int32_t)ctx->smem;
+    info[4] = (inst >= 0 && inst < ctx->n) ? ctx->R[inst] : ctx->totalR;
+    info[5] = (inst >= 0 && inst < ctx->n) ? ctx->N[inst] : ctx->uniformN;
+    return PT_OK;
+}
+
+pt_status pt_sweep(pt_ctx* ctx, int32_t n_sweeps) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    if (n_sweeps < 0) return fail(PT_EINVAL, "n_sweeps must be >= 0");
+    if (n_sweeps == 0) return PT_OK;
+    return launch_run(ctx, kModeSweeps, n_sweeps);
+}
+
+pt_status pt_global_propose(pt_ctx* ctx) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    return launch_run(ctx, kModePropose, 0);
+}
+
+pt_status pt_exchange(pt_ctx* ctx) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    return launch_run(ctx, kModeExchange, 0);
+}
+
+pt_status pt_run_cycles(pt_ctx* ctx, int32_t n_cycles) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    if (n_cycles < 0) return fail(PT_EINVAL, "n_cycles must be >= 0");
+    if (n_cycles == 0) return PT_OK;
+    return launch_run(ctx, kModeCycles, n_cycles);
+}
+
+pt_status pt_energies_device(pt_ctx* ctx, int32_t* dev_out) {
+    if (!ctx || !dev_out) return fail(PT_EINVAL, "NULL argument");
+    cudaError_t e = launch_gather_energies(ctx->d_Eptr, ctx->d_wosptr, ctx->d_eoff, ctx->n, dev_out, ctx->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "gather: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+pt_status pt_energies(pt_ctx* ctx, int32_t* out) {
+    if (!ctx || !out) return fail(PT_EINVAL, "NULL argument");
+    pt_status s = pt_energies_device(ctx, ctx->d_eout);
+    if (s != PT_OK) return s;
+    CK(cudaMemcpyAsync(out, ctx->d_eout, (size_t)ctx->totalR * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_read_state(pt_ctx* ctx, int32_t inst, int8_t* spins, int32_t* E) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int R = ctx->R[inst], N = ctx->N[inst];
+    if (spins) {
+        int8_t* d = nullptr;
+        CK(cudaMallocAsync((void**)&d, (size_t)R * N, ctx->stream));
+        cudaError_t e = ctx->engine == 0 ? launch_lattice_read(ctx->d_lat, inst, d, R * N, ctx->stream)
+                                         : launch_graph_read(ctx->d_gr, inst, d, R * N, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(spins, d, (size_t)R * N, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaFreeAsync(d, ctx->stream);
+        if (e != cudaSuccess) return fail(PT_ECUDA, "read_state: %s", cudaGetErrorString(e));
+    }
+    if (E) {
+        s = pt_energies_device(ctx, ctx->d_eout);
+        if (s != PT_OK) return s;
+        CK(cudaMemcpyAsync(E, ctx->d_eout + ctx->eoff[inst], (size_t)R * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_read_walkers(pt_ctx* ctx, int32_t inst, int32_t* walker) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    if (!walker) return fail(PT_EINVAL, "walker is NULL");
+    const int R = ctx->R[inst];
+    std::vector<int16_t> w(R);
+    const int16_t* src = ctx->engine == 0 ? ctx->lat[inst].wos : ctx->gr[inst].wos;
+    CK(cudaMemcpyAsync(w.data(), src, (size_t)R * 2, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < R; ++r) walker[r] = w[r];
+    return PT_OK;
+}
+
+pt_status pt_read_counters(pt_ctx* ctx, int32_t inst, int64_t counters[3], int32_t* cursors) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    Counters h{};
+    CK(cudaMemcpyAsync(&h, ctr_ptr(ctx, inst), sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cursors)
+        CK(cudaMemcpyAsync(cursors, cursor_ptr(ctx, inst), (size_t)ctx->R[inst] * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (counters) { counters[0] = h.sweeps; counters[1] = h.n_ex; counters[2] = h.n_prop; }
+    return PT_OK;
+}
+
+pt_status pt_read_stats(pt_ctx* ctx, int32_t inst, int64_t* swap_acc, int64_t* swap_att,
+                        int64_t* prop_acc, int64_t* prop_att) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int R = ctx->R[inst];
+    std::vector<unsigned long long> h(4 * (size_t)R);
+    const unsigned long long* src = ctx->engine == 0 ? ctx->lat[inst].stats : ctx->gr[inst].stats;
+    CK(cudaMemcpyAsync(h.data(), src, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < R; ++r) {
+        if (r + 1 < R) {
+            if (swap_acc) swap_acc[r] = (int64_t)h[r];
+            if (swap_att) swap_att[r] = (int64_t)h[R + r];
+        }
+        if (prop_acc) prop_acc[r] = (int64_t)h[2 * R + r];
+        if (prop_att) prop_att[r] = (int64_t)h[3 * R + r];
+    }
+    return PT_OK;
+}
+
+pt_status pt_write_state(pt_ctx* ctx, int32_t inst, const int8_t* spins, const int32_t* walker,
+                         const int64_t counters[3], const int32_t* cursors) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    if (!spins || !walker || !counters) return fail(PT_EINVAL, "NULL argument");
+    const int R = ctx->R[inst], N = ctx->N[inst];
+    std::vector<int> seen(R, 0);
+    for (int r = 0; r < R; ++r) {
+        if (walker[r] < 0 || walker[r] >= R || seen[walker[r]]++) return fail(PT_EINVAL, "walker ids must be a permutation of 0..R-1");
+    }
+    for (size_t i = 0; i < (size_t)R * N; ++i)
+        if (spins[i] != 1 && spins[i] != -1) return fail(PT_EINVAL, "spins must be +-1");
+    if (cursors && ctx->cfg.pool_size > 0)
+        for (int r = 0; r < R; ++r)
+            if (cursors[r] < 0 || cursors[r] >= ctx->cfg.pool_size) return fail(PT_EINVAL, "cursor out of range");
+    std::vector<int8_t> hclamp;
+    if (ctx->engine == 1) {  // clamped spins must keep their values
+        hclamp.resize(N);
+        CK(cudaMemcpyAsync(hclamp.data(), ctx->gr[inst].clamp, N, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < R; ++r)
+            for (int i = 0; i < N; ++i)
+                if (hclamp[i] != 0 && spins[(size_t)r * N + i] != hclamp[i])
+                    return fail(PT_EINVAL, "spin %d of slot %d contradicts its clamp", i, r);
+    }
+    // walker labels
+    const int Wpad = ctx->engine == 0 ? ctx->W[inst] * 32 : ctx->R4[inst];
+    std::vector<int16_t> wos(R), sow(Wpad, -1);
+    for (int r = 0; r < R; ++r) { wos[r] = (int16_t)walker[r]; sow[walker[r]] = (int16_t)r; }
+    int8_t* d_sp = nullptr;
+    int32_t* d_w = nullptr;
+    CK(cudaMallocAsync((void**)&d_sp, (size_t)R * N, ctx->stream));
+    CK(cudaMallocAsync((void**)&d_w, (size_t)R * 4, ctx->stream));
+    CK(cudaMemcpyAsync(d_sp, spins, (size_t)R * N, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_w, walker, (size_t)R * 4, cudaMemcpyHostToDevice, ctx->stream));
+    Counters h{};
+    h.sweeps = counters[0]; h.n_ex = counters[1]; h.n_prop = counters[2];
+    cudaError_t e;
+    if (ctx->engine == 0) {
+        CK(cudaMemcpyAsync(ctx->lat[inst].wos, wos.data(), R * 2, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->lat[inst].sow, sow.data(), Wpad * 2, cudaMemcpyHostToDevice, ctx->stream));
+        e = launch_lattice_write(ctx->d_lat, inst, d_sp, d_w, ctx->W[inst] * N, ctx->stream);
+    } else {
+        CK(cudaMemcpyAsync(ctx->gr[inst].wos, wos.data(), R * 2, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->gr[inst].sow, sow.data(), Wpad * 2, cudaMemcpyHostToDevice, ctx->stream));
+        e = launch_graph_write(ctx->d_gr, inst, d_sp, d_w, R * N, ctx->stream);
+    }
+    if (e != cudaSuccess) return fail(PT_ECUDA, "write_state: %s", cudaGetErrorString(e));
+    CK(cudaMemcpyAsync(ctr_ptr(ctx, inst), &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+    if (cursors && ctx->cfg.pool_size > 0)
+        CK(cudaMemcpyAsync(cursor_ptr(ctx, inst), cursors, (size_t)R * 4, cudaMemcpyHostToDevice, ctx->stream));
+    cudaFreeAsync(d_sp, ctx->stream);
+    cudaFreeAsync(d_w, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    // energies of the written state (all instances: the energy pass leaves others unchanged)
+    s = launch_run(ctx, kModeEnergy, 0);
+    if (s != PT_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_load_proposals(pt_ctx* ctx, int32_t inst, int32_t replica, const int8_t* spins,
+                            int32_t count, int32_t first) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int R = ctx->R[inst], N = ctx->N[inst], NW = ctx->NW[inst], P = ctx->cfg.pool_size;
+    if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
+    if (replica < 0 || replica >= R) return fail(PT_EINVAL, "replica %d out of range", replica);
+    if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
+    if (count == 0) return PT_OK;
+    if (!spins) return fail(PT_EINVAL, "spins is NULL");
+    std::vector<uint32_t> bits((size_t)count * NW, 0u);
+    for (int e = 0; e < count; ++e)
+        for (int i = 0; i < N; ++i) {
+            const int8_t v = spins[(size_t)e * N + i];
+            if (v != 1 && v != -1) return fail(PT_EINVAL, "pool spins must be +-1");
+            if (v > 0) bits[(size_t)e * NW + (i >> 5)] |= 1u << (i & 31);
+        }
+    uint32_t* dst = ctx->pool + ctx->slab_off[inst] + (size_t)replica * NW + (size_t)first * ctx->slab;
+    CK(cudaMemcpy2DAsync(dst, ctx->slab * 4, bits.data(), (size_t)NW * 4, (size_t)NW * 4, count,
+                         cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_load_proposals_packed(pt_ctx* ctx, const uint32_t* words, int32_t first, int32_t count) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    const int P = ctx->cfg.pool_size;
+    if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
+    if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
+    if (count == 0) return PT_OK;
+    if (!words) return fail(PT_EINVAL, "words is NULL");
+    CK(cudaMemcpyAsync(ctx->pool + (size_t)first * ctx->slab, words, (size_t)count * ctx->slab * 4,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_read_proposals_packed(pt_ctx* ctx, uint32_t* words, int32_t first, int32_t count) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    const int P = ctx->cfg.pool_size;
+    if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
+    if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
+    if (count == 0) return PT_OK;
+    if (!words) return fail(PT_EINVAL, "words is NULL");
+    CK(cudaMemcpyAsync(words, ctx->pool + (size_t)first * ctx->slab, (size_t)count * ctx->slab * 4,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_capture_proposals(pt_ctx* dst, const pt_ctx* src, int32_t entry) {
+    if (!dst || !src) return fail(PT_EINVAL, "NULL context");
+    if (dst->engine != src->engine || dst->n != src->n) return fail(PT_EINVAL, "batches differ in shape");
+    for (int k = 0; k < dst->n; ++k)
+        if (dst->N[k] != src->N[k] || dst->R[k] != src->R[k]) return fail(PT_EINVAL, "instance %d differs in shape", k);
+    if (dst->cfg.pool_size <= 0) return fail(PT_ESTATE, "destination has no pool");
+    if (entry < 0 || entry >= dst->cfg.pool_size) return fail(PT_EINVAL, "entry out of range");
+    cudaError_t e = dst->engine == 0 ? launch_lattice_capture(dst->d_lat, src->d_lat, dst->n, entry, dst->stream)
+                                     : launch_graph_capture(dst->d_gr, src->d_gr, dst->n, entry, dst->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "capture: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------ gather kernel
+namespace pt {
+__global__ void gather_energies_kernel(const int32_t* const* E, const int16_t* const* wos,
+                                       const int32_t* off, int32_t* out) {
+    const int k = blockIdx.x;
+    const int R = off[k + 1] - off[k];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) out[off[k] + r] = E[k][wos[k][r]];
+}
+cudaError_t launch_gather_energies(const int32_t* const* E, const int16_t* const* wos,
+                                   const int32_t* off, int n, int32_t* out, cudaStream_t s) {
+    gather_energies_kernel<<<n, 128, 0, s>>>(E, wos, off, out);
+    return cudaGetLastError();
+}
+}  // namespace pt

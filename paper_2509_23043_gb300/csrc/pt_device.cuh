@@ -1,0 +1,157 @@
+// Device-side building blocks shared by the lattice (bit-packed) and graph kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pt {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Random-stream domains: the top byte of counter word 2 (see the kernels for the layout).
+constexpr uint32_t kDomInit = 0u, kDomPlane = 1u, kDomWord = 2u, kDomExch = 3u, kDomProp = 4u;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64-bit
+// multiplies with xors, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Global-move decision (Eq. P_swap and Eq. P_accept): accept with min[1, exp(x)] using a
+// 32-bit uniform u, i.e. iff x >= 0 or u + 1 <= 2^32 exp(x), in FP64.
+__device__ __forceinline__ bool accept_fp64(double x, uint32_t u) {
+    if (x >= 0.0) return true;
+    return ((double)u + 1.0) <= ldexp(exp(x), 32);
+}
+
+// bitwise select: bits of a where m is 1, of b where m is 0
+__device__ __forceinline__ uint32_t mux(uint32_t m, uint32_t a, uint32_t b) {
+    return (m & a) | (~m & b);
+}
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
+    return (a & b) | (a & c) | (b & c);
+}
+
+// 32x32 bit transpose across a warp: lane l holds row l (bit b = column b); afterwards lane
+// t holds column t (bit l = old bit t of lane l). Five butterfly stages, each a shuffle, a
+// per-lane rotate and a bitwise select.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = (j == 16) ? 0x0000FFFFu : (j == 8) ? 0x00FF00FFu
+                         : (j == 4) ? 0x0F0F0F0Fu : (j == 2) ? 0x33333333u : 0x55555555u;
+        const bool upper = (lane & j) != 0;
+        const uint32_t y = __shfl_xor_sync(kFull, x, j);
+        const uint32_t rot = __funnelshift_l(y, y, upper ? 32 - j : j);
+        const uint32_t keep = upper ? ~m : m;
+        x = (x & keep) | (rot & ~keep);
+    }
+    return x;
+}
+
+// 32 bits of a bit string S[0..nw) starting at bit position pos (may be out of range:
+// bits outside the string read as 0).
+__device__ __forceinline__ uint32_t bits_at(const uint32_t* S, int nw, int pos) {
+    const int q = pos >> 5;
+    const int r = pos & 31;
+    const uint32_t lo = (q >= 0 && q < nw) ? S[q] : 0u;
+    const uint32_t hi = (q + 1 >= 0 && q + 1 < nw) ? S[q + 1] : 0u;
+    return __funnelshift_r(lo, hi, r);
+}
+
+// ------------------------------------------------------------------------------------
+// Per-instance descriptors (device memory). Pointers are into the context's buffers.
+// ------------------------------------------------------------------------------------
+struct Counters {
+    long long sweeps;   // sweeps done (the sweep index of the next sweep)
+    long long n_ex;     // exchange events done
+    long long n_prop;   // proposal events done
+    long long pad;
+};
+
+// Lattice engine: periodic L^3, J = +-1, no field, no clamp, Metropolis. Spins bit-packed:
+// word [wb][site], bit b = walker 32*wb + b.
+struct LatInst {
+    uint32_t iid;
+    int32_t L, N, R, W, NW, ncol, P;
+    int32_t col_off[4];
+    uint32_t* spins;       // [W][N]
+    const uint32_t* sdesc; // [N]: bits 0-5 bond negative (+x,-x,+y,-y,+z,-z),
+                           //      8-13 wrap in that direction, 16-21 neighbour has a lower
+                           //      colour, 24 all six neighbours lower
+    const uint16_t* csites;// [N] sites in colour order
+    int32_t* E;            // [W*32] per walker
+    int16_t* sow;          // [W*32] slot of walker (-1: padding lane)
+    int16_t* wos;          // [R] walker of slot
+    const uint32_t* thr;   // [R][4] Metropolis thresholds for dE = 4, 8, 12 (and 0 pad)
+    const double* beta;    // [R]
+    const uint8_t* prop;   // [R]
+    int32_t* cursor;       // [R]
+    const uint32_t* ebits; // [6][NW]: negative-bond bits +x,+y,+z; wrap bits x,y,z
+    const uint32_t* pool;  // entry e, slot r at pool + e * pstride + r * NW
+    long long pstride;     // words between consecutive pool entries
+    Counters* ctr;
+    unsigned long long* stats;  // [4][R]: swap acc, swap att, prop acc, prop att
+};
+
+// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spins int8 [N][R4].
+struct GraphInst {
+    uint32_t iid;
+    int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
+    int32_t col_off[33];
+    int8_t* spins;           // [N][R4]
+    const int8_t* clamp;     // [N]: 0 free, +-1 clamped
+    const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
+    const int32_t* adj;      // [2 NE] neighbour index
+    const int32_t* adjJ;     // [2 NE] coupling
+    const int32_t* h;        // [N]
+    const int32_t* csites;   // [nfree] free sites in colour order
+    const int32_t* ei;       // [NE]
+    const int32_t* ej;       // [NE]
+    const int32_t* eJ;       // [NE]
+    const uint32_t* cbits;   // [2][NW]: clamped mask, clamp value (+1) bits
+    int32_t* E;              // [R4] per walker
+    int16_t* sow;            // [R4]
+    int16_t* wos;            // [R]
+    const uint32_t* thr;     // [R][2*Imax+1]
+    const double* beta;      // [R]
+    const uint8_t* prop;     // [R]
+    int32_t* cursor;         // [R]
+    const uint32_t* pool;    // entry e, slot r at pool + e * pstride + r * NW
+    long long pstride;
+    Counters* ctr;
+    unsigned long long* stats;
+};
+
+// Kernel modes
+enum : int32_t {
+    kModeSweeps = 1,     // n sweeps then energies
+    kModePropose = 2,    // one proposal event
+    kModeExchange = 4,   // one exchange event
+    kModeCycles = 8,     // n cycles of Algorithm 1
+    kModeEnergy = 16,    // energies only
+};
+
+struct RunArgs {
+    uint64_t seed;
+    int32_t mode;
+    int32_t n;
+    int32_t M, every, start, stop;
+    int32_t update;      // graph engine: 0 Metropolis, 1 Gibbs
+    int32_t pad;
+};
+
+__device__ __forceinline__ bool proposal_due(long long s, const RunArgs& a) {
+    if (a.every <= 0 || s < a.start) return false;
+    if (a.stop > 0 && s > a.stop) return false;
+    return ((s - a.start) % a.every) == 0;
+}
+
+}  // namespace pt

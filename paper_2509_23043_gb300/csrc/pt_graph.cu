@@ -1,0 +1,364 @@
+// Graph engine: parallel tempering with global proposals (Algorithm 1 of arXiv 2509.23043)
+// on general sparse integer-coupled Ising graphs with fields and clamped spins (e.g. the
+// invertible multiplier of Supplementary S4), Gibbs (the paper's rule, Methods) or
+// Metropolis local moves, colour class by colour class (DSATUR colouring, Methods).
+//
+// Layout. Spins int8 [N][R4] (R4 = R rounded up to 4): one 32-bit word holds four walkers of
+// one site, so a thread updates four walkers of one site with one Philox call, whose four
+// output words are the four walkers' uniforms. A walker keeps its storage column; exchange
+// permutes slot <-> walker labels, thresholds are looked up by the walker's current slot.
+#include "pt_device.cuh"
+#include "pt_layout.h"
+
+namespace pt {
+
+struct GraphSmem {
+    int8_t* spins;
+    uint32_t* thr;
+    int32_t* rowp;
+    int32_t* adj;
+    int32_t* adjJ;
+    int32_t* h;
+    int32_t* csites;
+    int32_t* E;
+    int32_t* Eacc;
+    uint32_t* st;
+    int16_t* sow;
+    int16_t* wos;
+    uint32_t* pbuf;
+};
+
+__device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst& I, int nwarps,
+                                                 bool with_pool) {
+    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, nwarps, with_pool);
+    GraphSmem S;
+    S.spins = reinterpret_cast<int8_t*>(base + l.spins);
+    S.thr = reinterpret_cast<uint32_t*>(base + l.thr);
+    S.rowp = reinterpret_cast<int32_t*>(base + l.rowp);
+    S.adj = reinterpret_cast<int32_t*>(base + l.adj);
+    S.adjJ = reinterpret_cast<int32_t*>(base + l.adjJ);
+    S.h = reinterpret_cast<int32_t*>(base + l.h);
+    S.csites = reinterpret_cast<int32_t*>(base + l.csites);
+    S.E = reinterpret_cast<int32_t*>(base + l.E);
+    S.Eacc = reinterpret_cast<int32_t*>(base + l.Eacc);
+    S.st = reinterpret_cast<uint32_t*>(base + l.st);
+    S.sow = reinterpret_cast<int16_t*>(base + l.sow);
+    S.wos = reinterpret_cast<int16_t*>(base + l.wos);
+    S.pbuf = reinterpret_cast<uint32_t*>(base + l.pbuf);
+    return S;
+}
+
+__device__ __forceinline__ int sbyte(uint32_t w, int k) {
+    return (int)(int8_t)((w >> (8 * k)) & 0xFFu);
+}
+
+// One sweep: every free site of every colour class, four walkers per thread.
+__device__ void graph_sweep(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
+                            uint32_t sweep_idx, int update) {
+    const int Q = I.R4 >> 2;
+    const int tw = 2 * I.Imax + 1;
+    uint32_t* sp = reinterpret_cast<uint32_t*>(S.spins);
+    for (int c = 0; c < I.ncol; ++c) {
+        const int base = I.col_off[c];
+        const int nc = I.col_off[c + 1] - base;
+        const int nitems = nc * Q;
+        for (int q = threadIdx.x; q < nitems; q += blockDim.x) {
+            const int quad = q / nc;
+            const int site = S.csites[base + (q - quad * nc)];
+            const int hs = S.h[site];
+            int f0 = hs, f1 = hs, f2 = hs, f3 = hs;
+            for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
+                const uint32_t wd = sp[S.adj[a] * Q + quad];
+                const int J = S.adjJ[a];
+                f0 += J * sbyte(wd, 0);
+                f1 += J * sbyte(wd, 1);
+                f2 += J * sbyte(wd, 2);
+                f3 += J * sbyte(wd, 3);
+            }
+            const uint32_t own = sp[site * Q + quad];
+            const uint4 r = philox(make_uint4((uint32_t)site, sweep_idx,
+                                              (kDomWord << 24) | (uint32_t)quad, I.iid), k0, k1);
+            const int f[4] = {f0, f1, f2, f3};
+            const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+            uint32_t out = own;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const int w = quad * 4 + k4;
+                if (w >= I.R) break;
+                const int slot = S.sow[w];
+                const int m = sbyte(own, k4);
+                int nm;
+                if (update == 1) {
+                    nm = (u[k4] < S.thr[slot * tw + f[k4] + I.Imax]) ? 1 : -1;
+                } else {
+                    const int mI = m * f[k4];   // dE = 2 m I
+                    nm = (mI <= 0 || u[k4] < S.thr[slot * tw + mI + I.Imax]) ? -m : m;
+                }
+                out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(uint8_t)(int8_t)nm << (8 * k4));
+            }
+            if (out != own) sp[site * Q + quad] = out;
+        }
+        __syncthreads();
+    }
+}
+
+// Exact energies of every walker: E = -1/2 sum_i m_i (I_i + h_i), lanes = walkers.
+__device__ void graph_energy(const GraphInst& I, GraphSmem& S) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int wb = 0; wb * 32 < I.R; ++wb) {
+        const int w = wb * 32 + lane;
+        int acc = 0;
+        if (w < I.R) {
+            for (int site = warp; site < I.N; site += nwarps) {
+                const int hs = S.h[site];
+                int f = hs;
+                for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a)
+                    f += S.adjJ[a] * (int)S.spins[S.adj[a] * I.R4 + w];
+                acc += (int)S.spins[site * I.R4 + w] * (f + hs);
+            }
+            atomicAdd(&S.Eacc[w], acc);
+        }
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < I.R4; w += blockDim.x) {
+        S.E[w] = -(S.Eacc[w] / 2);
+        S.Eacc[w] = 0;
+    }
+    __syncthreads();
+}
+
+__device__ void graph_exchange(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
+                               long long n_ex) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int first = (n_ex & 1) ? 0 : 1;
+        for (int r = first + 2 * lane; r + 1 < I.R; r += 64) {
+            const int wa = S.wos[r], wc = S.wos[r + 1];
+            const int dE = S.E[wc] - S.E[wa];
+            const double x = (I.beta[r + 1] - I.beta[r]) * (double)dE;
+            bool acc = x >= 0.0;
+            if (!acc) {
+                const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_ex, kDomExch << 24, I.iid),
+                                       k0, k1);
+                acc = accept_fp64(x, q.x);
+            }
+            S.st[I.R + r] += 1u;
+            if (acc) {
+                S.wos[r] = (int16_t)wc;
+                S.wos[r + 1] = (int16_t)wa;
+                S.sow[wa] = (int16_t)(r + 1);
+                S.sow[wc] = (int16_t)r;
+                S.st[r] += 1u;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
+                              long long n_prop) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int N = I.N, NW = I.NW;
+    uint32_t* buf = S.pbuf + warp * NW;
+    for (int r = warp; r < I.R; r += nwarps) {
+        if (!I.prop[r]) continue;
+        const int w = S.wos[r];
+        const int c = I.cursor[r];
+        const uint32_t* entry = I.pool + (size_t)c * I.pstride + (size_t)r * NW;
+        for (int k = lane; k < NW; k += 32)
+            buf[k] = (__ldg(entry + k) & ~I.cbits[k]) | I.cbits[NW + k];  // clamps applied
+        __syncwarp();
+        int e = 0;
+        for (int k = lane; k < I.NE; k += 32) {
+            const int a = __ldg(I.ei + k), b = __ldg(I.ej + k);
+            const uint32_t ba = (buf[a >> 5] >> (a & 31)) & 1u, bb = (buf[b >> 5] >> (b & 31)) & 1u;
+            e -= (ba == bb) ? __ldg(I.eJ + k) : -__ldg(I.eJ + k);
+        }
+        for (int i = lane; i < N; i += 32)
+            e -= ((buf[i >> 5] >> (i & 31)) & 1u) ? S.h[i] : -S.h[i];
+        const int ET = __reduce_add_sync(kFull, e);
+        int acc = 0;
+        if (lane == 0) {
+            const double x = I.beta[r] * (double)(S.E[w] - ET);
+            acc = x >= 0.0;
+            if (!acc) {
+                const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid),
+                                       k0, k1);
+                acc = accept_fp64(x, q.x);
+            }
+        }
+        acc = __shfl_sync(kFull, acc, 0);
+        if (acc) {
+            for (int i = lane; i < N; i += 32)
+                S.spins[i * I.R4 + w] = ((buf[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
+        }
+        if (lane == 0) {
+            if (acc) S.E[w] = ET;
+            I.cursor[r] = (c + 1) % I.P;
+            S.st[3 * I.R + r] += 1u;
+            if (acc) S.st[2 * I.R + r] += 1u;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict__ insts,
+                                                     RunArgs a, int with_pool) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const GraphInst& I = insts[blockIdx.x];
+    const int nwarps = blockDim.x >> 5;
+    GraphSmem S = carve_graph(smem, I, nwarps, with_pool != 0);
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int N = I.N, R = I.R, R4 = I.R4;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(I.spins);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(S.spins);
+        for (int i = tid; i < N * R4 / 4; i += T) dst[i] = src[i];
+    }
+    const int tw = 2 * I.Imax + 1;
+    for (int i = tid; i < R * tw; i += T) S.thr[i] = I.thr[i];
+    for (int i = tid; i <= N; i += T) S.rowp[i] = I.rowp[i];
+    for (int i = tid; i < 2 * I.NE; i += T) { S.adj[i] = I.adj[i]; S.adjJ[i] = I.adjJ[i]; }
+    for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
+    for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
+    for (int i = tid; i < R4; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
+    for (int i = tid; i < R; i += T) S.wos[i] = I.wos[i];
+    for (int i = tid; i < 4 * R; i += T) S.st[i] = 0u;
+    long long sweeps = I.ctr->sweeps, n_ex = I.ctr->n_ex, n_prop = I.ctr->n_prop;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    __syncthreads();
+
+    if (a.mode & kModeEnergy) graph_energy(I, S);
+    if (a.mode & kModeSweeps) {
+        for (int k = 0; k < a.n; ++k) {
+            graph_sweep(I, S, k0, k1, (uint32_t)sweeps, a.update);
+            ++sweeps;
+        }
+        if (a.n > 0) graph_energy(I, S);
+    }
+    if (a.mode & kModePropose) {
+        ++n_prop;
+        if (with_pool) graph_propose(I, S, k0, k1, n_prop);
+        __syncthreads();
+    }
+    if (a.mode & kModeExchange) {
+        ++n_ex;
+        graph_exchange(I, S, k0, k1, n_ex);
+    }
+    if (a.mode & kModeCycles) {
+        for (int cyc = 0; cyc < a.n; ++cyc) {
+            for (int m = 0; m < a.M; ++m) {
+                graph_sweep(I, S, k0, k1, (uint32_t)sweeps, a.update);
+                ++sweeps;
+            }
+            graph_energy(I, S);
+            if (proposal_due(sweeps, a)) {
+                ++n_prop;
+                if (with_pool) graph_propose(I, S, k0, k1, n_prop);
+                __syncthreads();
+            }
+            ++n_ex;
+            graph_exchange(I, S, k0, k1, n_ex);
+        }
+    }
+
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(S.spins);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(I.spins);
+        for (int i = tid; i < N * R4 / 4; i += T) dst[i] = src[i];
+    }
+    for (int i = tid; i < R4; i += T) { I.E[i] = S.E[i]; I.sow[i] = S.sow[i]; }
+    for (int i = tid; i < R; i += T) I.wos[i] = S.wos[i];
+    for (int i = tid; i < 4 * R; i += T)
+        if (S.st[i]) I.stats[i] += S.st[i];
+    if (tid == 0) {
+        I.ctr->sweeps = sweeps;
+        I.ctr->n_ex = n_ex;
+        I.ctr->n_prop = n_prop;
+    }
+}
+
+// Random initial state: walker w's spin at a free site is bit (w & 31) of output word 0 of
+// Philox(site, 0, w >> 5, id); clamped sites take their clamp value.
+__global__ void graph_init_kernel(const GraphInst* __restrict__ insts, uint64_t seed) {
+    const GraphInst& I = insts[blockIdx.x];
+    const int8_t* cl = I.clamp;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int idx = threadIdx.x; idx < I.N * I.R4; idx += blockDim.x) {
+        const int i = idx / I.R4, w = idx - i * I.R4;
+        int8_t s = -1;
+        if (w < I.R) {
+            if (cl[i] != 0) {
+                s = cl[i];
+            } else {
+                const uint4 r = philox(make_uint4((uint32_t)i, 0u, (kDomInit << 24) | (uint32_t)(w >> 5),
+                                                  I.iid), k0, k1);
+                s = ((r.x >> (w & 31)) & 1u) ? 1 : -1;
+            }
+        }
+        I.spins[idx] = s;
+    }
+}
+
+__global__ void graph_capture_kernel(const GraphInst* __restrict__ dst,
+                                     const GraphInst* __restrict__ src, int entry) {
+    const GraphInst& D = dst[blockIdx.x];
+    const GraphInst& Sr = src[blockIdx.x];
+    const int N = Sr.N, NW = Sr.NW;
+    for (int idx = threadIdx.x; idx < Sr.R * NW; idx += blockDim.x) {
+        const int r = idx / NW, k = idx - r * NW;
+        const int w = Sr.wos[r];
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int i = k * 32 + b;
+            if (i < N && Sr.spins[i * Sr.R4 + w] > 0) word |= 1u << b;
+        }
+        const_cast<uint32_t*>(D.pool)[(size_t)entry * D.pstride + (size_t)r * NW + k] = word;
+    }
+}
+
+__global__ void graph_read_kernel(const GraphInst* __restrict__ insts, int inst, int8_t* out) {
+    const GraphInst& I = insts[inst];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
+         idx += gridDim.x * blockDim.x) {
+        const int r = idx / I.N, i = idx - r * I.N;
+        out[idx] = I.spins[i * I.R4 + I.wos[r]];
+    }
+}
+
+__global__ void graph_write_kernel(const GraphInst* __restrict__ insts, int inst,
+                                   const int8_t* in, const int32_t* walker) {
+    const GraphInst& I = insts[inst];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
+         idx += gridDim.x * blockDim.x) {
+        const int r = idx / I.N, i = idx - r * I.N;
+        I.spins[i * I.R4 + walker[r]] = in[idx];
+    }
+}
+
+cudaError_t launch_graph(const GraphInst* d_insts, int n, int threads, size_t smem,
+                         const RunArgs& a, int with_pool, cudaStream_t stream) {
+    cudaFuncSetAttribute(graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    graph_kernel<<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    return cudaGetLastError();
+}
+cudaError_t launch_graph_init(const GraphInst* d, int n, uint64_t seed, cudaStream_t s) {
+    graph_init_kernel<<<n, 256, 0, s>>>(d, seed);
+    return cudaGetLastError();
+}
+cudaError_t launch_graph_capture(const GraphInst* dst, const GraphInst* src, int n, int entry,
+                                 cudaStream_t s) {
+    graph_capture_kernel<<<n, 256, 0, s>>>(dst, src, entry);
+    return cudaGetLastError();
+}
+cudaError_t launch_graph_read(const GraphInst* d, int inst, int8_t* out, int total, cudaStream_t s) {
+    graph_read_kernel<<<(total + 255) / 256, 256, 0, s>>>(d, inst, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_graph_write(const GraphInst* d, int inst, const int8_t* in, const int32_t* walker,
+                               int total, cudaStream_t s) {
+    graph_write_kernel<<<(total + 255) / 256, 256, 0, s>>>(d, inst, in, walker);
+    return cudaGetLastError();
+}
+
+}  // namespace pt

@@ -1,0 +1,64 @@
+// Shared-memory layouts of the engines' kernels; used by the host to size the launch and by
+// the device to carve the buffer, so the two can never disagree.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define PT_HD __host__ __device__
+#else
+#define PT_HD
+#endif
+
+namespace pt {
+
+PT_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct LatLayout {
+    size_t tw, spins, sdesc, ebits, pbuf, E, Eacc, st, sow, wos, csites, total;
+};
+
+PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool) {
+    LatLayout l;
+    size_t o = 0;
+    l.tw = o;     o = align16(o + (size_t)W * 32 * 16);
+    l.spins = o;  o = align16(o + (size_t)W * N * 4);
+    l.sdesc = o;  o = align16(o + (size_t)N * 4);
+    l.ebits = o;  o = align16(o + (with_pool ? (size_t)6 * NW * 4 : 0));
+    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
+    l.E = o;      o = align16(o + (size_t)W * 32 * 4);
+    l.Eacc = o;   o = align16(o + (size_t)W * 32 * 4);
+    l.st = o;     o = align16(o + (size_t)4 * R * 4);
+    l.sow = o;    o = align16(o + (size_t)W * 32 * 2);
+    l.wos = o;    o = align16(o + (size_t)R * 2);
+    l.csites = o; o = align16(o + (size_t)N * 2);
+    l.total = o;
+    return l;
+}
+
+struct GraphLayout {
+    size_t spins, thr, rowp, adj, adjJ, h, csites, E, Eacc, st, sow, wos, pbuf, total;
+};
+
+PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
+                                      int nwarps, bool with_pool) {
+    GraphLayout l;
+    size_t o = 0;
+    l.spins = o;  o = align16(o + (size_t)N * R4);
+    l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
+    l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
+    l.adj = o;    o = align16(o + (size_t)2 * NE * 4);
+    l.adjJ = o;   o = align16(o + (size_t)2 * NE * 4);
+    l.h = o;      o = align16(o + (size_t)N * 4);
+    l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
+    l.E = o;      o = align16(o + (size_t)R4 * 4);
+    l.Eacc = o;   o = align16(o + (size_t)R4 * 4);
+    l.st = o;     o = align16(o + (size_t)4 * R * 4);
+    l.sow = o;    o = align16(o + (size_t)R4 * 2);
+    l.wos = o;    o = align16(o + (size_t)R * 2);
+    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
+    l.total = o;
+    return l;
+}
+
+}  // namespace pt
