@@ -53,8 +53,9 @@ def parse():
     p.add_argument("--R", type=int, default=32)
     p.add_argument("--sweeps-per-step", type=int, default=100)
     p.add_argument("--pool-size", type=int, default=1024)
-    p.add_argument("--pool-burnin", type=int, default=2000)
-    p.add_argument("--pool-gap", type=int, default=2)
+    # pools from a 10^6-sweep PT run per instance: 5e5 burn-in, then 1024 captures 488 apart
+    p.add_argument("--pool-burnin", type=int, default=500_000)
+    p.add_argument("--pool-gap", type=int, default=488)
     p.add_argument("--threads", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")

@@ -160,6 +160,14 @@ pt_status launch_run(pt_ctx* c, int mode, int nn) {
     a.start = c->cfg.propose_start;
     a.stop = c->cfg.propose_stop;
     a.update = c->cfg.update;
+    // Philox round keys: key bumped by the Weyl constants before each round after the first
+    uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        a.rk0[i] = k0;
+        a.rk1[i] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     cudaError_t e;
     if (c->engine == 0)
         e = launch_lattice(c->d_lat, c->n, c->maxW, c->threads, c->smem, a, c->with_pool, c->stream);
@@ -226,7 +234,7 @@ pt_status validate(const pt_instance_desc& d, int k) {
 pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    std::vector<size_t> o_spins(n), o_sdesc(n), o_cs(n), o_E(n), o_sow(n), o_wos(n), o_thr(n),
+    std::vector<size_t> o_spins(n), o_itab(n), o_pos(n), o_E(n), o_sow(n), o_wos(n), o_thr(n),
         o_beta(n), o_prop(n), o_cur(n), o_eb(n), o_ctr(n), o_st(n);
     c->lat.resize(n);
     size_t maxsmem = 0;
@@ -235,50 +243,65 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         const pt_instance_desc& d = descs[k];
         const int L = d.lattice_L, N = d.n_spins, R = d.n_replicas, W = (R + 31) / 32, NW = (N + 31) / 32;
         c->N[k] = N; c->R[k] = R; c->W[k] = W; c->NW[k] = NW; c->R4[k] = W * 32;
-        if (N > 65535) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 65535", k);
+        if (N > 8192) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 8192 (L <= 20)", k);
         LatInst& I = c->lat[k];
         memset(&I, 0, sizeof I);
         I.iid = d.instance_id; I.L = L; I.N = N; I.R = R; I.W = W; I.NW = NW;
         I.ncol = (L % 2 == 0) ? 2 : 3;
         I.P = c->cfg.pool_size;
-        // colour classes
+        // colour classes, and one table entry per site in colour order
         std::vector<int> col(N);
         for (int i = 0; i < N; ++i) col[i] = lattice_colour(i, L);
-        std::vector<uint16_t> cs;
-        cs.reserve(N);
+        std::vector<uint32_t> eb(6 * (size_t)NW, 0u);
+        std::vector<uint32_t> itab;
+        itab.reserve(4 * (size_t)N);
+        const int L2 = L * L;
+        // colour-major position of every site (the shared-memory order of the spins)
+        std::vector<uint16_t> pos(N);
+        {
+            int p = 0;
+            for (int cc = 0; cc < I.ncol; ++cc)
+                for (int i = 0; i < N; ++i)
+                    if (col[i] == cc) pos[i] = (uint16_t)p++;
+        }
         I.col_off[0] = 0;
+        int filled = 0;
         for (int cc = 0; cc < I.ncol; ++cc) {
-            for (int i = 0; i < N; ++i)
-                if (col[i] == cc) cs.push_back((uint16_t)i);
-            I.col_off[cc + 1] = (int)cs.size();
+            for (int i = 0; i < N; ++i) {
+                if (col[i] != cc) continue;
+                const int x = i % L, y = (i / L) % L, z = i / L2;
+                const int xm = (x + L - 1) % L, ym = (y + L - 1) % L, zm = (z + L - 1) % L;
+                const int nbr[6] = {(x + 1) % L + L * (y + L * z), xm + L * (y + L * z),
+                                    x + L * ((y + 1) % L + L * z), x + L * (ym + L * z),
+                                    x + L * (y + L * ((z + 1) % L)), x + L * (y + L * zm)};
+                // the +d bond of i is edge 3i+d; its -d bond is the +d bond of nbr[2d+1]
+                const int Jv[6] = {d.edge_J[3 * i + 0], d.edge_J[3 * nbr[1] + 0], d.edge_J[3 * i + 1],
+                                   d.edge_J[3 * nbr[3] + 1], d.edge_J[3 * i + 2], d.edge_J[3 * nbr[5] + 2]};
+                uint32_t flags = 0;
+                int nlow = 0;
+                uint32_t e16[6];
+                for (int dir = 0; dir < 6; ++dir) {
+                    if (col[nbr[dir]] < cc) { flags |= 1u << dir; ++nlow; }
+                    e16[dir] = (uint32_t)(4 * pos[nbr[dir]]) | (Jv[dir] < 0 ? 0x8000u : 0u);
+                }
+                if (nlow == 6) flags |= 64u;
+                itab.push_back((uint32_t)i | (flags << 16));
+                itab.push_back(e16[0] | (e16[1] << 16));
+                itab.push_back(e16[2] | (e16[3] << 16));
+                itab.push_back(e16[4] | (e16[5] << 16));
+                ++filled;
+            }
+            I.col_off[cc + 1] = filled;
             maxitems = std::max(maxitems, (I.col_off[cc + 1] - I.col_off[cc]) * W);
         }
-        for (int cc = I.ncol + 1; cc < 4; ++cc) I.col_off[cc] = (int)cs.size();
-        // site descriptors and bit strings of the bonds (for proposal energies)
-        std::vector<uint32_t> sdesc(N, 0u), eb(6 * (size_t)NW, 0u);
-        const int L2 = L * L;
+        for (int cc = I.ncol + 1; cc < 4; ++cc) I.col_off[cc] = filled;
+        // bit strings of the bonds (for proposal energies): negative +d bonds, wraps
         for (int i = 0; i < N; ++i) {
             const int x = i % L, y = (i / L) % L, z = i / L2;
-            const int xm = (x + L - 1) % L, ym = (y + L - 1) % L, zm = (z + L - 1) % L;
-            const int nbr[6] = {(x + 1) % L + L * (y + L * z), xm + L * (y + L * z),
-                                x + L * ((y + 1) % L + L * z), x + L * (ym + L * z),
-                                x + L * (y + L * ((z + 1) % L)), x + L * (y + L * zm)};
-            // bond owners: +d bond of i is edge 3i+d; -d bond of i is the +d bond of nbr[2d+1]
-            const int Jv[6] = {d.edge_J[3 * i + 0], d.edge_J[3 * nbr[1] + 0], d.edge_J[3 * i + 1],
-                               d.edge_J[3 * nbr[3] + 1], d.edge_J[3 * i + 2], d.edge_J[3 * nbr[5] + 2]};
-            const bool wrap[6] = {x == L - 1, x == 0, y == L - 1, y == 0, z == L - 1, z == 0};
-            uint32_t s = 0;
-            int nlow = 0;
-            for (int dir = 0; dir < 6; ++dir) {
-                if (Jv[dir] < 0) s |= 1u << dir;
-                if (wrap[dir]) s |= 1u << (8 + dir);
-                if (col[nbr[dir]] < col[i]) { s |= 1u << (16 + dir); ++nlow; }
-            }
-            if (nlow == 6) s |= 1u << 24;
-            sdesc[i] = s;
+            const bool wrap[3] = {x == L - 1, y == L - 1, z == L - 1};
             for (int dd = 0; dd < 3; ++dd) {
                 if (d.edge_J[3 * i + dd] < 0) eb[(size_t)dd * NW + (i >> 5)] |= 1u << (i & 31);
-                if (wrap[2 * dd]) eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
+                if (wrap[dd]) eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
             }
         }
         std::vector<uint32_t> thr(4 * (size_t)R, 0u);
@@ -293,8 +316,8 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         if (d.prop_enabled)
             for (int r = 0; r < R; ++r) prop[r] = d.prop_enabled[r] ? 1 : 0;
         o_spins[k] = A.zeros((size_t)W * N * 4);
-        o_sdesc[k] = A.add(sdesc.data(), sdesc.size() * 4);
-        o_cs[k] = A.add(cs.data(), cs.size() * 2);
+        o_itab[k] = A.add(itab.data(), itab.size() * 4);
+        o_pos[k] = A.add(pos.data(), pos.size() * 2);
         o_E[k] = A.zeros((size_t)W * 32 * 4);
         o_sow[k] = A.add(sow.data(), sow.size() * 2);
         o_wos[k] = A.add(wos.data(), wos.size() * 2);
@@ -310,10 +333,10 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         c->NWmax = std::max(c->NWmax, NW);
         c->maxW = std::max(c->maxW, W);
     }
-    // launch shape: about four words per thread per colour class, at most 42 (counter width)
+    // launch shape: about two words per thread per colour class, at most 42 (counter width)
     int T = c->cfg.threads_per_block;
     if (T <= 0) {
-        T = ((maxitems / 4 + 31) / 32) * 32;
+        T = ((maxitems / 2 + 31) / 32) * 32;
         T = std::max(64, std::min(512, T));
     }
     if (T % 32 != 0 || T < 32 || T > 512) return fail(PT_EINVAL, "lattice engine: threads_per_block must be a multiple of 32 in [32, 512]");
@@ -322,7 +345,12 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     c->threads = T;
     c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
     for (int k = 0; k < n; ++k) {
-        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0);
+        LatInst& I = c->lat[k];
+        int maxcol = 0;
+        for (int cc = 0; cc < I.ncol; ++cc) maxcol = std::max(maxcol, I.col_off[cc + 1] - I.col_off[cc]);
+        I.nit = (maxcol + T - 1) / T;
+        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32,
+                                           c->with_pool != 0);
         maxsmem = std::max(maxsmem, l.total);
     }
     int dev = 0, optin = 0;
@@ -344,8 +372,8 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     for (int k = 0; k < n; ++k) {
         LatInst& I = c->lat[k];
         I.spins = (uint32_t*)(b + o_spins[k]);
-        I.sdesc = (const uint32_t*)(b + o_sdesc[k]);
-        I.csites = (const uint16_t*)(b + o_cs[k]);
+        I.itab = (const uint4*)(b + o_itab[k]);
+        I.pos = (const uint16_t*)(b + o_pos[k]);
         I.E = (int32_t*)(b + o_E[k]);
         I.sow = (int16_t*)(b + o_sow[k]);
         I.wos = (int16_t*)(b + o_wos[k]);

@@ -25,10 +25,37 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 }
 
 // Global-move decision (Eq. P_swap and Eq. P_accept): accept with min[1, exp(x)] using a
-// 32-bit uniform u, i.e. iff x >= 0 or u + 1 <= 2^32 exp(x), in FP64.
+// 32-bit uniform u, i.e. iff x >= 0 or u + 1 <= 2^32 exp(x), decided as in FP64.
+// The FP64 exponential is only evaluated near a tie: a float evaluation is within a relative
+// 1.7e-6 of 2^32 exp(x) (|x| <= 22.2 rounded to float: 1.4e-6; expf within 2 ulp: 2.4e-7;
+// u + 1 and the margin products rounded: 2e-7), so outside a relative margin of 2^-16 the
+// float comparison already gives the FP64 decision.
 __device__ __forceinline__ bool accept_fp64(double x, uint32_t u) {
     if (x >= 0.0) return true;
+    if (x < -22.2) return false;                      // 2^32 exp(x) < 1 <= u + 1
+    const float y = expf((float)x) * 4294967296.0f;
+    const float a = (float)u + 1.0f;
+    if (a < y * (1.0f - 1.52587890625e-05f)) return true;
+    if (a > y * (1.0f + 1.52587890625e-05f)) return false;
     return ((double)u + 1.0) <= ldexp(exp(x), 32);
+}
+
+// The same decision for x = b * dE (b >= 0 an FP64 inverse-temperature difference or value,
+// dE an integer energy difference), the FP64 ratio of Eq. P_swap / Eq. P_accept. x >= 0 is
+// read off the signs; otherwise a float product of b and dE (relative error <= 3 * 2^-24 from
+// the FP64 product) feeds the float filter, and only near-ties evaluate the FP64 product and
+// exponential.
+__device__ __forceinline__ bool accept_ratio(double b, float bf, int dE, uint32_t u) {
+    if (dE >= 0 || b == 0.0) return true;             // x = b dE >= 0 (incl. -0.0)
+    const float xf = bf * (float)dE;
+    if (xf < -22.4f) return false;                    // x < -22.2: 2^32 exp(x) < 1 <= u + 1
+    if (xf != 0.0f && xf > -22.1f) {
+        const float y = expf(xf) * 4294967296.0f;
+        const float a = (float)u + 1.0f;
+        if (a < y * (1.0f - 1.52587890625e-05f)) return true;
+        if (a > y * (1.0f + 1.52587890625e-05f)) return false;
+    }
+    return accept_fp64(b * (double)dE, u);
 }
 
 // bitwise select: bits of a where m is 1, of b where m is 0
@@ -81,12 +108,19 @@ struct Counters {
 struct LatInst {
     uint32_t iid;
     int32_t L, N, R, W, NW, ncol, P;
+    int32_t nit;           // words per thread per colour class at the launch's block size
     int32_t col_off[4];
-    uint32_t* spins;       // [W][N]
-    const uint32_t* sdesc; // [N]: bits 0-5 bond negative (+x,-x,+y,-y,+z,-z),
-                           //      8-13 wrap in that direction, 16-21 neighbour has a lower
-                           //      colour, 24 all six neighbours lower
-    const uint16_t* csites;// [N] sites in colour order
+    uint32_t* spins;       // [W][N] in site order
+    const uint4* itab;     // [N] one entry per site, in colour order (item k of colour c is
+                           // itab[col_off[c] + k]); in shared memory the spins are stored in
+                           // this colour-major order (item k of colour c at col_off[c] + k).
+                           // Eight 16-bit fields:
+                           //   x.lo  site index
+                           //   x.hi  bits 0-5: neighbour d has a lower colour; bit 6: all six
+                           //   y,z,w six neighbours (+x,-x,+y,-y,+z,-z): bits 0-14 byte offset
+                           //         of the neighbour's word in colour-major order, bit 15 set
+                           //         iff the bond is -1
+    const uint16_t* pos;   // [N] colour-major position of each site
     int32_t* E;            // [W*32] per walker
     int16_t* sow;          // [W*32] slot of walker (-1: padding lane)
     int16_t* wos;          // [R] walker of slot
@@ -146,7 +180,20 @@ struct RunArgs {
     int32_t M, every, start, stop;
     int32_t update;      // graph engine: 0 Metropolis, 1 Gibbs
     int32_t pad;
+    uint32_t rk0[10];    // Philox round keys of the seed (kernel parameters, so the rounds
+    uint32_t rk1[10];    // read them as constant operands)
 };
+
+// Philox4x32-10 with precomputed round keys.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RunArgs& a) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ a.rk0[i], lo1, hi0 ^ c.w ^ a.rk1[i], lo0);
+    }
+    return c;
+}
 
 __device__ __forceinline__ bool proposal_due(long long s, const RunArgs& a) {
     if (a.every <= 0 || s < a.start) return false;

@@ -53,7 +53,7 @@ __device__ __forceinline__ int sbyte(uint32_t w, int k) {
 }
 
 // One sweep: every free site of every colour class, four walkers per thread.
-__device__ void graph_sweep(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
+__device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                             uint32_t sweep_idx, int update) {
     const int Q = I.R4 >> 2;
     const int tw = 2 * I.Imax + 1;
@@ -76,8 +76,8 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, uint32_t k0, uint3
                 f3 += J * sbyte(wd, 3);
             }
             const uint32_t own = sp[site * Q + quad];
-            const uint4 r = philox(make_uint4((uint32_t)site, sweep_idx,
-                                              (kDomWord << 24) | (uint32_t)quad, I.iid), k0, k1);
+            const uint4 r = philox_rk(make_uint4((uint32_t)site, sweep_idx,
+                                                 (kDomWord << 24) | (uint32_t)quad, I.iid), a);
             const int f[4] = {f0, f1, f2, f3};
             const uint32_t u[4] = {r.x, r.y, r.z, r.w};
             uint32_t out = own;
@@ -135,12 +135,12 @@ __device__ void graph_exchange(const GraphInst& I, GraphSmem& S, uint32_t k0, ui
         for (int r = first + 2 * lane; r + 1 < I.R; r += 64) {
             const int wa = S.wos[r], wc = S.wos[r + 1];
             const int dE = S.E[wc] - S.E[wa];
-            const double x = (I.beta[r + 1] - I.beta[r]) * (double)dE;
-            bool acc = x >= 0.0;
+            const double db = I.beta[r + 1] - I.beta[r];
+            bool acc = dE >= 0 || db == 0.0;
             if (!acc) {
                 const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_ex, kDomExch << 24, I.iid),
                                        k0, k1);
-                acc = accept_fp64(x, q.x);
+                acc = accept_ratio(db, (float)db, dE, q.x);
             }
             S.st[I.R + r] += 1u;
             if (acc) {
@@ -179,12 +179,12 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
         const int ET = __reduce_add_sync(kFull, e);
         int acc = 0;
         if (lane == 0) {
-            const double x = I.beta[r] * (double)(S.E[w] - ET);
-            acc = x >= 0.0;
+            const int dE = S.E[w] - ET;
+            acc = dE >= 0 || I.beta[r] == 0.0;
             if (!acc) {
                 const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid),
                                        k0, k1);
-                acc = accept_fp64(x, q.x);
+                acc = accept_ratio(I.beta[r], (float)I.beta[r], dE, q.x);
             }
         }
         acc = __shfl_sync(kFull, acc, 0);
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeEnergy) graph_energy(I, S);
     if (a.mode & kModeSweeps) {
         for (int k = 0; k < a.n; ++k) {
-            graph_sweep(I, S, k0, k1, (uint32_t)sweeps, a.update);
+            graph_sweep(I, S, a, (uint32_t)sweeps, a.update);
             ++sweeps;
         }
         if (a.n > 0) graph_energy(I, S);
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
             for (int m = 0; m < a.M; ++m) {
-                graph_sweep(I, S, k0, k1, (uint32_t)sweeps, a.update);
+                graph_sweep(I, S, a, (uint32_t)sweeps, a.update);
                 ++sweeps;
             }
             graph_energy(I, S);

@@ -20,6 +20,11 @@
 // bonds to lower-colour neighbours right after its update (its lower neighbours are final).
 // Counts are kept as bit-sliced vertical counters and reduced across each warp by bit
 // transposes and popcounts.
+//
+// Per cycle the block synchronises four times: after each colour class, after the energy
+// counts, and after the bit-sliced thresholds are rebuilt. Every warp evaluates the exchange
+// decisions itself (they are deterministic) so that it can rebuild its share of the
+// threshold planes without waiting; warp 0 alone commits the new labels.
 #include "pt_device.cuh"
 #include "pt_layout.h"
 
@@ -27,59 +32,86 @@ namespace pt {
 
 constexpr int KB = 8;  // vertical counter bits: up to 255 bond counts per thread per word
 
+// Scalars of the instance held in registers for the whole launch.
+struct LP {
+    uint32_t iid;
+    int L, N, R, W, NW, ncol;
+    int cb[4];    // colour class c occupies positions cb[c] .. cb[c+1]-1
+};
+
+__device__ __forceinline__ LP load_lp(const LatInst& I) {
+    LP p;
+    p.iid = I.iid; p.L = I.L; p.N = I.N; p.R = I.R; p.W = I.W; p.NW = I.NW; p.ncol = I.ncol;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p.cb[c] = I.col_off[c];
+    return p;
+}
+
 struct LatSmem {
-    uint4* tw;
-    uint32_t* spins;
-    uint32_t* sdesc;
-    uint32_t* ebits;
-    uint32_t* pbuf;
-    int32_t* E;
-    int32_t* Eacc;
-    uint32_t* st;      // [4][R] statistics of this launch
-    int16_t* sow;
-    int16_t* wos;
-    uint16_t* csites;
+    uint4* tw;         // [W*32] bit-sliced thresholds {T4, T8, T12} per plane
+    uint32_t* spins;   // [W*N]
+    uint4* itab;       // [N]
+    double* beta;      // [R]
+    double* dbeta;     // [R] beta[r+1] - beta[r] in FP64 (0 for the last slot)
+    float* fbeta;      // [R] (float) beta[r]
+    float* fdbeta;     // [R] (float) dbeta[r]
+    uint4* thr;        // [R] {T(4), T(8), T(12), 0}
+    uint8_t* prop;     // [R]
+    uint32_t* ebits;   // [6*NW]   (with pool)
+    uint32_t* stage;   // [R*NW]   proposal staging (with pool)
+    int32_t* us;       // [R]      unsatisfied-bond counts of the staged proposals
+    int32_t* cursor;   // [R]
+    int16_t* accr;     // [W*32]   slot whose proposal the walker accepted, -1 none
+    int32_t* E;        // [W*32]
+    int32_t* Eacc;     // [2][W*32] double-buffered bond counts
+    uint32_t* st;      // [4][R]   statistics of this launch
+    int16_t* sow;      // [2][W*32] slot of walker, double-buffered
+    int16_t* wos;      // [2][W*32] walker of slot, double-buffered
+    int16_t* wsow;     // [nwarps][W*32] each warp's view of the new slot of walker
 };
 
 __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I, int nwarps,
                                                  bool with_pool) {
-    LatLayout lay = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool);
+    const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool);
     LatSmem S;
-    S.tw = reinterpret_cast<uint4*>(base + lay.tw);
-    S.spins = reinterpret_cast<uint32_t*>(base + lay.spins);
-    S.sdesc = reinterpret_cast<uint32_t*>(base + lay.sdesc);
-    S.ebits = reinterpret_cast<uint32_t*>(base + lay.ebits);
-    S.pbuf = reinterpret_cast<uint32_t*>(base + lay.pbuf);
-    S.E = reinterpret_cast<int32_t*>(base + lay.E);
-    S.Eacc = reinterpret_cast<int32_t*>(base + lay.Eacc);
-    S.st = reinterpret_cast<uint32_t*>(base + lay.st);
-    S.sow = reinterpret_cast<int16_t*>(base + lay.sow);
-    S.wos = reinterpret_cast<int16_t*>(base + lay.wos);
-    S.csites = reinterpret_cast<uint16_t*>(base + lay.csites);
+    S.tw = reinterpret_cast<uint4*>(base + l.tw);
+    S.spins = reinterpret_cast<uint32_t*>(base + l.spins);
+    S.itab = reinterpret_cast<uint4*>(base + l.itab);
+    S.beta = reinterpret_cast<double*>(base + l.beta);
+    S.dbeta = reinterpret_cast<double*>(base + l.dbeta);
+    S.fbeta = reinterpret_cast<float*>(base + l.fbeta);
+    S.fdbeta = reinterpret_cast<float*>(base + l.fdbeta);
+    S.thr = reinterpret_cast<uint4*>(base + l.thr);
+    S.prop = reinterpret_cast<uint8_t*>(base + l.prop);
+    S.ebits = reinterpret_cast<uint32_t*>(base + l.ebits);
+    S.stage = reinterpret_cast<uint32_t*>(base + l.stage);
+    S.us = reinterpret_cast<int32_t*>(base + l.us);
+    S.cursor = reinterpret_cast<int32_t*>(base + l.cursor);
+    S.accr = reinterpret_cast<int16_t*>(base + l.accr);
+    S.E = reinterpret_cast<int32_t*>(base + l.E);
+    S.Eacc = reinterpret_cast<int32_t*>(base + l.Eacc);
+    S.st = reinterpret_cast<uint32_t*>(base + l.st);
+    S.sow = reinterpret_cast<int16_t*>(base + l.sow);
+    S.wos = reinterpret_cast<int16_t*>(base + l.wos);
+    S.wsow = reinterpret_cast<int16_t*>(base + l.wsow);
     return S;
 }
 
-// Bit-sliced thresholds of walker block wb: tw[wb*32 + k] = {plane k of T(dE=4), of T(dE=8),
-// of T(dE=12)}, lane b taking the thresholds of the slot walker 32 wb + b currently holds.
-__device__ void rebuild_thresholds(const LatInst& I, LatSmem& S) {
+// Bit-sliced thresholds of every walker block from a slot-of-walker map:
+// tw[wb*32 + k] = {plane k of T(dE=4), of T(dE=8), of T(dE=12)} with lane b taking the
+// thresholds of the slot of walker 32 wb + b. This warp writes planes warp, warp+nwarps, ...
+__device__ __forceinline__ void rebuild_planes(const LP& P, LatSmem& S, const int16_t* sow) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int wb = warp; wb < I.W; wb += nwarps) {
+    for (int wb = 0; wb < P.W; ++wb) {
         const int w = wb * 32 + lane;
-        const int slot = (w < I.R) ? S.sow[w] : -1;
-        uint32_t t4 = 0, t8 = 0, t12 = 0;
-        if (slot >= 0) {
-            const uint4 t = reinterpret_cast<const uint4*>(I.thr)[slot];
-            t4 = t.x; t8 = t.y; t12 = t.z;
+        const int slot = (w < P.R) ? sow[w] : -1;
+        const uint4 t = slot >= 0 ? S.thr[slot] : make_uint4(0u, 0u, 0u, 0u);
+        for (int k = warp; k < 32; k += nwarps) {
+            const uint32_t bx = __ballot_sync(kFull, (t.x >> (31 - k)) & 1u);
+            const uint32_t by = __ballot_sync(kFull, (t.y >> (31 - k)) & 1u);
+            const uint32_t bz = __ballot_sync(kFull, (t.z >> (31 - k)) & 1u);
+            if (lane == 0) S.tw[wb * 32 + k] = make_uint4(bx, by, bz, 0u);
         }
-        uint4 mine = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll 4
-        for (int k = 0; k < 32; ++k) {
-            const uint32_t bx = __ballot_sync(kFull, (t4 >> (31 - k)) & 1u);
-            const uint32_t by = __ballot_sync(kFull, (t8 >> (31 - k)) & 1u);
-            const uint32_t bz = __ballot_sync(kFull, (t12 >> (31 - k)) & 1u);
-            if (lane == k) mine = make_uint4(bx, by, bz, 0u);
-        }
-        S.tw[wb * 32 + lane] = mine;
     }
 }
 
@@ -101,95 +133,132 @@ __device__ __forceinline__ void vc_add3(uint32_t (&c)[KB], uint32_t n0, uint32_t
     }
 }
 
+// Compare four bit planes of u (one Philox output) with the class-selected thresholds.
+__device__ __forceinline__ void compare4(const uint4& r, const uint4* tw, uint32_t b0, uint32_t b1,
+                                         uint32_t& und, uint32_t& lt) {
+    const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint4 tt = tw[j];
+        // count 0 -> T(dE=12), 1 -> T(8), 2 -> T(4)
+        const uint32_t tk = mux(b1, tt.x, mux(b0, tt.y, tt.z));
+        lt |= und & ~rw[j] & tk;
+        und &= ~(rw[j] ^ tk);
+    }
+}
+
+__device__ __forceinline__ uint32_t nb_word(const uint8_t* base, uint32_t e16) {
+    return *reinterpret_cast<const uint32_t*>(base + (e16 & 0x7FFFu));
+}
+__device__ __forceinline__ uint32_t nb_sign(uint32_t e16) {
+    return 0u - ((e16 >> 15) & 1u);
+}
+
+// The six "bond unsatisfied" words s ^ n_d ^ Jneg_d of a table entry.
+__device__ __forceinline__ void bond_words(const uint8_t* sp, const uint4& it, uint32_t s,
+                                           uint32_t (&u)[6]) {
+    u[0] = s ^ nb_word(sp, it.y) ^ nb_sign(it.y);
+    u[1] = s ^ nb_word(sp, it.y >> 16) ^ nb_sign(it.y >> 16);
+    u[2] = s ^ nb_word(sp, it.z) ^ nb_sign(it.z);
+    u[3] = s ^ nb_word(sp, it.z >> 16) ^ nb_sign(it.z >> 16);
+    u[4] = s ^ nb_word(sp, it.w) ^ nb_sign(it.w);
+    u[5] = s ^ nb_word(sp, it.w >> 16) ^ nb_sign(it.w >> 16);
+}
+
+// Energy bookkeeping of one updated word: add its new count of unsatisfied bonds to
+// lower-colour neighbours to the thread's vertical counter.
+__device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t flags,
+                                                  const uint32_t (&u)[6], uint32_t b0,
+                                                  uint32_t b1, uint32_t b2, uint32_t flip) {
+    uint32_t n0, n1, n2;
+    if (flags & 64u) {
+        // all six neighbours are lower: the new count is 6 - c where flipped
+        n0 = b0;
+        n1 = b1 ^ (flip & ~b0);
+        n2 = b2 ^ (flip & ~(b1 & b0));
+    } else {
+        uint32_t v[6];
+#pragma unroll
+        for (int dir = 0; dir < 6; ++dir)
+            v[dir] = (u[dir] ^ flip) & (0u - ((flags >> dir) & 1u));
+        const uint32_t e1 = v[0] ^ v[1] ^ v[2], f1 = maj3(v[0], v[1], v[2]);
+        const uint32_t e2 = v[3] ^ v[4] ^ v[5], f2 = maj3(v[3], v[4], v[5]);
+        n0 = e1 ^ e2;
+        const uint32_t g = e1 & e2;
+        n1 = f1 ^ f2 ^ g;
+        n2 = maj3(f1, f2, g);
+    }
+    vc_add3(cnt, n0, n1, n2);
+}
+
 // One sweep: colour classes in order, all (site, walker-block) words of a class in parallel.
 template <int MAXW>
-__device__ __forceinline__ void lattice_sweep(const LatInst& I, LatSmem& S, uint32_t k0,
-                                              uint32_t k1, uint32_t sweep_idx, bool flip_on,
-                                              bool energy_on, uint32_t (&cnt)[MAXW][KB],
-                                              const int (&off)[12]) {
+__device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const RunArgs& a,
+                                              uint32_t sweep_idx, bool flip_on, bool energy_on,
+                                              uint32_t (&cnt)[MAXW][KB]) {
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int c = 0; c < I.ncol; ++c) {
-        const int base = I.col_off[c];
-        const int nc = I.col_off[c + 1] - base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c >= P.ncol) break;
+        const int base = P.cb[c];
+        const int nc = P.cb[c + 1] - base;
         const bool acc = energy_on && c > 0;
 #pragma unroll
         for (int wb = 0; wb < MAXW; ++wb) {
-            if (wb >= I.W) break;
-            uint32_t* sp = S.spins + wb * I.N;
-            const int rem = I.R - wb * 32;
+            if (wb >= P.W) break;
+            uint8_t* sp = reinterpret_cast<uint8_t*>(S.spins + wb * P.N);
+            uint32_t* own_p = S.spins + wb * P.N + base;
+            const int rem = P.R - wb * 32;
             const uint32_t vmask = rem >= 32 ? kFull : ((1u << rem) - 1u);
             const uint32_t ctr2 = (kDomPlane << 24) | (uint32_t)wb;
             const uint4* tw = S.tw + wb * 32;
             for (int k = tid; k < nc; k += T) {
-                const int site = S.csites[base + k];
-                const uint32_t d = S.sdesc[site];
-                const uint32_t s = sp[site];
+                const uint4 it = S.itab[base + k];
+                const uint32_t s = own_p[k];
                 uint32_t u[6];
-#pragma unroll
-                for (int dir = 0; dir < 6; ++dir) {
-                    const int nb = site + (((d >> (8 + dir)) & 1u) ? off[6 + dir] : off[dir]);
-                    u[dir] = s ^ sp[nb] ^ (0u - ((d >> dir) & 1u));
-                }
+                bond_words(sp, it, s, u);
                 const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
                 const uint32_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
                 const uint32_t b0 = s1 ^ s2, t = s1 & s2;
                 const uint32_t b1 = c1 ^ c2 ^ t, b2 = maj3(c1, c2, t);
                 uint32_t flip = 0;
                 if (flip_on) {
-                    const uint32_t always = b2 | (b1 & b0);   // c >= 3: dE <= 0
+                    const uint32_t always = b2 | (b1 & b0);   // count >= 3: dE <= 0
                     uint32_t und = ~always & vmask, lt = 0;
-                    for (int qb = 0; qb < 8 && und; ++qb) {
-                        const uint4 r = philox(
-                            make_uint4((uint32_t)site, sweep_idx, ctr2 | ((uint32_t)qb << 16), I.iid),
-                            k0, k1);
-                        const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint4 tt = tw[qb * 4 + j];
-                            // c = 0 -> T(12), 1 -> T(8), 2 -> T(4)
-                            const uint32_t tk = mux(b1, tt.x, mux(b0, tt.y, tt.z));
-                            lt |= und & ~rw[j] & tk;
-                            und &= ~(rw[j] ^ tk);
+                    if (und) {
+                        // plane blocks 0-2 are almost always needed by some walker of the
+                        // warp: draw them together (three independent Philox chains)
+                        const uint32_t site = it.x & 0xFFFFu;
+                        const uint4 r0 = philox_rk(make_uint4(site, sweep_idx, ctr2, P.iid), a);
+                        const uint4 r1 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (1u << 16), P.iid), a);
+                        const uint4 r2 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (2u << 16), P.iid), a);
+                        compare4(r0, tw, b0, b1, und, lt);
+                        compare4(r1, tw + 4, b0, b1, und, lt);
+                        compare4(r2, tw + 8, b0, b1, und, lt);
+                        for (uint32_t qb = 3; qb < 8 && und; ++qb) {
+                            const uint4 r = philox_rk(make_uint4(site, sweep_idx, ctr2 | (qb << 16), P.iid), a);
+                            compare4(r, tw + 4 * qb, b0, b1, und, lt);
                         }
                     }
                     flip = (always | lt) & vmask;
-                    if (flip) sp[site] = s ^ flip;
+                    if (flip) own_p[k] = s ^ flip;
                 }
-                if (acc) {
-                    uint32_t n0, n1, n2;
-                    if (d & (1u << 24)) {
-                        // all six neighbours are lower: the new count is 6 - c where flipped
-                        n0 = b0;
-                        n1 = b1 ^ (flip & ~b0);
-                        n2 = b2 ^ (flip & ~(b1 & b0));
-                    } else {
-                        uint32_t v[6];
-#pragma unroll
-                        for (int dir = 0; dir < 6; ++dir)
-                            v[dir] = (u[dir] ^ flip) & (0u - ((d >> (16 + dir)) & 1u));
-                        const uint32_t e1 = v[0] ^ v[1] ^ v[2], f1 = maj3(v[0], v[1], v[2]);
-                        const uint32_t e2 = v[3] ^ v[4] ^ v[5], f2 = maj3(v[3], v[4], v[5]);
-                        n0 = e1 ^ e2;
-                        const uint32_t g = e1 & e2;
-                        n1 = f1 ^ f2 ^ g;
-                        n2 = maj3(f1, f2, g);
-                    }
-                    vc_add3(cnt[wb], n0, n1, n2);
-                }
+                if (acc) count_lower_bonds(cnt[wb], it.x >> 16, u, b0, b1, b2, flip);
             }
         }
         __syncthreads();
     }
 }
 
-// Reduce the vertical counters to per-walker energies E = 2U - 3N.
+// Reduce the vertical counters into the bond counts Eacc[p] (per walker); ends synchronised.
 template <int MAXW>
-__device__ __forceinline__ void lattice_energy_finalize(const LatInst& I, LatSmem& S,
-                                                        uint32_t (&cnt)[MAXW][KB]) {
+__device__ __forceinline__ void lattice_count_reduce(const LP& P, LatSmem& S,
+                                                     uint32_t (&cnt)[MAXW][KB], int p) {
     const int lane = threadIdx.x & 31;
+    int32_t* acc_out = S.Eacc + p * P.W * 32;
 #pragma unroll
     for (int wb = 0; wb < MAXW; ++wb) {
-        if (wb >= I.W) break;
+        if (wb >= P.W) break;
         uint32_t acc = 0;
 #pragma unroll
         for (int j = 0; j < KB; ++j) {
@@ -199,135 +268,186 @@ __device__ __forceinline__ void lattice_energy_finalize(const LatInst& I, LatSme
             }
             cnt[wb][j] = 0u;
         }
-        if (acc) atomicAdd(&S.Eacc[wb * 32 + lane], (int)acc);
-    }
-    __syncthreads();
-    for (int w = threadIdx.x; w < I.W * 32; w += blockDim.x) {
-        S.E[w] = 2 * S.Eacc[w] - 3 * I.N;
-        S.Eacc[w] = 0;
+        if (acc) atomicAdd(&acc_out[wb * 32 + lane], (int)acc);
     }
     __syncthreads();
 }
 
-// One exchange event (Eq. P_swap). Returns (block-uniformly) whether any pair swapped.
-__device__ bool lattice_exchange(const LatInst& I, LatSmem& S, uint32_t k0, uint32_t k1,
-                                 long long n_ex, int* flag) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+// E[w] = 2U - 3N from the counts of buffer p; zero the other buffer for the next cycle.
+__device__ __forceinline__ void lattice_store_energies(const LP& P, LatSmem& S, int p) {
+    for (int w = threadIdx.x; w < P.W * 32; w += blockDim.x) {
+        S.E[w] = 2 * S.Eacc[p * P.W * 32 + w] - 3 * P.N;
+        S.Eacc[(p ^ 1) * P.W * 32 + w] = 0;
+    }
+}
+
+// One exchange event (Eq. P_swap) on the labels of buffer q with energies E = 2 Ecount - 3N
+// (Ecount != nullptr) or S.E: warp 0 decides every pair and writes the new labels to buffer
+// q^1 and the statistics; then every warp rebuilds its share of the threshold planes from
+// the new slot-of-walker map. The caller synchronises afterwards.
+__device__ void lattice_exchange(const LP& P, LatSmem& S, const RunArgs& a, long long n_ex,
+                                 int q, const int32_t* Ecount) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = P.R, WR = P.W * 32;
+    int16_t* wos_n = S.wos + (q ^ 1) * WR;
+    int16_t* sow_n = S.sow + (q ^ 1) * WR;
+    if (warp == 0) {
+        const int16_t* wos = S.wos + q * WR;
+        const int16_t* sow = S.sow + q * WR;
+        for (int r = lane; r < R; r += 32) wos_n[r] = wos[r];
+        for (int w = lane; w < WR; w += 32) sow_n[w] = sow[w];
+        __syncwarp();
         const int first = (n_ex & 1) ? 0 : 1;
-        bool any = false;
-        for (int r = first + 2 * lane; r + 1 < I.R; r += 64) {
-            const int wa = S.wos[r], wc = S.wos[r + 1];
-            const int dE = S.E[wc] - S.E[wa];
-            const double x = (I.beta[r + 1] - I.beta[r]) * (double)dE;
-            bool acc = x >= 0.0;
+        for (int r = first + 2 * lane; r + 1 < R; r += 64) {
+            const int wa = wos[r], wc = wos[r + 1];
+            const int ea = Ecount ? 2 * Ecount[wa] - 3 * P.N : S.E[wa];
+            const int ec = Ecount ? 2 * Ecount[wc] - 3 * P.N : S.E[wc];
+            const int dE = ec - ea;
+            bool acc = dE >= 0 || S.dbeta[r] == 0.0;
             if (!acc) {
-                const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_ex, kDomExch << 24, I.iid),
-                                       k0, k1);
-                acc = accept_fp64(x, q.x);
+                const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_ex, kDomExch << 24, P.iid), a);
+                acc = accept_ratio(S.dbeta[r], S.fdbeta[r], dE, u.x);
             }
-            S.st[I.R + r] += 1u;
+            S.st[R + r] += 1u;
             if (acc) {
-                S.wos[r] = (int16_t)wc;
-                S.wos[r + 1] = (int16_t)wa;
-                S.sow[wa] = (int16_t)(r + 1);
-                S.sow[wc] = (int16_t)r;
                 S.st[r] += 1u;
-                any = true;
+                wos_n[r] = (int16_t)wc;
+                wos_n[r + 1] = (int16_t)wa;
+                sow_n[wa] = (int16_t)(r + 1);
+                sow_n[wc] = (int16_t)r;
             }
         }
-        any = __any_sync(kFull, any);
-        if (lane == 0) *flag = any ? 1 : 0;
     }
     __syncthreads();
-    return *flag != 0;
+    rebuild_planes(P, S, sow_n);
 }
 
-// One proposal event (Algorithm 1, Eq. P_accept), one warp per proposal-enabled slot.
-__device__ void lattice_propose(const LatInst& I, LatSmem& S, uint32_t k0, uint32_t k1,
-                                long long n_prop) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int L = I.L, N = I.N, NW = I.NW;
-    uint32_t* buf = S.pbuf + warp * NW;
-    const int st[3] = {1, L, L * L};
-    for (int r = warp; r < I.R; r += nwarps) {
-        if (!I.prop[r]) continue;
-        const int w = S.wos[r];
-        const int c = I.cursor[r];
-        const uint32_t* entry = I.pool + (size_t)c * I.pstride + (size_t)r * NW;
-        for (int k = lane; k < NW; k += 32) buf[k] = __ldg(entry + k);
-        __syncwarp();
-        int U = 0;
-        for (int k = lane; k < NW; k += 32) {
-            const uint32_t vk = (k < NW - 1 || (N & 31) == 0) ? kFull : ((1u << (N & 31)) - 1u);
-            const uint32_t sk = buf[k];
-#pragma unroll
-            for (int dd = 0; dd < 3; ++dd) {
-                const uint32_t Wd = S.ebits[(3 + dd) * NW + k];
-                const uint32_t A = bits_at(buf, NW, 32 * k + st[dd]);
-                const uint32_t B = Wd ? bits_at(buf, NW, 32 * k + st[dd] - L * st[dd]) : 0u;
-                const uint32_t nb = (A & ~Wd) | (B & Wd);
-                U += __popc((sk ^ nb ^ S.ebits[dd * NW + k]) & vk);
-            }
-        }
-        U = __reduce_add_sync(kFull, U);
-        const int ET = 2 * U - 3 * N;
-        int acc = 0;
-        if (lane == 0) {
-            const double x = I.beta[r] * (double)(S.E[w] - ET);
-            acc = x >= 0.0;
-            if (!acc) {
-                const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid),
-                                       k0, k1);
-                acc = accept_fp64(x, q.x);
-            }
-        }
-        acc = __shfl_sync(kFull, acc, 0);
-        if (acc) {
-            uint32_t* sp = S.spins + (w >> 5) * N;
-            const uint32_t bit = 1u << (w & 31);
-            for (int i = lane; i < N; i += 32) {
-                const uint32_t want = (buf[i >> 5] >> (i & 31)) & 1u;
-                const uint32_t cur = (sp[i] & bit) ? 1u : 0u;  // only this warp owns this bit
-                if (want != cur) atomicXor(&sp[i], bit);
-            }
-        }
-        if (lane == 0) {
-            if (acc) S.E[w] = ET;
-            I.cursor[r] = (c + 1) % I.P;
-            S.st[3 * I.R + r] += 1u;
-            if (acc) S.st[2 * I.R + r] += 1u;
-        }
-        __syncwarp();
+// One proposal event (Algorithm 1, Eq. P_accept) with energies in S.E and labels of buffer q.
+// A: stage the next pool entry of every proposal-enabled slot; B: count its unsatisfied
+// bonds (funnel shifts along x, y, z with the wrap masks; E^T = 2U - 3N); C: one thread per
+// slot decides in FP64 and advances the cursor; D: merge accepted entries into their walkers'
+// lanes 32 sites at a time by a warp bit transpose. Ends synchronised.
+__device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
+                                long long n_prop, int q) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = T >> 5;
+    const int L = I.L, N = I.N, NW = I.NW, R = I.R, WR = I.W * 32;
+    const int16_t* wos = S.wos + q * WR;
+    for (int idx = tid; idx < R * NW; idx += T) {
+        const int r = idx / NW, k = idx - r * NW;
+        if (S.prop[r])
+            S.stage[idx] = __ldg(I.pool + (size_t)S.cursor[r] * I.pstride + (size_t)r * NW + k);
     }
+    for (int r = tid; r < R; r += T) S.us[r] = 0;
+    for (int w = tid; w < WR; w += T) S.accr[w] = -1;
+    __syncthreads();
+    const int st[3] = {1, L, L * L};
+    const int total = R * NW;
+    for (int base = warp * 32; base < total; base += T) {
+        const int idx = base + lane;
+        int r = -1, cnt = 0;
+        if (idx < total) {
+            r = idx / NW;
+            const int k = idx - r * NW;
+            if (S.prop[r]) {
+                const uint32_t* sb = S.stage + r * NW;
+                const uint32_t vk = (k < NW - 1 || (N & 31) == 0) ? kFull : ((1u << (N & 31)) - 1u);
+                const uint32_t sk = sb[k];
+#pragma unroll
+                for (int dd = 0; dd < 3; ++dd) {
+                    const uint32_t Wd = S.ebits[(3 + dd) * NW + k];
+                    const uint32_t A = bits_at(sb, NW, 32 * k + st[dd]);
+                    const uint32_t B = Wd ? bits_at(sb, NW, 32 * k + st[dd] - L * st[dd]) : 0u;
+                    const uint32_t nb = (A & ~Wd) | (B & Wd);
+                    cnt += __popc((sk ^ nb ^ S.ebits[dd * NW + k]) & vk);
+                }
+            }
+        }
+        const uint32_t m = __match_any_sync(kFull, r);
+        const int v = __reduce_add_sync(m, cnt);
+        if (r >= 0 && lane == __ffs(m) - 1 && v) atomicAdd(&S.us[r], v);
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += T) {
+        if (!S.prop[r]) continue;
+        const int w = wos[r];
+        const int ET = 2 * S.us[r] - 3 * N;
+        const int dE = S.E[w] - ET;                   // x = beta_r (E_r - E^T)
+        bool acc = dE >= 0 || S.beta[r] == 0.0;
+        if (!acc) {
+            const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid), a);
+            acc = accept_ratio(S.beta[r], S.fbeta[r], dE, u.x);
+        }
+        if (acc) {
+            S.E[w] = ET;
+            S.accr[w] = (int16_t)r;
+            S.st[2 * R + r] += 1u;
+        }
+        S.cursor[r] = (S.cursor[r] + 1) % I.P;
+        S.st[3 * R + r] += 1u;
+    }
+    __syncthreads();
+    for (int wb = 0; wb < I.W; ++wb) {
+        const int w = wb * 32 + lane;
+        const int r = (w < R) ? S.accr[w] : -1;
+        const uint32_t am = __ballot_sync(kFull, r >= 0);
+        if (!am) continue;
+        uint32_t* sp = S.spins + wb * N;
+        for (int g = warp; g < NW; g += nwarps) {
+            const uint32_t row = r >= 0 ? S.stage[r * NW + g] : 0u;
+            const uint32_t col = warp_transpose32(row, lane);
+            const int site = 32 * g + lane;
+            if (site < N) {
+                const int ps = I.pos[site];
+                sp[ps] = (col & am) | (sp[ps] & ~am);
+            }
+        }
+    }
+    __syncthreads();
 }
 
 template <int MAXW>
 __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict__ insts,
-                                                       RunArgs a, int with_pool) {
+                                                      RunArgs a, int with_pool) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int flag;
     const LatInst& I = insts[blockIdx.x];
     const int nwarps = blockDim.x >> 5;
     LatSmem S = carve_lattice(smem, I, nwarps, with_pool != 0);
     const int tid = threadIdx.x, T = blockDim.x;
-    const int N = I.N, L = I.L, W = I.W, R = I.R;
+    const LP P = load_lp(I);
+    const int N = P.N, W = P.W, R = P.R, WR = W * 32;
 
-    // state in
-    for (int i = tid; i < W * N; i += T) S.spins[i] = I.spins[i];
-    for (int i = tid; i < N; i += T) { S.sdesc[i] = I.sdesc[i]; S.csites[i] = I.csites[i]; }
-    for (int i = tid; i < W * 32; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
-    for (int i = tid; i < R; i += T) S.wos[i] = I.wos[i];
+    // state in (spins to colour-major order)
+    for (int i = tid; i < W * N; i += T) {
+        const int wb = i / N, site = i - wb * N;
+        S.spins[wb * N + I.pos[site]] = I.spins[i];
+    }
+    for (int i = tid; i < N; i += T) S.itab[i] = I.itab[i];
+    for (int i = tid; i < WR; i += T) {
+        S.E[i] = I.E[i];
+        S.Eacc[i] = 0;
+        S.Eacc[WR + i] = 0;
+        S.sow[i] = I.sow[i];
+        S.wos[i] = i < R ? I.wos[i] : (int16_t)-1;
+    }
+    for (int i = tid; i < R; i += T) {
+        const double b = I.beta[i];
+        const double db = (i + 1 < R) ? I.beta[i + 1] - b : 0.0;
+        S.beta[i] = b;
+        S.dbeta[i] = db;
+        S.fbeta[i] = (float)b;
+        S.fdbeta[i] = (float)db;
+        S.thr[i] = reinterpret_cast<const uint4*>(I.thr)[i];
+        S.prop[i] = I.prop[i];
+    }
     for (int i = tid; i < 4 * R; i += T) S.st[i] = 0u;
-    if (with_pool)
+    if (with_pool) {
         for (int i = tid; i < 6 * I.NW; i += T) S.ebits[i] = I.ebits[i];
+        for (int i = tid; i < R; i += T) S.cursor[i] = I.cursor[i];
+    }
     long long sweeps = I.ctr->sweeps, n_ex = I.ctr->n_ex, n_prop = I.ctr->n_prop;
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-    const int L2 = L * L, L3 = L2 * L;
-    const int off[12] = {1, -1, L, -L, L2, -L2,
-                         1 - L, L - 1, L - L2, L2 - L, L2 - L3, L3 - L2};
     __syncthreads();
-    rebuild_thresholds(I, S);
+    rebuild_planes(P, S, S.sow);
     __syncthreads();
 
     uint32_t cnt[MAXW][KB];
@@ -335,56 +455,76 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     for (int wb = 0; wb < MAXW; ++wb)
 #pragma unroll
         for (int j = 0; j < KB; ++j) cnt[wb][j] = 0u;
+    int p = 0;   // bond-count buffer of this cycle
+    int q = 0;   // label buffer holding the current slot <-> walker maps
 
     if (a.mode & kModeEnergy) {
-        lattice_sweep<MAXW>(I, S, k0, k1, (uint32_t)sweeps, false, true, cnt, off);
-        lattice_energy_finalize<MAXW>(I, S, cnt);
+        lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, false, true, cnt);
+        lattice_count_reduce<MAXW>(P, S, cnt, p);
+        lattice_store_energies(P, S, p);
+        p ^= 1;
+        __syncthreads();
     }
     if (a.mode & kModeSweeps) {
         for (int k = 0; k < a.n; ++k) {
-            lattice_sweep<MAXW>(I, S, k0, k1, (uint32_t)sweeps, true, k == a.n - 1, cnt, off);
+            lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, true, k == a.n - 1, cnt);
             ++sweeps;
         }
-        if (a.n > 0) lattice_energy_finalize<MAXW>(I, S, cnt);
+        if (a.n > 0) {
+            lattice_count_reduce<MAXW>(P, S, cnt, p);
+            lattice_store_energies(P, S, p);
+            p ^= 1;
+            __syncthreads();
+        }
     }
     if (a.mode & kModePropose) {
         ++n_prop;
-        if (with_pool) lattice_propose(I, S, k0, k1, n_prop);
-        __syncthreads();
+        if (with_pool) lattice_propose(I, S, a, n_prop, q);
     }
     if (a.mode & kModeExchange) {
         ++n_ex;
-        if (lattice_exchange(I, S, k0, k1, n_ex, &flag)) {
-            rebuild_thresholds(I, S);
-            __syncthreads();
-        }
+        lattice_exchange(P, S, a, n_ex, q, nullptr);
+        q ^= 1;
+        __syncthreads();
     }
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
             for (int m = 0; m < a.M; ++m) {
-                lattice_sweep<MAXW>(I, S, k0, k1, (uint32_t)sweeps, true, m == a.M - 1, cnt, off);
+                lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, true, m == a.M - 1, cnt);
                 ++sweeps;
             }
-            lattice_energy_finalize<MAXW>(I, S, cnt);
-            if (proposal_due(sweeps, a)) {
-                ++n_prop;
-                if (with_pool) lattice_propose(I, S, k0, k1, n_prop);
-                __syncthreads();
-            }
+            lattice_count_reduce<MAXW>(P, S, cnt, p);
             ++n_ex;
-            if (lattice_exchange(I, S, k0, k1, n_ex, &flag)) {
-                rebuild_thresholds(I, S);
+            if (proposal_due(sweeps, a)) {
+                lattice_store_energies(P, S, p);
                 __syncthreads();
+                ++n_prop;
+                if (with_pool) lattice_propose(I, S, a, n_prop, q);
+                lattice_exchange(P, S, a, n_ex, q, nullptr);
+            } else {
+                lattice_exchange(P, S, a, n_ex, q, S.Eacc + p * WR);
+                lattice_store_energies(P, S, p);
             }
+            p ^= 1;
+            q ^= 1;
+            __syncthreads();
         }
     }
 
-    // state out
-    for (int i = tid; i < W * N; i += T) I.spins[i] = S.spins[i];
-    for (int i = tid; i < W * 32; i += T) { I.E[i] = S.E[i]; I.sow[i] = S.sow[i]; }
-    for (int i = tid; i < R; i += T) I.wos[i] = S.wos[i];
+    // state out (back to site order)
+    for (int i = tid; i < W * N; i += T) {
+        const int wb = i / N, site = i - wb * N;
+        I.spins[i] = S.spins[wb * N + I.pos[site]];
+    }
+    for (int i = tid; i < WR; i += T) {
+        I.E[i] = S.E[i];
+        I.sow[i] = S.sow[q * WR + i];
+    }
+    for (int i = tid; i < R; i += T) I.wos[i] = S.wos[q * WR + i];
     for (int i = tid; i < 4 * R; i += T)
         if (S.st[i]) I.stats[i] += S.st[i];
+    if (with_pool)
+        for (int i = tid; i < R; i += T) I.cursor[i] = S.cursor[i];
     if (tid == 0) {
         I.ctr->sweeps = sweeps;
         I.ctr->n_ex = n_ex;

@@ -15,23 +15,34 @@ namespace pt {
 PT_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct LatLayout {
-    size_t tw, spins, sdesc, ebits, pbuf, E, Eacc, st, sow, wos, csites, total;
+    size_t tw, spins, itab, beta, dbeta, fbeta, fdbeta, thr, prop, ebits, stage, us, cursor, accr, E, Eacc, st, sow, wos,
+        wsow, total;
 };
 
 PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool) {
     LatLayout l;
+    const size_t WR = (size_t)W * 32;
     size_t o = 0;
-    l.tw = o;     o = align16(o + (size_t)W * 32 * 16);
-    l.spins = o;  o = align16(o + (size_t)W * N * 4);
-    l.sdesc = o;  o = align16(o + (size_t)N * 4);
+    l.tw = o;     o = align16(o + WR * 16);
+    l.spins = o;  o = align16(o + WR / 32 * N * 4);
+    l.itab = o;   o = align16(o + (size_t)N * 16);
+    l.beta = o;   o = align16(o + (size_t)R * 8);
+    l.dbeta = o;  o = align16(o + (size_t)R * 8);
+    l.fbeta = o;  o = align16(o + (size_t)R * 4);
+    l.fdbeta = o; o = align16(o + (size_t)R * 4);
+    l.thr = o;    o = align16(o + (size_t)R * 16);
+    l.prop = o;   o = align16(o + (size_t)R);
     l.ebits = o;  o = align16(o + (with_pool ? (size_t)6 * NW * 4 : 0));
-    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
-    l.E = o;      o = align16(o + (size_t)W * 32 * 4);
-    l.Eacc = o;   o = align16(o + (size_t)W * 32 * 4);
+    l.stage = o;  o = align16(o + (with_pool ? (size_t)R * NW * 4 : 0));
+    l.us = o;     o = align16(o + (with_pool ? (size_t)R * 4 : 0));
+    l.cursor = o; o = align16(o + (with_pool ? (size_t)R * 4 : 0));
+    l.accr = o;   o = align16(o + (with_pool ? WR * 2 : 0));
+    l.E = o;      o = align16(o + WR * 4);
+    l.Eacc = o;   o = align16(o + 2 * WR * 4);
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
-    l.sow = o;    o = align16(o + (size_t)W * 32 * 2);
-    l.wos = o;    o = align16(o + (size_t)R * 2);
-    l.csites = o; o = align16(o + (size_t)N * 2);
+    l.sow = o;    o = align16(o + 2 * WR * 2);
+    l.wos = o;    o = align16(o + 2 * WR * 2);
+    l.wsow = o;   o = align16(o + (size_t)nwarps * WR * 2);
     l.total = o;
     return l;
 }
