@@ -165,6 +165,24 @@ pt_status pt_energies_device(pt_ctx *ctx, int32_t *dev_out);
  * be NULL). Synchronises. */
 pt_status pt_read_state(pt_ctx *ctx, int32_t inst, int8_t *spins, int32_t *E);
 
+/* Same result as pt_read_state, for callers that must not allocate device memory while they
+ * run: a real-time or latency-bounded host loop that keeps every allocation (and the
+ * implicit synchronisation cudaMalloc/cudaFree can cause) out of its steady state, or a
+ * process whose device memory is fully budgeted up front. The paper has no counterpart;
+ * this is a property of the library only.
+ *  - Allocates nothing: the unpacked spins pass through a fixed device buffer of 256 KiB
+ *    (a file-scope __device__ array; every GPU that loads the library holds it until exit),
+ *    and the energies through the context's own buffer made at creation.
+ *  - R * N above 262144 returns PT_ENOTSUP with a message.
+ *  - The first call on a device looks up the buffer's device address (once per device, with
+ *    the context's device current); make that first call before any stream capture.
+ *  - All calls share the one buffer, which keeps the last call's contents. Calls are
+ *    stream ordered and synchronise, so calls from one thread never overlap; calls from
+ *    several host threads at once would race on the buffer and must be serialised by the
+ *    caller.
+ * spins (int8 [R][N], slot order) and E (int32 [R]) are host buffers, either may be NULL. */
+pt_status pt_read_state_noalloc(pt_ctx *ctx, int32_t inst, int8_t *spins, int32_t *E);
+
 /* Walker identity held by each slot (int32 [R]): a configuration keeps its walker id when
  * an exchange moves it to another slot. Synchronises. */
 pt_status pt_read_walkers(pt_ctx *ctx, int32_t inst, int32_t *walker);

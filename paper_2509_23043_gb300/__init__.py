@@ -47,6 +47,7 @@ EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed
            "pt_read_proposals_packed",
            "pt_capture_proposals", "pt_sweep", "pt_global_propose", "pt_exchange",
            "pt_run_cycles", "pt_energies", "pt_energies_device", "pt_read_state",
+           "pt_read_state_noalloc",
            "pt_read_walkers", "pt_write_state", "pt_read_counters", "pt_read_stats", "pt_info",
            "pt_set_stream", "pt_destroy", "pt_last_error"]
 
@@ -71,7 +72,8 @@ def lib():
         "pt_capture_proposals": [vp, vp, i32],
         "pt_sweep": [vp, i32], "pt_global_propose": [vp], "pt_exchange": [vp],
         "pt_run_cycles": [vp, i32], "pt_energies": [vp, vp], "pt_energies_device": [vp, vp],
-        "pt_read_state": [vp, i32, vp, vp], "pt_read_walkers": [vp, i32, vp],
+        "pt_read_state": [vp, i32, vp, vp], "pt_read_state_noalloc": [vp, i32, vp, vp],
+        "pt_read_walkers": [vp, i32, vp],
         "pt_write_state": [vp, i32, vp, vp, i64p, vp], "pt_read_counters": [vp, i32, i64p, vp],
         "pt_read_stats": [vp, i32, vp, vp, vp, vp], "pt_info": [vp, i32, vp],
         "pt_set_stream": [vp, vp], "pt_destroy": [vp],
@@ -243,6 +245,16 @@ def read_state(ctx: Context, inst: int):
     s = np.zeros((R, N), dtype=np.int8)
     E = np.zeros(R, dtype=np.int32)
     _check(lib().pt_read_state(ctx.handle, inst, _ptr(s), _ptr(E)))
+    return s, E
+
+
+def read_state_noalloc(ctx: Context, inst: int):
+    """pt_read_state_noalloc: as read_state, through the library's fixed device buffer."""
+    _inst(ctx, inst)
+    R, N = ctx.R[inst], ctx.N[inst]
+    s = np.zeros((R, N), dtype=np.int8)
+    E = np.zeros(R, dtype=np.int32)
+    _check(lib().pt_read_state_noalloc(ctx.handle, inst, _ptr(s), _ptr(E)))
     return s, E
 
 

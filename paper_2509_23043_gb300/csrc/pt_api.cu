@@ -4,6 +4,7 @@
 // and pt_graph.cu.
 #include <cmath>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -913,3 +914,65 @@ cudaError_t launch_gather_energies(const int32_t* const* E, const int16_t* const
     return cudaGetLastError();
 }
 }  // namespace pt
+
+// ------------------------------------------------------------------ allocation-free state read
+// pt_read_state allocates a temporary device buffer for the unpacked spins on every call.
+// pt_read_state_noalloc serves callers that must not allocate device memory in their steady
+// state: it unpacks into a fixed file-scope device buffer instead. Host code cannot use the
+// array's name as a device address, so the address is looked up once per device with
+// cudaGetSymbolAddress and cached. The buffer is shared by every call and keeps the last
+// call's contents; the read kernel overwrites every byte that is copied out, so nothing has
+// to be cleared first.
+namespace {
+constexpr size_t kReadScratchBytes = 256 * 1024;
+constexpr int kMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) int8_t g_read_scratch[kReadScratchBytes];
+
+namespace {
+std::mutex g_scratch_mutex;
+int8_t* g_scratch_ptr[kMaxDevices] = {};
+
+pt_status scratch_for_current_device(int8_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PT_ENOTSUP, "device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_read_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PT_ECUDA, "cudaGetSymbolAddress(read scratch): %s", cudaGetErrorString(e));
+        g_scratch_ptr[dev] = static_cast<int8_t*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return PT_OK;
+}
+}  // namespace
+
+extern "C" pt_status pt_read_state_noalloc(pt_ctx* ctx, int32_t inst, int8_t* spins, int32_t* E) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int R = ctx->R[inst], N = ctx->N[inst];
+    if (spins) {
+        if ((size_t)R * (size_t)N > kReadScratchBytes)
+            return fail(PT_ENOTSUP, "R*N = %zu exceeds the %zu-byte allocation-free read buffer; "
+                        "use pt_read_state", (size_t)R * (size_t)N, kReadScratchBytes);
+        int8_t* d = nullptr;
+        s = scratch_for_current_device(&d);
+        if (s != PT_OK) return s;
+        cudaError_t e = ctx->engine == 0 ? launch_lattice_read(ctx->d_lat, inst, d, R * N, ctx->stream)
+                                         : launch_graph_read(ctx->d_gr, inst, d, R * N, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(spins, d, (size_t)R * N, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return fail(PT_ECUDA, "read_state_noalloc: %s", cudaGetErrorString(e));
+    }
+    if (E) {
+        s = pt_energies_device(ctx, ctx->d_eout);
+        if (s != PT_OK) return s;
+        CK(cudaMemcpyAsync(E, ctx->d_eout + ctx->eoff[inst], (size_t)R * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
