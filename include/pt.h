@@ -209,6 +209,30 @@ pt_status pt_read_stats(pt_ctx *ctx, int32_t inst, int64_t *swap_acc, int64_t *s
  * threads per block used, and the instance's R and N (inst may be -1 for batch values only).*/
 pt_status pt_info(const pt_ctx *ctx, int32_t inst, int32_t info[6]);
 
+/* Size-class groups: instances of one shape (lattice: same L and walker-block count) are
+ * launched together with one block shape; the groups of a context run concurrently, each
+ * on its own stream forked from the context's stream. group = -1: info[0] = number of
+ * groups. Else info = {members, threads per block, shared-memory bytes, first member}. */
+pt_status pt_group_info(const pt_ctx *ctx, int32_t group, int32_t info[4]);
+
+/* Autotune the block size of every group: each candidate runs probe_cycles cycles from a
+ * device snapshot of the state, which is restored afterwards (the run is unchanged). The
+ * chosen sizes are written to threads_out [groups] (may be NULL). */
+pt_status pt_autotune(pt_ctx *ctx, int32_t probe_cycles, int32_t *threads_out);
+
+/* pt_run_cycles through a CUDA graph: the first call for a cycle count captures the launches
+ * of every group (fork/join over the group streams) and later calls replay it. Ordered on
+ * the context's stream like every other call. */
+pt_status pt_run_cycles_graph(pt_ctx *ctx, int32_t n_cycles);
+
+/* Continuous batching support (lattice engine). pt_set_instance replaces the instance in
+ * slot `inst` by a new one of the same shape (same L and R): couplings, ladder, proposal
+ * set and instance id; its state is redrawn from the new id, its counters, cursors and
+ * statistics reset, and the slot activated. pt_set_active(ctx, inst, 0) makes every later
+ * launch skip the slot (its state is kept); 1 makes it take part again. */
+pt_status pt_set_instance(pt_ctx *ctx, int32_t inst, const pt_instance_desc *desc);
+pt_status pt_set_active(pt_ctx *ctx, int32_t inst, int32_t active);
+
 /* Change the stream of all later calls. */
 pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
 

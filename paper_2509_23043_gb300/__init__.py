@@ -49,7 +49,8 @@ EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed
            "pt_run_cycles", "pt_energies", "pt_energies_device", "pt_read_state",
            "pt_read_state_noalloc",
            "pt_read_walkers", "pt_write_state", "pt_read_counters", "pt_read_stats", "pt_info",
-           "pt_set_stream", "pt_destroy", "pt_last_error"]
+           "pt_group_info", "pt_autotune", "pt_run_cycles_graph", "pt_set_instance",
+           "pt_set_active", "pt_set_stream", "pt_destroy", "pt_last_error"]
 
 _lib = None
 
@@ -76,6 +77,9 @@ def lib():
         "pt_read_walkers": [vp, i32, vp],
         "pt_write_state": [vp, i32, vp, vp, i64p, vp], "pt_read_counters": [vp, i32, i64p, vp],
         "pt_read_stats": [vp, i32, vp, vp, vp, vp], "pt_info": [vp, i32, vp],
+        "pt_group_info": [vp, i32, vp], "pt_autotune": [vp, i32, vp],
+        "pt_run_cycles_graph": [vp, i32], "pt_set_instance": [vp, i32, C.POINTER(_Desc)],
+        "pt_set_active": [vp, i32, i32],
         "pt_set_stream": [vp, vp], "pt_destroy": [vp],
     }
     for name, args in sig.items():
@@ -154,6 +158,17 @@ class Context:
         if getattr(self, "handle", None) and self.handle.value and _lib is not None:
             _lib.pt_destroy(self.handle)
             self.handle = None
+
+
+def _desc(inst, beta, prop, iid, keep):
+    b = _arr(beta, np.float64)
+    ei, ej, eJ = _arr(inst.edge_i, np.int32), _arr(inst.edge_j, np.int32), _arr(inst.edge_J, np.int32)
+    h = _arr(getattr(inst, "h", None), np.int32)
+    cl = _arr(getattr(inst, "clamp", None), np.int8)
+    pe = None if prop is None else _arr(prop, np.uint8)
+    keep += [b, ei, ej, eJ, h, cl, pe]
+    return _Desc(int(iid) & 0xFFFFFFFF, int(inst.n_spins), int(getattr(inst, "lattice_L", 0)),
+                 len(ei), _ptr(ei), _ptr(ej), _ptr(eJ), _ptr(h), _ptr(cl), len(b), _ptr(b), _ptr(pe))
 
 
 def create_instances(instances: Sequence, betas: Sequence, config: Config,
@@ -293,6 +308,39 @@ def info(ctx: Context, inst: int = -1) -> dict:
     _check(lib().pt_info(ctx.handle, inst, _ptr(v)))
     return {"n": int(v[0]), "engine": "lattice" if v[1] == 0 else "graph",
             "threads": int(v[2]), "smem": int(v[3]), "R": int(v[4]), "N": int(v[5])}
+
+
+def group_info(ctx: Context) -> list[dict]:
+    v = np.zeros(4, dtype=np.int32)
+    _check(lib().pt_group_info(ctx.handle, -1, _ptr(v)))
+    out = []
+    for g in range(int(v[0])):
+        _check(lib().pt_group_info(ctx.handle, g, _ptr(v)))
+        out.append({"members": int(v[0]), "threads": int(v[1]), "smem": int(v[2]), "first": int(v[3])})
+    return out
+
+
+def autotune(ctx: Context, probe_cycles: int = 20) -> list[int]:
+    n = len(group_info(ctx))
+    t = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().pt_autotune(ctx.handle, probe_cycles, _ptr(t)))
+    return [int(x) for x in t[:n]]
+
+
+def run_cycles_graph(ctx: Context, n_cycles: int):
+    _check(lib().pt_run_cycles_graph(ctx.handle, n_cycles))
+
+
+def set_instance(ctx: Context, inst: int, instance, beta, prop_enabled=None, instance_id: int = 0):
+    _inst(ctx, inst)
+    keep = []
+    d = _desc(instance, beta, prop_enabled, instance_id, keep)
+    _check(lib().pt_set_instance(ctx.handle, inst, C.byref(d)))
+
+
+def set_active(ctx: Context, inst: int, active: bool):
+    _inst(ctx, inst)
+    _check(lib().pt_set_active(ctx.handle, inst, 1 if active else 0))
 
 
 def set_stream(ctx: Context, stream):

@@ -121,24 +121,43 @@ int lattice_colour(int n, int L) {
 
 }  // namespace
 
+// A group: instances of one size class, launched together with one block shape on one
+// stream; the groups of a context run concurrently.
+struct Group {
+    std::vector<int> members;
+    int T = 128;
+    size_t smem = 0;
+    int maxW = 1;
+    int maxitems = 0;          // largest (colour class x walker blocks) of a member
+    void* d_insts = nullptr;   // LatInst[] or GraphInst[] of the members
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+// Arena offsets of one lattice instance's arrays (for slot replacement).
+struct LatOff { size_t spins, itab, pos, E, sow, wos, thr, beta, prop, cur, eb, ctr, st, active; };
+
 struct pt_ctx {
     int engine = 0;           // 0 lattice, 1 graph
     int n = 0;
     pt_config cfg{};
     cudaStream_t stream = nullptr;
-    int threads = 128;
-    size_t smem = 0;
-    int maxW = 1;
     int with_pool = 0;
     int NWmax = 0;
     int uniformN = -1;        // N when all instances share it, else -1
-    std::vector<int> N, R, W, NW, R4;
+    int optin = 0;            // device limit on dynamic shared memory per block
+    std::vector<int> N, R, W, NW, R4, L;
     std::vector<size_t> slab_off;  // words, instance offset inside one pool entry
     size_t slab = 0;               // words per pool entry (all instances, all slots)
     uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
     uint32_t* pool = nullptr;
     std::vector<LatInst> lat;
     std::vector<GraphInst> gr;
+    std::vector<LatOff> loff;
+    std::vector<int> group_of;     // group index of each instance
+    std::vector<Group> groups;
+    cudaEvent_t fork = nullptr;
     LatInst* d_lat = nullptr;
     GraphInst* d_gr = nullptr;
     int32_t* d_eoff = nullptr;          // [n] offsets of each instance in the energy output
@@ -147,11 +166,21 @@ struct pt_ctx {
     int32_t* d_eout = nullptr;          // [sum R] gather buffer
     int totalR = 0;
     std::vector<int> eoff;
+    // CUDA graph of pt_run_cycles_graph (one cycle count at a time)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int gcycles = -1;
 };
+
+namespace pt {
+cudaError_t configure_lattice_kernels(int smem);
+cudaError_t configure_graph_kernels(int smem);
+}  // namespace pt
 
 namespace {
 
-pt_status launch_run(pt_ctx* c, int mode, int nn) {
+RunArgs make_args(const pt_ctx* c, int mode, int nn) {
     RunArgs a{};
     a.seed = c->cfg.seed;
     a.mode = mode;
@@ -169,13 +198,55 @@ pt_status launch_run(pt_ctx* c, int mode, int nn) {
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    cudaError_t e;
+    return a;
+}
+
+cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, int count,
+                         const RunArgs& a, cudaStream_t s) {
     if (c->engine == 0)
-        e = launch_lattice(c->d_lat, c->n, c->maxW, c->threads, c->smem, a, c->with_pool, c->stream);
-    else
-        e = launch_graph(c->d_gr, c->n, c->threads, c->smem, a, c->with_pool, c->stream);
+        return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, g.T, g.smem, a,
+                              c->with_pool, s);
+    return launch_graph(static_cast<const GraphInst*>(d_insts), count, g.T, g.smem, a, c->with_pool, s);
+}
+
+// Launch one kernel per group on stream s; with several groups they fork from s onto their
+// own streams and join back, so they run concurrently (also inside a stream capture).
+pt_status launch_on(pt_ctx* c, int mode, int nn, cudaStream_t s) {
+    const RunArgs a = make_args(c, mode, nn);
+    cudaError_t e = cudaSuccess;
+    if (c->groups.size() == 1) {
+        const Group& g = c->groups[0];
+        e = launch_group(c, g, g.d_insts, (int)g.members.size(), a, s);
+    } else {
+        e = cudaEventRecord(c->fork, s);
+        for (size_t k = 0; e == cudaSuccess && k < c->groups.size(); ++k) {
+            const Group& g = c->groups[k];
+            e = cudaStreamWaitEvent(g.stream, c->fork, 0);
+            if (e == cudaSuccess) e = launch_group(c, g, g.d_insts, (int)g.members.size(), a, g.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.done, 0);
+        }
+    }
     if (e != cudaSuccess) return fail(PT_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return PT_OK;
+}
+
+pt_status launch_run(pt_ctx* c, int mode, int nn) { return launch_on(c, mode, nn, c->stream); }
+
+// One instance alone (initial energies of a replaced slot).
+pt_status launch_one(pt_ctx* c, int inst, int mode) {
+    const Group& g = c->groups[c->group_of[inst]];
+    const void* d = c->engine == 0 ? static_cast<const void*>(c->d_lat + inst)
+                                   : static_cast<const void*>(c->d_gr + inst);
+    cudaError_t e = launch_group(c, g, d, 1, make_args(c, mode, 0), c->stream);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+void drop_graph(pt_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gcycles = -1;
 }
 
 bool is_lattice_desc(const pt_instance_desc& d, const pt_config& cfg) {
@@ -232,136 +303,183 @@ pt_status validate(const pt_instance_desc& d, int k) {
 }
 
 // -------------------------------------------------------------------------------- lattice
+// Host image of one lattice instance: colouring, per-site table, bond bit strings,
+// thresholds and initial labels.
+struct LatHost {
+    int L, N, R, W, NW, ncol;
+    int col_off[4];
+    std::vector<uint32_t> itab, eb, thr;
+    std::vector<uint16_t> pos;
+    std::vector<int16_t> sow, wos;
+    std::vector<uint8_t> prop;
+    int maxitems = 0;
+};
+
+pt_status lattice_host(const pt_instance_desc& d, LatHost& h, int k) {
+    const int L = d.lattice_L, N = d.n_spins, R = d.n_replicas, W = (R + 31) / 32, NW = (N + 31) / 32;
+    if (N > 8192) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 8192 (L <= 20)", k);
+    h.L = L; h.N = N; h.R = R; h.W = W; h.NW = NW;
+    h.ncol = (L % 2 == 0) ? 2 : 3;
+    std::vector<int> col(N);
+    for (int i = 0; i < N; ++i) col[i] = lattice_colour(i, L);
+    h.eb.assign(6 * (size_t)NW, 0u);
+    h.itab.clear();
+    h.itab.reserve(4 * (size_t)N);
+    const int L2 = L * L;
+    // colour-major position of every site (the shared-memory order of the spins)
+    h.pos.assign(N, 0);
+    {
+        int p = 0;
+        for (int cc = 0; cc < h.ncol; ++cc)
+            for (int i = 0; i < N; ++i)
+                if (col[i] == cc) h.pos[i] = (uint16_t)p++;
+    }
+    h.col_off[0] = 0;
+    int filled = 0;
+    h.maxitems = 0;
+    for (int cc = 0; cc < h.ncol; ++cc) {
+        for (int i = 0; i < N; ++i) {
+            if (col[i] != cc) continue;
+            const int x = i % L, y = (i / L) % L, z = i / L2;
+            const int xm = (x + L - 1) % L, ym = (y + L - 1) % L, zm = (z + L - 1) % L;
+            const int nbr[6] = {(x + 1) % L + L * (y + L * z), xm + L * (y + L * z),
+                                x + L * ((y + 1) % L + L * z), x + L * (ym + L * z),
+                                x + L * (y + L * ((z + 1) % L)), x + L * (y + L * zm)};
+            // the +d bond of i is edge 3i+d; its -d bond is the +d bond of nbr[2d+1]
+            const int Jv[6] = {d.edge_J[3 * i + 0], d.edge_J[3 * nbr[1] + 0], d.edge_J[3 * i + 1],
+                               d.edge_J[3 * nbr[3] + 1], d.edge_J[3 * i + 2], d.edge_J[3 * nbr[5] + 2]};
+            uint32_t flags = 0;
+            int nlow = 0;
+            uint32_t e16[6];
+            for (int dir = 0; dir < 6; ++dir) {
+                if (col[nbr[dir]] < cc) { flags |= 1u << dir; ++nlow; }
+                e16[dir] = (uint32_t)(4 * h.pos[nbr[dir]]) | (Jv[dir] < 0 ? 0x8000u : 0u);
+            }
+            if (nlow == 6) flags |= 64u;
+            h.itab.push_back((uint32_t)i | (flags << 16));
+            h.itab.push_back(e16[0] | (e16[1] << 16));
+            h.itab.push_back(e16[2] | (e16[3] << 16));
+            h.itab.push_back(e16[4] | (e16[5] << 16));
+            ++filled;
+        }
+        h.col_off[cc + 1] = filled;
+        h.maxitems = std::max(h.maxitems, (h.col_off[cc + 1] - h.col_off[cc]) * W);
+    }
+    for (int cc = h.ncol + 1; cc < 4; ++cc) h.col_off[cc] = filled;
+    // bit strings of the bonds (for proposal energies): negative +d bonds, wraps
+    for (int i = 0; i < N; ++i) {
+        const int x = i % L, y = (i / L) % L, z = i / L2;
+        const bool wrap[3] = {x == L - 1, y == L - 1, z == L - 1};
+        for (int dd = 0; dd < 3; ++dd) {
+            if (d.edge_J[3 * i + dd] < 0) h.eb[(size_t)dd * NW + (i >> 5)] |= 1u << (i & 31);
+            if (wrap[dd]) h.eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
+        }
+    }
+    h.thr.assign(4 * (size_t)R, 0u);
+    for (int r = 0; r < R; ++r) {
+        h.thr[4 * r + 0] = metropolis_threshold(d.beta[r], 4);
+        h.thr[4 * r + 1] = metropolis_threshold(d.beta[r], 8);
+        h.thr[4 * r + 2] = metropolis_threshold(d.beta[r], 12);
+    }
+    h.sow.assign(W * 32, -1);
+    h.wos.assign(R, 0);
+    for (int r = 0; r < R; ++r) { h.sow[r] = (int16_t)r; h.wos[r] = (int16_t)r; }
+    h.prop.assign(R, 0);
+    if (d.prop_enabled)
+        for (int r = 0; r < R; ++r) h.prop[r] = d.prop_enabled[r] ? 1 : 0;
+    return PT_OK;
+}
+
+void lattice_fill_inst(LatInst& I, const LatHost& h, uint32_t iid, int P) {
+    I.iid = iid; I.L = h.L; I.N = h.N; I.R = h.R; I.W = h.W; I.NW = h.NW; I.ncol = h.ncol; I.P = P;
+    for (int cc = 0; cc < 4; ++cc) I.col_off[cc] = h.col_off[cc];
+}
+
+// Block shape of a lattice group: about two words per thread per colour class (at most 42,
+// the width of the energy counters), unless threads_per_block fixes it.
+int lattice_auto_threads(int maxitems) {
+    int T = ((maxitems / 2 + 31) / 32) * 32;
+    return std::max(64, std::min(512, T));
+}
+
+pt_status lattice_group_shape(pt_ctx* c, Group& g, int T) {
+    if (T % 32 != 0 || T < 32 || T > 512)
+        return fail(PT_EINVAL, "lattice engine: threads_per_block must be a multiple of 32 in [32, 512]");
+    if ((g.maxitems + T - 1) / T > 42)
+        return fail(PT_ENOTSUP, "too many words per thread (%d); raise threads_per_block", (g.maxitems + T - 1) / T);
+    size_t smem = 0;
+    for (int k : g.members) {
+        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0);
+        smem = std::max(smem, l.total);
+    }
+    if (smem > (size_t)c->optin)
+        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", smem, c->optin);
+    g.T = T;
+    g.smem = smem;
+    return PT_OK;
+}
+
 pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    std::vector<size_t> o_spins(n), o_itab(n), o_pos(n), o_E(n), o_sow(n), o_wos(n), o_thr(n),
-        o_beta(n), o_prop(n), o_cur(n), o_eb(n), o_ctr(n), o_st(n);
     c->lat.resize(n);
-    size_t maxsmem = 0;
-    int maxitems = 0;
-    for (int k = 0; k < n; ++k) {
-        const pt_instance_desc& d = descs[k];
-        const int L = d.lattice_L, N = d.n_spins, R = d.n_replicas, W = (R + 31) / 32, NW = (N + 31) / 32;
-        c->N[k] = N; c->R[k] = R; c->W[k] = W; c->NW[k] = NW; c->R4[k] = W * 32;
-        if (N > 8192) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 8192 (L <= 20)", k);
-        LatInst& I = c->lat[k];
-        memset(&I, 0, sizeof I);
-        I.iid = d.instance_id; I.L = L; I.N = N; I.R = R; I.W = W; I.NW = NW;
-        I.ncol = (L % 2 == 0) ? 2 : 3;
-        I.P = c->cfg.pool_size;
-        // colour classes, and one table entry per site in colour order
-        std::vector<int> col(N);
-        for (int i = 0; i < N; ++i) col[i] = lattice_colour(i, L);
-        std::vector<uint32_t> eb(6 * (size_t)NW, 0u);
-        std::vector<uint32_t> itab;
-        itab.reserve(4 * (size_t)N);
-        const int L2 = L * L;
-        // colour-major position of every site (the shared-memory order of the spins)
-        std::vector<uint16_t> pos(N);
-        {
-            int p = 0;
-            for (int cc = 0; cc < I.ncol; ++cc)
-                for (int i = 0; i < N; ++i)
-                    if (col[i] == cc) pos[i] = (uint16_t)p++;
-        }
-        I.col_off[0] = 0;
-        int filled = 0;
-        for (int cc = 0; cc < I.ncol; ++cc) {
-            for (int i = 0; i < N; ++i) {
-                if (col[i] != cc) continue;
-                const int x = i % L, y = (i / L) % L, z = i / L2;
-                const int xm = (x + L - 1) % L, ym = (y + L - 1) % L, zm = (z + L - 1) % L;
-                const int nbr[6] = {(x + 1) % L + L * (y + L * z), xm + L * (y + L * z),
-                                    x + L * ((y + 1) % L + L * z), x + L * (ym + L * z),
-                                    x + L * (y + L * ((z + 1) % L)), x + L * (y + L * zm)};
-                // the +d bond of i is edge 3i+d; its -d bond is the +d bond of nbr[2d+1]
-                const int Jv[6] = {d.edge_J[3 * i + 0], d.edge_J[3 * nbr[1] + 0], d.edge_J[3 * i + 1],
-                                   d.edge_J[3 * nbr[3] + 1], d.edge_J[3 * i + 2], d.edge_J[3 * nbr[5] + 2]};
-                uint32_t flags = 0;
-                int nlow = 0;
-                uint32_t e16[6];
-                for (int dir = 0; dir < 6; ++dir) {
-                    if (col[nbr[dir]] < cc) { flags |= 1u << dir; ++nlow; }
-                    e16[dir] = (uint32_t)(4 * pos[nbr[dir]]) | (Jv[dir] < 0 ? 0x8000u : 0u);
-                }
-                if (nlow == 6) flags |= 64u;
-                itab.push_back((uint32_t)i | (flags << 16));
-                itab.push_back(e16[0] | (e16[1] << 16));
-                itab.push_back(e16[2] | (e16[3] << 16));
-                itab.push_back(e16[4] | (e16[5] << 16));
-                ++filled;
-            }
-            I.col_off[cc + 1] = filled;
-            maxitems = std::max(maxitems, (I.col_off[cc + 1] - I.col_off[cc]) * W);
-        }
-        for (int cc = I.ncol + 1; cc < 4; ++cc) I.col_off[cc] = filled;
-        // bit strings of the bonds (for proposal energies): negative +d bonds, wraps
-        for (int i = 0; i < N; ++i) {
-            const int x = i % L, y = (i / L) % L, z = i / L2;
-            const bool wrap[3] = {x == L - 1, y == L - 1, z == L - 1};
-            for (int dd = 0; dd < 3; ++dd) {
-                if (d.edge_J[3 * i + dd] < 0) eb[(size_t)dd * NW + (i >> 5)] |= 1u << (i & 31);
-                if (wrap[dd]) eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
-            }
-        }
-        std::vector<uint32_t> thr(4 * (size_t)R, 0u);
-        for (int r = 0; r < R; ++r) {
-            thr[4 * r + 0] = metropolis_threshold(d.beta[r], 4);
-            thr[4 * r + 1] = metropolis_threshold(d.beta[r], 8);
-            thr[4 * r + 2] = metropolis_threshold(d.beta[r], 12);
-        }
-        std::vector<int16_t> sow(W * 32, -1), wos(R);
-        for (int r = 0; r < R; ++r) { sow[r] = (int16_t)r; wos[r] = (int16_t)r; }
-        std::vector<uint8_t> prop(R, 0);
-        if (d.prop_enabled)
-            for (int r = 0; r < R; ++r) prop[r] = d.prop_enabled[r] ? 1 : 0;
-        o_spins[k] = A.zeros((size_t)W * N * 4);
-        o_itab[k] = A.add(itab.data(), itab.size() * 4);
-        o_pos[k] = A.add(pos.data(), pos.size() * 2);
-        o_E[k] = A.zeros((size_t)W * 32 * 4);
-        o_sow[k] = A.add(sow.data(), sow.size() * 2);
-        o_wos[k] = A.add(wos.data(), wos.size() * 2);
-        o_thr[k] = A.add(thr.data(), thr.size() * 4);
-        o_beta[k] = A.add(d.beta, (size_t)R * 8);
-        o_prop[k] = A.add(prop.data(), prop.size());
-        o_cur[k] = A.zeros((size_t)R * 4);
-        o_eb[k] = A.add(eb.data(), eb.size() * 4);
-        o_ctr[k] = A.zeros(sizeof(Counters));
-        o_st[k] = A.zeros((size_t)4 * R * 8);
-        c->slab_off[k] = c->slab;
-        c->slab += (size_t)R * NW;
-        c->NWmax = std::max(c->NWmax, NW);
-        c->maxW = std::max(c->maxW, W);
-    }
-    // launch shape: about two words per thread per colour class, at most 42 (counter width)
-    int T = c->cfg.threads_per_block;
-    if (T <= 0) {
-        T = ((maxitems / 2 + 31) / 32) * 32;
-        T = std::max(64, std::min(512, T));
-    }
-    if (T % 32 != 0 || T < 32 || T > 512) return fail(PT_EINVAL, "lattice engine: threads_per_block must be a multiple of 32 in [32, 512]");
-    if ((maxitems + T - 1) / T > 42)
-        return fail(PT_ENOTSUP, "too many words per thread (%d); raise threads_per_block", (maxitems + T - 1) / T);
-    c->threads = T;
+    c->loff.resize(n);
+    std::vector<int> maxitems(n);
     c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
     for (int k = 0; k < n; ++k) {
+        const pt_instance_desc& d = descs[k];
+        LatHost h;
+        pt_status st = lattice_host(d, h, k);
+        if (st != PT_OK) return st;
+        c->N[k] = h.N; c->R[k] = h.R; c->W[k] = h.W; c->NW[k] = h.NW; c->R4[k] = h.W * 32; c->L[k] = h.L;
+        maxitems[k] = h.maxitems;
         LatInst& I = c->lat[k];
-        int maxcol = 0;
-        for (int cc = 0; cc < I.ncol; ++cc) maxcol = std::max(maxcol, I.col_off[cc + 1] - I.col_off[cc]);
-        I.nit = (maxcol + T - 1) / T;
-        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32,
-                                           c->with_pool != 0);
-        maxsmem = std::max(maxsmem, l.total);
+        memset(&I, 0, sizeof I);
+        lattice_fill_inst(I, h, d.instance_id, c->cfg.pool_size);
+        LatOff& o = c->loff[k];
+        const int32_t one = 1;
+        o.spins = A.zeros((size_t)h.W * h.N * 4);
+        o.itab = A.add(h.itab.data(), h.itab.size() * 4);
+        o.pos = A.add(h.pos.data(), h.pos.size() * 2);
+        o.E = A.zeros((size_t)h.W * 32 * 4);
+        o.sow = A.add(h.sow.data(), h.sow.size() * 2);
+        o.wos = A.add(h.wos.data(), h.wos.size() * 2);
+        o.thr = A.add(h.thr.data(), h.thr.size() * 4);
+        o.beta = A.add(d.beta, (size_t)h.R * 8);
+        o.prop = A.add(h.prop.data(), h.prop.size());
+        o.cur = A.zeros((size_t)h.R * 4);
+        o.eb = A.add(h.eb.data(), h.eb.size() * 4);
+        o.ctr = A.zeros(sizeof(Counters));
+        o.st = A.zeros((size_t)4 * h.R * 8);
+        o.active = A.add(&one, 4);
+        c->slab_off[k] = c->slab;
+        c->slab += (size_t)h.R * h.NW;
+        c->NWmax = std::max(c->NWmax, h.NW);
     }
-    int dev = 0, optin = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (maxsmem > (size_t)optin)
-        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, optin);
-    c->smem = maxsmem;
-    if (c->maxW > 2) c->maxW = 4;
-
+    // groups: one per (walker blocks, L)
+    c->group_of.assign(n, -1);
+    for (int k = 0; k < n; ++k) {
+        int gk = -1;
+        for (size_t g = 0; g < c->groups.size(); ++g) {
+            const int m = c->groups[g].members[0];
+            if (c->W[m] == c->W[k] && c->L[m] == c->L[k]) { gk = (int)g; break; }
+        }
+        if (gk < 0) { c->groups.emplace_back(); gk = (int)c->groups.size() - 1; }
+        c->groups[gk].members.push_back(k);
+        c->group_of[k] = gk;
+    }
+    for (Group& g : c->groups) {
+        for (int k : g.members) {
+            g.maxitems = std::max(g.maxitems, maxitems[k]);
+            g.maxW = std::max(g.maxW, c->W[k]);
+        }
+        if (g.maxW > 2) g.maxW = 4;
+        const int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block : lattice_auto_threads(g.maxitems);
+        pt_status st = lattice_group_shape(c, g, T);
+        if (st != PT_OK) return st;
+    }
+    CK(configure_lattice_kernels(c->optin));
+    c->arena_bytes = A.host.size();
     CK(cudaMallocAsync((void**)&c->arena, A.host.size(), c->stream));
     CK(cudaMemcpyAsync(c->arena, A.host.data(), A.host.size(), cudaMemcpyHostToDevice, c->stream));
     if (c->with_pool) {
@@ -372,40 +490,48 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     uint8_t* b = c->arena;
     for (int k = 0; k < n; ++k) {
         LatInst& I = c->lat[k];
-        I.spins = (uint32_t*)(b + o_spins[k]);
-        I.itab = (const uint4*)(b + o_itab[k]);
-        I.pos = (const uint16_t*)(b + o_pos[k]);
-        I.E = (int32_t*)(b + o_E[k]);
-        I.sow = (int16_t*)(b + o_sow[k]);
-        I.wos = (int16_t*)(b + o_wos[k]);
-        I.thr = (const uint32_t*)(b + o_thr[k]);
-        I.beta = (const double*)(b + o_beta[k]);
-        I.prop = (const uint8_t*)(b + o_prop[k]);
-        I.cursor = (int32_t*)(b + o_cur[k]);
-        I.ebits = (const uint32_t*)(b + o_eb[k]);
-        I.ctr = (Counters*)(b + o_ctr[k]);
-        I.stats = (unsigned long long*)(b + o_st[k]);
+        const LatOff& o = c->loff[k];
+        I.spins = (uint32_t*)(b + o.spins);
+        I.itab = (const uint4*)(b + o.itab);
+        I.pos = (const uint16_t*)(b + o.pos);
+        I.E = (int32_t*)(b + o.E);
+        I.sow = (int16_t*)(b + o.sow);
+        I.wos = (int16_t*)(b + o.wos);
+        I.thr = (const uint32_t*)(b + o.thr);
+        I.beta = (const double*)(b + o.beta);
+        I.prop = (const uint8_t*)(b + o.prop);
+        I.cursor = (int32_t*)(b + o.cur);
+        I.ebits = (const uint32_t*)(b + o.eb);
+        I.ctr = (Counters*)(b + o.ctr);
+        I.stats = (unsigned long long*)(b + o.st);
+        I.active = (const int32_t*)(b + o.active);
         I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
         I.pstride = (long long)c->slab;
     }
     CK(cudaMallocAsync((void**)&c->d_lat, sizeof(LatInst) * n, c->stream));
     CK(cudaMemcpyAsync(c->d_lat, c->lat.data(), sizeof(LatInst) * n, cudaMemcpyHostToDevice, c->stream));
+    for (Group& g : c->groups) {
+        std::vector<LatInst> m;
+        for (int k : g.members) m.push_back(c->lat[k]);
+        CK(cudaMallocAsync(&g.d_insts, sizeof(LatInst) * m.size(), c->stream));
+        CK(cudaMemcpyAsync(g.d_insts, m.data(), sizeof(LatInst) * m.size(), cudaMemcpyHostToDevice, c->stream));
+    }
     cudaError_t e = launch_lattice_init(c->d_lat, n, c->cfg.seed, c->stream);
     if (e != cudaSuccess) return fail(PT_ECUDA, "init: %s", cudaGetErrorString(e));
-    return launch_run(c, kModeEnergy, 0);
+    CK(cudaStreamSynchronize(c->stream));   // host images above must outlive their copies
+    return PT_OK;
 }
 
 // -------------------------------------------------------------------------------- graph
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st; };
+    struct Off { size_t spins, clamp, rowp, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
     int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block : 128;
     if (T % 32 != 0 || T < 32 || T > 1024) return fail(PT_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
-    c->threads = T;
     c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
     for (int k = 0; k < n; ++k) {
         const pt_instance_desc& d = descs[k];
@@ -500,18 +626,24 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].cur = A.zeros((size_t)R * 4);
         o[k].ctr = A.zeros(sizeof(Counters));
         o[k].st = A.zeros((size_t)4 * R * 8);
+        const int32_t one = 1;
+        o[k].active = A.add(&one, 4);
         c->slab_off[k] = c->slab;
         c->slab += (size_t)R * NW;
         c->NWmax = std::max(c->NWmax, NW);
         const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, T / 32, c->with_pool != 0);
         maxsmem = std::max(maxsmem, l.total);
     }
-    int dev = 0, optin = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (maxsmem > (size_t)optin)
-        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, optin);
-    c->smem = maxsmem;
+    if (maxsmem > (size_t)c->optin)
+        return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, c->optin);
+    c->groups.assign(1, Group{});
+    Group& grp = c->groups[0];
+    for (int k = 0; k < n; ++k) grp.members.push_back(k);
+    grp.T = T;
+    grp.smem = maxsmem;
+    c->group_of.assign(n, 0);
+    CK(configure_graph_kernels(c->optin));
+    c->arena_bytes = A.host.size();
     CK(cudaMallocAsync((void**)&c->arena, A.host.size(), c->stream));
     CK(cudaMemcpyAsync(c->arena, A.host.data(), A.host.size(), cudaMemcpyHostToDevice, c->stream));
     if (c->with_pool) {
@@ -542,19 +674,32 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.cursor = (int32_t*)(b + o[k].cur);
         I.ctr = (Counters*)(b + o[k].ctr);
         I.stats = (unsigned long long*)(b + o[k].st);
+        I.active = (const int32_t*)(b + o[k].active);
         I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
         I.pstride = (long long)c->slab;
     }
     CK(cudaMallocAsync((void**)&c->d_gr, sizeof(GraphInst) * n, c->stream));
     CK(cudaMemcpyAsync(c->d_gr, c->gr.data(), sizeof(GraphInst) * n, cudaMemcpyHostToDevice, c->stream));
+    grp.d_insts = c->d_gr;   // the group is the whole batch, in instance order
     cudaError_t e = launch_graph_init(c->d_gr, n, c->cfg.seed, c->stream);
     if (e != cudaSuccess) return fail(PT_ECUDA, "init: %s", cudaGetErrorString(e));
-    return launch_run(c, kModeEnergy, 0);
+    CK(cudaStreamSynchronize(c->stream));
+    return PT_OK;
 }
 
 void release(pt_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->stream;
+    drop_graph(c);
+    for (Group& g : c->groups) {
+        if (g.d_insts && !(c->engine == 1)) cudaFreeAsync(g.d_insts, s);
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->gev_in) cudaEventDestroy(c->gev_in);
+    if (c->gev_out) cudaEventDestroy(c->gev_out);
     if (c->arena) cudaFreeAsync(c->arena, s);
     if (c->pool) cudaFreeAsync(c->pool, s);
     if (c->d_lat) cudaFreeAsync(c->d_lat, s);
@@ -609,10 +754,30 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     c->n = n;
     c->cfg = *cfg;
     c->stream = (cudaStream_t)cuda_stream;
-    c->N.resize(n); c->R.resize(n); c->W.resize(n); c->NW.resize(n); c->R4.resize(n);
+    c->N.resize(n); c->R.resize(n); c->W.resize(n); c->NW.resize(n); c->R4.resize(n); c->L.resize(n);
     c->slab_off.resize(n);
+    {
+        int dev = 0;
+        cudaError_t e0 = cudaGetDevice(&dev);
+        if (e0 == cudaSuccess)
+            e0 = cudaDeviceGetAttribute(&c->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e0 != cudaSuccess) { release(c); return fail(PT_ECUDA, "device query: %s", cudaGetErrorString(e0)); }
+    }
+    for (int k = 0; k < n; ++k) c->L[k] = descs[k].lattice_L;
     pt_status s = lat0 ? build_lattice(c, descs) : build_graph(c, descs);
     if (s != PT_OK) { release(c); return s; }
+    {
+        cudaError_t e1 = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+        for (Group& g : c->groups) {
+            if (c->groups.size() > 1 && e1 == cudaSuccess) {
+                e1 = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+                if (e1 == cudaSuccess) e1 = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+            }
+        }
+        if (e1 != cudaSuccess) { release(c); return fail(PT_ECUDA, "streams: %s", cudaGetErrorString(e1)); }
+        s = launch_run(c, kModeEnergy, 0);   // energies of the initial state
+        if (s != PT_OK) { release(c); return s; }
+    }
     // energy gather tables
     c->eoff.resize(n);
     int tot = 0;
@@ -657,12 +822,186 @@ pt_status pt_set_stream(pt_ctx* ctx, void* s) {
     return PT_OK;
 }
 
+pt_status pt_group_info(const pt_ctx* ctx, int32_t group, int32_t info[4]) {
+    if (!ctx || !info) return fail(PT_EINVAL, "NULL argument");
+    if (group < 0) { info[0] = (int32_t)ctx->groups.size(); return PT_OK; }
+    if (group >= (int32_t)ctx->groups.size()) return fail(PT_EINVAL, "group %d out of range", group);
+    const Group& g = ctx->groups[group];
+    info[0] = (int32_t)g.members.size();
+    info[1] = g.T;
+    info[2] = (int32_t)g.smem;
+    info[3] = g.members[0];
+    return PT_OK;
+}
+
+pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    if (probe_cycles < 1) return fail(PT_EINVAL, "probe_cycles must be >= 1");
+    drop_graph(ctx);
+    uint8_t* snap = nullptr;
+    CK(cudaMallocAsync((void**)&snap, ctx->arena_bytes, ctx->stream));
+    CK(cudaMemcpyAsync(snap, ctx->arena, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    pt_status st = PT_OK;
+    const RunArgs a = make_args(ctx, kModeCycles, probe_cycles);
+    const int cand[] = {64, 96, 128, 192, 256, 384, 512};
+    for (size_t gi = 0; gi < ctx->groups.size() && e == cudaSuccess && st == PT_OK; ++gi) {
+        Group& g = ctx->groups[gi];
+        const Group keep = g;
+        float best = 1e30f;
+        int bestT = g.T;
+        for (int T : cand) {
+            if (ctx->engine == 1 && T > 1024) continue;
+            Group trial = keep;
+            if (ctx->engine == 0) {
+                if (lattice_group_shape(ctx, trial, T) != PT_OK) continue;
+            } else {
+                const GraphInst& I0 = ctx->gr[g.members[0]];
+                size_t smem = 0;
+                for (int k : g.members) {
+                    const GraphInst& I = ctx->gr[k];
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, T / 32, ctx->with_pool != 0);
+                    smem = std::max(smem, l.total);
+                }
+                (void)I0;
+                if (smem > (size_t)ctx->optin) continue;
+                trial.T = T;
+                trial.smem = smem;
+            }
+            // warm-up then timed probe, each from the snapshot
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = cudaMemcpyAsync(ctx->arena, snap, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, ctx->stream);
+                if (e == cudaSuccess) e = launch_group(ctx, trial, trial.d_insts, (int)trial.members.size(), a, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            }
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && ms < best) { best = ms; bestT = T; }
+        }
+        if (e == cudaSuccess) {
+            if (ctx->engine == 0) st = lattice_group_shape(ctx, g, bestT);
+            else {
+                size_t smem = 0;
+                for (int k : g.members) {
+                    const GraphInst& I = ctx->gr[k];
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, bestT / 32, ctx->with_pool != 0);
+                    smem = std::max(smem, l.total);
+                }
+                g.T = bestT;
+                g.smem = smem;
+            }
+        }
+        if (threads_out) threads_out[gi] = g.T;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->arena, snap, ctx->arena_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaFreeAsync(snap, ctx->stream);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(PT_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    return st;
+}
+
+pt_status pt_run_cycles_graph(pt_ctx* ctx, int32_t n_cycles) {
+    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    if (n_cycles < 1) return fail(PT_EINVAL, "n_cycles must be >= 1");
+    cudaError_t e = cudaSuccess;
+    if (!ctx->gstream) {
+        e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(PT_ECUDA, "graph stream: %s", cudaGetErrorString(e));
+    }
+    if (!ctx->gexec || ctx->gcycles != n_cycles) {
+        drop_graph(ctx);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail(PT_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+        pt_status st = launch_on(ctx, kModeCycles, n_cycles, ctx->gstream);
+        e = cudaStreamEndCapture(ctx->gstream, &graph);
+        if (st != PT_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(PT_ECUDA, "graph: %s", cudaGetErrorString(e));
+        ctx->gcycles = n_cycles;
+    }
+    e = cudaEventRecord(ctx->gev_in, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->gstream, ctx->gev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ctx->gexec, ctx->gstream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->gev_out, ctx->gstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->gev_out, 0);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+pt_status pt_set_active(pt_ctx* ctx, int32_t inst, int32_t active) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int32_t v = active ? 1 : 0;
+    const int32_t* dst = ctx->engine == 0 ? ctx->lat[inst].active : ctx->gr[inst].active;
+    CK(cudaMemcpyAsync(const_cast<int32_t*>(dst), &v, 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+pt_status pt_set_instance(pt_ctx* ctx, int32_t inst, const pt_instance_desc* desc) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    if (!desc) return fail(PT_EINVAL, "desc is NULL");
+    if (ctx->engine != 0) return fail(PT_ENOTSUP, "slot replacement is implemented for the lattice engine");
+    s = validate(*desc, inst);
+    if (s != PT_OK) return s;
+    if (!is_lattice_desc(*desc, ctx->cfg)) return fail(PT_EINVAL, "the new instance needs the lattice engine");
+    if (desc->lattice_L != ctx->L[inst] || desc->n_replicas != ctx->R[inst])
+        return fail(PT_EINVAL, "slot %d holds L=%d, R=%d; the new instance must have the same shape",
+                    inst, ctx->L[inst], ctx->R[inst]);
+    LatHost h;
+    s = lattice_host(*desc, h, inst);
+    if (s != PT_OK) return s;
+    LatInst& I = ctx->lat[inst];
+    lattice_fill_inst(I, h, desc->instance_id, ctx->cfg.pool_size);
+    const LatOff& o = ctx->loff[inst];
+    uint8_t* b = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int32_t one = 1;
+    CK(cudaMemcpyAsync(b + o.itab, h.itab.data(), h.itab.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.sow, h.sow.data(), h.sow.size() * 2, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.wos, h.wos.data(), h.wos.size() * 2, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.thr, h.thr.data(), h.thr.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.beta, desc->beta, (size_t)h.R * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.prop, h.prop.data(), h.prop.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + o.eb, h.eb.data(), h.eb.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(b + o.cur, 0, (size_t)h.R * 4, st));
+    CK(cudaMemsetAsync(b + o.ctr, 0, sizeof(Counters), st));
+    CK(cudaMemsetAsync(b + o.st, 0, (size_t)4 * h.R * 8, st));
+    CK(cudaMemcpyAsync(b + o.active, &one, 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_lat + inst, &I, sizeof(LatInst), cudaMemcpyHostToDevice, st));
+    {
+        const Group& g = ctx->groups[ctx->group_of[inst]];
+        int pos = 0;
+        while (g.members[pos] != inst) ++pos;
+        CK(cudaMemcpyAsync(static_cast<LatInst*>(g.d_insts) + pos, &I, sizeof(LatInst), cudaMemcpyHostToDevice, st));
+    }
+    cudaError_t e = launch_lattice_init(ctx->d_lat + inst, 1, ctx->cfg.seed, st);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "init: %s", cudaGetErrorString(e));
+    s = launch_one(ctx, inst, kModeEnergy);
+    if (s != PT_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    return PT_OK;
+}
+
 pt_status pt_info(const pt_ctx* ctx, int32_t inst, int32_t info[6]) {
     if (!ctx || !info) return fail(PT_EINVAL, "NULL argument");
+    const Group& g = ctx->groups[(inst >= 0 && inst < ctx->n) ? ctx->group_of[inst] : 0];
     info[0] = ctx->n;
     info[1] = ctx->engine;
-    info[2] = ctx->threads;
-    info[3] = (int32_t)ctx->smem;
+    info[2] = g.T;
+    info[3] = (int32_t)g.smem;
     info[4] = (inst >= 0 && inst < ctx->n) ? ctx->R[inst] : ctx->totalR;
     info[5] = (inst >= 0 && inst < ctx->n) ? ctx->N[inst] : ctx->uniformN;
     return PT_OK;

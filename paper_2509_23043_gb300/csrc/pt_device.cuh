@@ -121,6 +121,7 @@ struct LatInst {
                            //         of the neighbour's word in colour-major order, bit 15 set
                            //         iff the bond is -1
     const uint16_t* pos;   // [N] colour-major position of each site
+    const int32_t* active; // nonzero: the instance takes part in launches
     int32_t* E;            // [W*32] per walker
     int16_t* sow;          // [W*32] slot of walker (-1: padding lane)
     int16_t* wos;          // [R] walker of slot
@@ -162,6 +163,7 @@ struct GraphInst {
     long long pstride;
     Counters* ctr;
     unsigned long long* stats;
+    const int32_t* active;   // nonzero: the instance takes part in launches
 };
 
 // Kernel modes

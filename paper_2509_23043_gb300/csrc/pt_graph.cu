@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
                                                      RunArgs a, int with_pool) {
     extern __shared__ __align__(16) uint8_t smem[];
     const GraphInst& I = insts[blockIdx.x];
+    if (!*I.active) return;
     const int nwarps = blockDim.x >> 5;
     GraphSmem S = carve_graph(smem, I, nwarps, with_pool != 0);
     const int tid = threadIdx.x, T = blockDim.x;
@@ -336,9 +337,12 @@ __global__ void graph_write_kernel(const GraphInst* __restrict__ insts, int inst
     }
 }
 
+cudaError_t configure_graph_kernels(int smem) {
+    return cudaFuncSetAttribute(graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_graph(const GraphInst* d_insts, int n, int threads, size_t smem,
                          const RunArgs& a, int with_pool, cudaStream_t stream) {
-    cudaFuncSetAttribute(graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     graph_kernel<<<n, threads, smem, stream>>>(d_insts, a, with_pool);
     return cudaGetLastError();
 }

@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
                                                       RunArgs a, int with_pool) {
     extern __shared__ __align__(16) uint8_t smem[];
     const LatInst& I = insts[blockIdx.x];
+    if (!*I.active) return;   // a free serving slot: the whole block leaves at once
     const int nwarps = blockDim.x >> 5;
     LatSmem S = carve_lattice(smem, I, nwarps, with_pool != 0);
     const int tid = threadIdx.x, T = blockDim.x;
@@ -596,21 +597,20 @@ __global__ void lattice_write_kernel(const LatInst* __restrict__ insts, int inst
 // ------------------------------------------------------------------------------------
 // host-callable launchers
 // ------------------------------------------------------------------------------------
+// The kernels' dynamic shared-memory limit is raised once, outside any stream capture.
+cudaError_t configure_lattice_kernels(int smem) {
+    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int threads, size_t smem,
                            const RunArgs& a, int with_pool, cudaStream_t stream) {
     switch (maxW) {
-    case 1:
-        cudaFuncSetAttribute(lattice_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        lattice_kernel<1><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
-        break;
-    case 2:
-        cudaFuncSetAttribute(lattice_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        lattice_kernel<2><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
-        break;
-    default:
-        cudaFuncSetAttribute(lattice_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        lattice_kernel<4><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
-        break;
+    case 1: lattice_kernel<1><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
+    case 2: lattice_kernel<2><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
+    default: lattice_kernel<4><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
     }
     return cudaGetLastError();
 }
