@@ -126,6 +126,12 @@ pt_status pt_load_proposals(pt_ctx *ctx, int32_t inst, int32_t replica, const in
 pt_status pt_load_proposals_packed(pt_ctx *ctx, const uint32_t *words, int32_t first,
                                    int32_t count);
 
+/* Bulk load of bit-packed pool entries for one instance: host words [count][R][ceil(N/32)]
+ * (same bit order as above) written to positions first .. first+count-1 of its slots.
+ * Synchronises (the host buffer may be freed on return). */
+pt_status pt_load_proposals_inst_packed(pt_ctx *ctx, int32_t inst, const uint32_t *words,
+                                        int32_t first, int32_t count);
+
 /* Inverse of pt_load_proposals_packed: copy pool positions first .. first+count-1 of every
  * instance and slot to host words in the same layout. Synchronises. */
 pt_status pt_read_proposals_packed(pt_ctx *ctx, uint32_t *words, int32_t first, int32_t count);

@@ -44,7 +44,7 @@ class _Config(C.Structure):
 
 
 EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed",
-           "pt_read_proposals_packed",
+           "pt_read_proposals_packed", "pt_load_proposals_inst_packed",
            "pt_capture_proposals", "pt_sweep", "pt_global_propose", "pt_exchange",
            "pt_run_cycles", "pt_energies", "pt_energies_device", "pt_read_state",
            "pt_read_state_noalloc",
@@ -70,6 +70,7 @@ def lib():
         "pt_load_proposals": [vp, i32, i32, vp, i32, i32],
         "pt_load_proposals_packed": [vp, vp, i32, i32],
         "pt_read_proposals_packed": [vp, vp, i32, i32],
+        "pt_load_proposals_inst_packed": [vp, i32, vp, i32, i32],
         "pt_capture_proposals": [vp, vp, i32],
         "pt_sweep": [vp, i32], "pt_global_propose": [vp], "pt_exchange": [vp],
         "pt_run_cycles": [vp, i32], "pt_energies": [vp, vp], "pt_energies_device": [vp, vp],
@@ -211,6 +212,13 @@ def load_proposals_packed(ctx: Context, words, first: int, count: int):
         _check(lib().pt_load_proposals_packed(ctx.handle, _ptr(arr), first, count))
     else:
         _check(lib().pt_load_proposals_packed(ctx.handle, C.c_void_p(w), first, count))
+
+
+def load_proposals_inst_packed(ctx: Context, inst: int, words, first: int = 0):
+    """words: uint32 [count][R][ceil(N/32)] bit strings for instance `inst`."""
+    _inst(ctx, inst)
+    w = _arr(words, np.uint32)
+    _check(lib().pt_load_proposals_inst_packed(ctx.handle, inst, _ptr(w), first, w.shape[0]))
 
 
 def read_proposals_packed(ctx: Context, words, first: int, count: int):

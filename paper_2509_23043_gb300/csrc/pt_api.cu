@@ -1211,6 +1211,22 @@ pt_status pt_load_proposals_packed(pt_ctx* ctx, const uint32_t* words, int32_t f
     return PT_OK;
 }
 
+pt_status pt_load_proposals_inst_packed(pt_ctx* ctx, int32_t inst, const uint32_t* words,
+                                        int32_t first, int32_t count) {
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    const int P = ctx->cfg.pool_size;
+    if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
+    if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
+    if (count == 0) return PT_OK;
+    if (!words) return fail(PT_EINVAL, "words is NULL");
+    const size_t row = (size_t)ctx->R[inst] * ctx->NW[inst] * 4;
+    CK(cudaMemcpy2DAsync(ctx->pool + ctx->slab_off[inst] + (size_t)first * ctx->slab, ctx->slab * 4,
+                         words, row, row, count, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
 pt_status pt_read_proposals_packed(pt_ctx* ctx, uint32_t* words, int32_t first, int32_t count) {
     if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
     const int P = ctx->cfg.pool_size;

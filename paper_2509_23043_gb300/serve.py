@@ -1,0 +1,269 @@
+"""Continuous-batching TAPT server on one GPU, and time-to-target accounting.
+
+Requests are lattice spin-glass instances that arrive over time. Each carries a proposal pool
+made offline by PT runs of this library (excluded from timing, as bank generation is in the
+paper's time-to-solution, Methods) and a reference lowest energy. The server keeps one
+context of pre-sized slots (one size class per L); a request is admitted into a free slot of
+its class when the device-memory budget allows. Its replica state and pool then stay on the
+device and it runs, cycle after cycle, together with every other admitted request in the
+same launches. When its best replica energy reaches the target, or the sweep budget is spent,
+it retires and frees its slot.
+
+Every request's random streams are keyed by its request id, and its counters start at zero
+on admission, so its trajectory (and its sweeps-to-target) is the same alone or in the mix.
+
+Time-to-solution follows the paper's definition of success within a run (Eq. for TTS and
+Supplementary S5): here one run per request, success = reaching E_ref + 0.1% |E_ref|.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (Config, create_instances, destroy, energies, load_proposals_inst_packed,
+               read_counters, read_proposals_packed, run_cycles, run_cycles_graph,
+               capture_proposals, set_active, set_instance, read_state)
+
+
+@dataclass
+class Request:
+    rid: int                    # request id; keys the random streams
+    instance: object            # lattice instance (instances.Instance)
+    betas: np.ndarray
+    prop: list
+    pool: np.ndarray | None     # uint32 [P][R][ceil(N/32)]
+    e_ref: int                  # reference lowest energy
+    arrival: float = 0.0        # seconds after the start of the stream
+    admitted: float = math.nan
+    finished: float = math.nan
+    sweeps: int = -1            # sweeps from admission to the target (-1: budget spent)
+    best: int = 0
+
+    @property
+    def L(self) -> int:
+        return int(self.instance.lattice_L)
+
+    @property
+    def target(self) -> int:
+        return int(math.floor(self.e_ref + 0.001 * abs(self.e_ref)))
+
+    @property
+    def tts(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Lattice:
+    """A placeholder periodic L^3 lattice (all bonds +1) for a free slot."""
+    L: int
+    n_spins: int = 0
+    edge_i: np.ndarray = field(default=None)
+    edge_j: np.ndarray = field(default=None)
+    edge_J: np.ndarray = field(default=None)
+    h: None = None
+    clamp: None = None
+    lattice_L: int = 0
+
+    def __post_init__(self):
+        L = self.L
+        n = np.arange(L ** 3)
+        x, y, z = n % L, (n // L) % L, n // (L * L)
+        nb = np.stack([((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z),
+                       x + L * (y + L * ((z + 1) % L))], axis=1)
+        self.n_spins = L ** 3
+        self.lattice_L = L
+        self.edge_i = np.repeat(n, 3).astype(np.int32)
+        self.edge_j = nb.reshape(-1).astype(np.int32)
+        self.edge_J = np.ones(3 * L ** 3, dtype=np.int32)
+
+
+def footprint_bytes(L: int, R: int, P: int) -> int:
+    """Device memory a slot of this shape holds: bit-packed state and its proposal pool."""
+    N = L ** 3
+    nw = (N + 31) // 32
+    W = (R + 31) // 32
+    return W * N * 4 + P * R * nw * 4 + N * 16
+
+
+def make_pools(insts, betas, ids, P: int, burnin: int, gap: int, seed: int = 0x9001,
+               stream=None) -> list[np.ndarray]:
+    """Pools of P configurations per slot from one PT run per instance (this library):
+    `burnin` sweeps, then a capture every `gap` sweeps. Returns uint32 [P][R][NW] each."""
+    cfg_g = Config(seed=seed)
+    gen = create_instances(insts, betas, cfg_g, instance_ids=[1_000_000 + i for i in ids],
+                           stream=stream)
+    dst = create_instances(insts, betas, Config(seed=seed, pool_size=P),
+                           instance_ids=list(ids), stream=stream)
+    run_cycles(gen, burnin)
+    for e in range(P):
+        run_cycles(gen, gap)
+        capture_proposals(dst, gen, e)
+    Rs = [len(b) for b in betas]
+    nws = [(int(i.n_spins) + 31) // 32 for i in insts]
+    slab = sum(R * nw for R, nw in zip(Rs, nws))
+    words = np.zeros((P, slab), dtype=np.uint32)
+    read_proposals_packed(dst, words, 0, P)
+    out, off = [], 0
+    for R, nw in zip(Rs, nws):
+        out.append(np.ascontiguousarray(words[:, off:off + R * nw].reshape(P, R, nw)))
+        off += R * nw
+    destroy(gen)
+    destroy(dst)
+    return out
+
+
+def reference_energies(insts, betas, ids, sweeps: int, chunk: int = 1000, seed: int = 0x5EF,
+                       stream=None) -> list[int]:
+    """Lowest energy met by a long PT run of every instance (checked every `chunk` sweeps)."""
+    ctx = create_instances(insts, betas, Config(seed=seed), instance_ids=[2_000_000 + i for i in ids],
+                           stream=stream)
+    best = [10 ** 9] * len(insts)
+    done = 0
+    while done < sweeps:
+        n = min(chunk, sweeps - done)
+        run_cycles(ctx, n)
+        done += n
+        for k, e in enumerate(energies(ctx)):
+            best[k] = min(best[k], int(e.min()))
+    destroy(ctx)
+    return best
+
+
+class TaptServer:
+    """Slots per lattice size L (all with R replicas and pools of P entries)."""
+
+    def __init__(self, slots_per_L: dict[int, int], betas: np.ndarray, prop: list,
+                 config: Config, hbm_budget: int | None = None, tick_cycles: int = 100,
+                 use_graph: bool = True, stream=None):
+        self.R = len(betas)
+        self.cfg = config
+        self.tick_cycles = tick_cycles
+        self.use_graph = use_graph
+        self.slot_L, placeholders, ids = [], [], []
+        for L, n in sorted(slots_per_L.items()):
+            for j in range(n):
+                self.slot_L.append(L)
+                placeholders.append(_Lattice(L))
+                ids.append(0xFFFF0000 + len(ids))
+        self.ctx = create_instances(placeholders, [betas] * len(placeholders), config,
+                                    prop_enabled=[prop] * len(placeholders), instance_ids=ids,
+                                    stream=stream)
+        for k in range(len(placeholders)):
+            set_active(self.ctx, k, False)
+        self.free = {L: [k for k, l in enumerate(self.slot_L) if l == L] for L in slots_per_L}
+        self.active: dict[int, Request] = {}
+        self.ticks_of: dict[int, int] = {}
+        self.budget = hbm_budget
+        self.used = 0
+
+    def _fp(self, req: Request) -> int:
+        return footprint_bytes(req.L, self.R, self.cfg.pool_size)
+
+    def try_admit(self, req: Request, now: float) -> bool:
+        if not self.free.get(req.L):
+            return False
+        if self.budget is not None and self.used + self._fp(req) > self.budget:
+            return False
+        k = self.free[req.L].pop()
+        set_instance(self.ctx, k, req.instance, req.betas, req.prop, instance_id=req.rid)
+        if req.pool is not None:
+            load_proposals_inst_packed(self.ctx, k, req.pool)
+        self.active[k] = req
+        self.ticks_of[k] = 0
+        self.used += self._fp(req)
+        req.admitted = now
+        return True
+
+    def tick(self, now_fn, budget_sweeps: int) -> list[Request]:
+        if not self.active:
+            return []
+        if self.use_graph:
+            run_cycles_graph(self.ctx, self.tick_cycles)
+        else:
+            run_cycles(self.ctx, self.tick_cycles)
+        E = energies(self.ctx)                      # synchronises: results of this tick
+        now = now_fn()
+        done = []
+        for k, req in list(self.active.items()):
+            self.ticks_of[k] += 1
+            sw = self.ticks_of[k] * self.tick_cycles * self.cfg.sweeps_per_cycle
+            req.best = int(E[k].min())
+            if req.best <= req.target or sw >= budget_sweeps:
+                req.sweeps = sw if req.best <= req.target else -1
+                req.finished = now
+                set_active(self.ctx, k, False)
+                self.free[req.L].append(k)
+                self.used -= self._fp(req)
+                del self.active[k]
+                done.append(req)
+        return done
+
+    def serve(self, requests: list[Request], budget_sweeps: int) -> list[Request]:
+        """Admit requests at their arrival times (in order), run until all retire."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        waiting: list[Request] = []
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        finished: list[Request] = []
+        while pending or waiting or self.active:
+            t = now()
+            while pending and pending[0].arrival <= t:
+                waiting.append(pending.pop(0))
+            still = []
+            for req in waiting:
+                if not self.try_admit(req, now()):
+                    still.append(req)
+            waiting = still
+            if not self.active:
+                if pending:
+                    time.sleep(max(0.0, min(0.002, pending[0].arrival - now())))
+                continue
+            finished += self.tick(now, budget_sweeps)
+        return finished
+
+
+def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int = 100,
+              stream=None) -> Request:
+    """One request in its own context and launch (plain PT when config.propose_every == 0)."""
+    ctx = create_instances([req.instance], [req.betas], config, prop_enabled=[req.prop],
+                           instance_ids=[req.rid], stream=stream)
+    if config.pool_size and req.pool is not None:
+        load_proposals_inst_packed(ctx, 0, req.pool)
+    t0 = time.perf_counter()
+    sw = 0
+    req.admitted = 0.0
+    while True:
+        run_cycles(ctx, tick_cycles)
+        sw += tick_cycles * config.sweeps_per_cycle
+        req.best = int(energies(ctx)[0].min())
+        if req.best <= req.target or sw >= budget_sweeps:
+            req.sweeps = sw if req.best <= req.target else -1
+            break
+    req.finished = time.perf_counter() - t0
+    req.arrival = 0.0
+    destroy(ctx)
+    return req
+
+
+def summarize(reqs: list[Request]) -> dict:
+    """p50/p99 time-to-solution (s and sweeps) over the solved requests, and the fitted TTS
+    exponent k of log TTS = a + k L (least squares over the per-L medians, as in Eq. for
+    TTS(n) = A exp(k n) of Supplementary S5)."""
+    solved = [r for r in reqs if r.sweeps >= 0]
+    out = {"requests": len(reqs), "solved": len(solved)}
+    if not solved:
+        return out
+    t = np.array([r.tts for r in solved])
+    s = np.array([r.sweeps for r in solved], dtype=np.float64)
+    out.update({"p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+                "p50_sweeps": float(np.percentile(s, 50)), "p99_sweeps": float(np.percentile(s, 99))})
+    Ls = sorted({r.L for r in solved})
+    if len(Ls) >= 2:
+        med = [float(np.median([r.tts for r in solved if r.L == L])) for L in Ls]
+        medsw = [float(np.median([r.sweeps for r in solved if r.L == L])) for L in Ls]
+        out["k_seconds_per_L"] = float(np.polyfit(Ls, np.log(med), 1)[0])
+        out["k_sweeps_per_L"] = float(np.polyfit(Ls, np.log(medsw), 1)[0])
+    return out
