@@ -39,13 +39,17 @@ sys.path.insert(0, str(ROOT))
 METRIC = "spin-flip attempts/ns; p50/p99 time-to-target of batched served TAPT vs plain PT"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-INT_LANES_PER_SM = 128   # 4 SM sub-partitions x 32 lanes issue one integer op per clock
+# The integer ALU pipe (logic, add, shift, compare) takes 2 warp instructions per clock per
+# SM, i.e. 64 lanes: ncu reports the pipe's share of its peak, and against the SM's issue
+# rate (4 warp instructions per clock) that peak is half the issue rate. Multiplies run on
+# the separate FMA pipe and are not counted against it.
+ALU_LANES_PER_SM = 64
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--instances", type=int, default=256)
@@ -59,6 +63,11 @@ def parse():
     p.add_argument("--threads", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-L", default="6,7,8,9,10,11,12")
+    p.add_argument("--serve-budget", type=int, default=20000)
+    p.add_argument("--serve-gap-ms", type=float, default=4.0)
     p.add_argument("--cpu-sample-instances", type=int, default=16)
     p.add_argument("--cpu-sample-sweeps", type=int, default=60)
     return p.parse_args()
@@ -170,22 +179,34 @@ def expected_plane_blocks(ctx, args, sample=4):
     return float(np.mean(blocks))
 
 
-def ops_per_word(e_blocks: float) -> float:
-    # 6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
-    # + 4.5 (energy count in the last colour, half the words) + per plane block:
-    # 40 (Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs)) + 4 x 5 compare
-    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (40 + 20)
+def alu_ops_per_word(e_blocks: float) -> float:
+    """Algorithmic integer-ALU operations of one bit-sliced word update (32 attempts):
+    6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
+    + 4.5 (energy count in the last colour, half the words) + per plane block: 20 (the
+    three-input XORs of Philox4x32-10's 10 rounds; its 20 wide multiplies run on the FMA pipe)
+    + 4 planes x 5 (compare)."""
+    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 20)
+
+
+PROFILE = ROOT / "profiles" / "lattice_kernel_batched_tapt_L10_R32_B256.md"
 
 
 def load_traffic(source_hash):
-    f = ROOT / "profiles" / "lattice_kernel_traffic.json"
-    if not f.exists():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel sources (lines "- source_sha256: ..." and "- dram_bytes_per_launch: ...")."""
+    if not PROFILE.exists():
+        return None
+    kv = {}
+    for line in PROFILE.read_text().splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != source_hash:
         return None
     try:
-        d = json.loads(f.read_text())
-    except Exception:
+        return {"dram_bytes_per_launch": int(kv["dram_bytes_per_launch"])}
+    except (KeyError, ValueError):
         return None
-    return d if d.get("source_sha256") == source_hash else None
 
 
 def source_hash():
@@ -193,6 +214,48 @@ def source_hash():
     for name in ("pt_lattice.cu", "pt_device.cuh", "pt_layout.h"):
         h.update((ROOT / "paper_2509_23043_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()
+
+
+# ------------------------------------------------------------------------------ served stream
+def served_stream(args, stream):
+    """Poisson arrivals of EA +-J requests (L uniform over --serve-L), each run by TAPT in the
+    continuous-batching server to within 0.1% of its reference lowest energy or the sweep
+    budget; the same requests run one instance per launch with plain PT (no proposals).
+    Pools (PT runs of this library) and reference energies (long PT runs) are made first and
+    are not part of any time-to-solution."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    from paper_2509_23043_gb300 import serve as S
+    g = np.random.default_rng(0x5E7E)
+    Ls = [int(x) for x in args.serve_L.split(",")]
+    R, P = 32, 256
+    betas = I.geometric_betas(0.1, 3.0, R)
+    prop = [1] * (R - 2) + [0, 0]
+    n = args.serve_requests
+    req_L = [int(g.choice(Ls)) for _ in range(n)]
+    insts = [I.ea_instance(L, seed=0x5E5E, index=k) for k, L in enumerate(req_L)]
+    ids = [10_000 + k for k in range(n)]
+    t0 = time.perf_counter()
+    pools = S.make_pools(insts, [betas] * n, ids, P, burnin=10_000, gap=20, stream=stream)
+    eref = S.reference_energies(insts, [betas] * n, ids, sweeps=200_000, chunk=2000, stream=stream)
+    prep_s = time.perf_counter() - t0
+    arrivals = np.cumsum(g.exponential(args.serve_gap_ms * 1e-3, size=n))
+    arrivals -= arrivals[0]
+    mk = lambda k, a: S.Request(ids[k], insts[k], betas, prop, pools[k], eref[k], arrival=float(a))
+    cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+    slots = {L: 4 for L in Ls}
+    srv = S.TaptServer(slots, betas, prop, cfg, hbm_budget=None, tick_cycles=100, stream=stream)
+    served = srv.serve([mk(k, arrivals[k]) for k in range(n)], budget_sweeps=args.serve_budget)
+    cfg_pt = pt.Config(seed=0x7A972509, propose_every=0, pool_size=0)
+    alone = [S.run_alone(mk(k, 0.0), cfg_pt, budget_sweeps=args.serve_budget, tick_cycles=100,
+                         stream=stream) for k in range(n)]
+    return {"workload": f"{n} requests, L uniform in {{{args.serve_L}}}, R={R}, Poisson arrivals "
+                        f"(mean gap {args.serve_gap_ms} ms), target E_ref + 0.1%|E_ref| "
+                        f"(E_ref: best of a 2e5-sweep PT run), budget {args.serve_budget} sweeps, "
+                        f"pools P={P} from 1e4+{20 * P}-sweep PT runs (untimed, {prep_s:.1f} s)",
+            "served_tapt": S.summarize(served),
+            "plain_pt_one_instance_per_launch": S.summarize(alone),
+            "slots_per_L": 4}
 
 
 # ------------------------------------------------------------------------------ CPU oracle
@@ -372,16 +435,20 @@ def main():
 
     # ---------------- roofline of the dominant kernel (the fused cycle kernel = the whole step)
     words_per_step = B * args.L ** 3 * ((args.R + 31) // 32) * spc
-    ops = ops_per_word(e_blocks) * words_per_step
+    ops = alu_ops_per_word(e_blocks) * words_per_step
     achieved = ops / (ms_step * 1e-3) / 1e12
-    peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = SM_COUNT * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     tr = load_traffic(source_hash())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                "kernel": "lattice_kernel", "ops_per_attempt": ops_per_word(e_blocks) / 32,
+                "kernel": "lattice_kernel", "alu_ops_per_attempt": alu_ops_per_word(e_blocks) / 32,
                 "plane_blocks_per_word": e_blocks,
-                "peak_basis": "152 SMs x 128 int lanes x 2070 MHz (nominal)"}
+                "peak_basis": "152 SMs x 64 integer-ALU lanes x 2070 MHz (nominal)"}
+
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = served_stream(args, stream.cuda_stream)
 
     cpu = None
     if cpu_pool is not None:
@@ -405,7 +472,7 @@ def main():
                        "pool": f"PT runs of this library: {args.pool_burnin} burn-in sweeps, "
                                f"then one capture every {args.pool_gap} sweeps (untimed)",
                        "threads_per_block": pt.info(ctx)["threads"]},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
             "gpu_launches": args.steps, "clocks": clk.summary(),
         }), flush=True)
     if dist:

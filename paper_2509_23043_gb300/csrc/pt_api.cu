@@ -17,7 +17,7 @@
 #include "pt_layout.h"
 
 namespace pt {
-cudaError_t launch_lattice(const LatInst*, int, int, int, size_t, const RunArgs&, int, cudaStream_t);
+cudaError_t launch_lattice(const LatInst*, int, int, int, int, size_t, const RunArgs&, int, cudaStream_t);
 cudaError_t launch_lattice_init(const LatInst*, int, uint64_t, cudaStream_t);
 cudaError_t launch_lattice_capture(const LatInst*, const LatInst*, int, int, cudaStream_t);
 cudaError_t launch_lattice_read(const LatInst*, int, int8_t*, int, cudaStream_t);
@@ -203,9 +203,15 @@ RunArgs make_args(const pt_ctx* c, int mode, int nn) {
 
 cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, int count,
                          const RunArgs& a, cudaStream_t s) {
-    if (c->engine == 0)
-        return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, g.T, g.smem, a,
+    if (c->engine == 0) {
+        // a thread's bond count per walker: at most 6 per word it updates in the colour
+        // classes that count (the last one for even L, the last two for odd L)
+        const int per_thread = (g.maxitems / std::max(g.maxW, 1) + g.T - 1) / g.T;
+        const int counting = (c->L[g.members[0]] % 2 == 0) ? 1 : 2;
+        const int kb4 = 6 * per_thread * counting < 16 ? 1 : 0;
+        return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, kb4, g.T, g.smem, a,
                               c->with_pool, s);
+    }
     return launch_graph(static_cast<const GraphInst*>(d_insts), count, g.T, g.smem, a, c->with_pool, s);
 }
 

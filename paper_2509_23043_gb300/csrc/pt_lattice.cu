@@ -30,7 +30,8 @@
 
 namespace pt {
 
-constexpr int KB = 8;  // vertical counter bits: up to 255 bond counts per thread per word
+// KB: vertical counter bits (a template parameter): a thread's count of unsatisfied bonds
+// per walker, over its words of the last colour class, must stay below 2^KB.
 
 // Scalars of the instance held in registers for the whole launch.
 struct LP {
@@ -67,7 +68,6 @@ struct LatSmem {
     uint32_t* st;      // [4][R]   statistics of this launch
     int16_t* sow;      // [2][W*32] slot of walker, double-buffered
     int16_t* wos;      // [2][W*32] walker of slot, double-buffered
-    int16_t* wsow;     // [nwarps][W*32] each warp's view of the new slot of walker
 };
 
 __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I, int nwarps,
@@ -93,29 +93,29 @@ __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I
     S.st = reinterpret_cast<uint32_t*>(base + l.st);
     S.sow = reinterpret_cast<int16_t*>(base + l.sow);
     S.wos = reinterpret_cast<int16_t*>(base + l.wos);
-    S.wsow = reinterpret_cast<int16_t*>(base + l.wsow);
     return S;
 }
 
-// Bit-sliced thresholds of every walker block from a slot-of-walker map:
-// tw[wb*32 + k] = {plane k of T(dE=4), of T(dE=8), of T(dE=12)} with lane b taking the
-// thresholds of the slot of walker 32 wb + b. This warp writes planes warp, warp+nwarps, ...
-__device__ __forceinline__ void rebuild_planes(const LP& P, LatSmem& S, const int16_t* sow) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+// Bit-sliced thresholds of every walker block from a slot-of-walker map, by one warp:
+// tw[wb*32 + k] = {plane k of T(dE=4), of T(dE=8), of T(dE=12)} over the walkers 32 wb + b.
+// Lane b holds its walker's three thresholds; a 32x32 bit transpose of each (bit 31-k of
+// lane b -> bit b of lane k) gives the planes, lane k storing plane k.
+__device__ __forceinline__ void rebuild_planes_warp(const LP& P, LatSmem& S, const int16_t* sow) {
+    const int lane = threadIdx.x & 31;
     for (int wb = 0; wb < P.W; ++wb) {
         const int w = wb * 32 + lane;
         const int slot = (w < P.R) ? sow[w] : -1;
         const uint4 t = slot >= 0 ? S.thr[slot] : make_uint4(0u, 0u, 0u, 0u);
-        for (int k = warp; k < 32; k += nwarps) {
-            const uint32_t bx = __ballot_sync(kFull, (t.x >> (31 - k)) & 1u);
-            const uint32_t by = __ballot_sync(kFull, (t.y >> (31 - k)) & 1u);
-            const uint32_t bz = __ballot_sync(kFull, (t.z >> (31 - k)) & 1u);
-            if (lane == 0) S.tw[wb * 32 + k] = make_uint4(bx, by, bz, 0u);
-        }
+        // plane k is bit 31-k: reverse the bits so that the transpose puts plane k in lane k
+        const uint32_t x = warp_transpose32(__brev(t.x), lane);
+        const uint32_t y = warp_transpose32(__brev(t.y), lane);
+        const uint32_t z = warp_transpose32(__brev(t.z), lane);
+        S.tw[wb * 32 + lane] = make_uint4(x, y, z, 0u);
     }
 }
 
 // Add the 3-bit per-walker value (n2 n1 n0) to a bit-sliced counter.
+template <int KB>
 __device__ __forceinline__ void vc_add3(uint32_t (&c)[KB], uint32_t n0, uint32_t n1, uint32_t n2) {
     uint32_t carry = c[0] & n0;
     c[0] ^= n0;
@@ -147,26 +147,36 @@ __device__ __forceinline__ void compare4(const uint4& r, const uint4* tw, uint32
     }
 }
 
-__device__ __forceinline__ uint32_t nb_word(const uint8_t* base, uint32_t e16) {
-    return *reinterpret_cast<const uint32_t*>(base + (e16 & 0x7FFFu));
-}
-__device__ __forceinline__ uint32_t nb_sign(uint32_t e16) {
-    return 0u - ((e16 >> 15) & 1u);
+__device__ __forceinline__ uint32_t nb_word(const uint8_t* base, uint32_t off) {
+    return *reinterpret_cast<const uint32_t*>(base + off);
 }
 
-// The six "bond unsatisfied" words s ^ n_d ^ Jneg_d of a table entry.
+// PTX prmt in its generic mode: a selector nibble with its top bit set replicates the sign
+// bit of the selected byte over the output byte. (CUDA's __byte_perm documents only the low
+// three selector bits, so the mode is requested through PTX.)
+template <unsigned SEL>
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t x) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(SEL));
+    return r;
+}
+
+// The six "bond unsatisfied" words s ^ n_d ^ Jneg_d of a table entry. A bond's sign is the
+// top bit of its 16-bit field (byte 1 or byte 3 of the word); replicating that byte's sign
+// over all four bytes gives the all-ones / all-zeros word Jneg_d in one operation.
 __device__ __forceinline__ void bond_words(const uint8_t* sp, const uint4& it, uint32_t s,
                                            uint32_t (&u)[6]) {
-    u[0] = s ^ nb_word(sp, it.y) ^ nb_sign(it.y);
-    u[1] = s ^ nb_word(sp, it.y >> 16) ^ nb_sign(it.y >> 16);
-    u[2] = s ^ nb_word(sp, it.z) ^ nb_sign(it.z);
-    u[3] = s ^ nb_word(sp, it.z >> 16) ^ nb_sign(it.z >> 16);
-    u[4] = s ^ nb_word(sp, it.w) ^ nb_sign(it.w);
-    u[5] = s ^ nb_word(sp, it.w >> 16) ^ nb_sign(it.w >> 16);
+    u[0] = s ^ nb_word(sp, it.y & 0x7FFFu) ^ prmt_sign<0x9999u>(it.y);
+    u[1] = s ^ nb_word(sp, (it.y >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.y);
+    u[2] = s ^ nb_word(sp, it.z & 0x7FFFu) ^ prmt_sign<0x9999u>(it.z);
+    u[3] = s ^ nb_word(sp, (it.z >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.z);
+    u[4] = s ^ nb_word(sp, it.w & 0x7FFFu) ^ prmt_sign<0x9999u>(it.w);
+    u[5] = s ^ nb_word(sp, (it.w >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.w);
 }
 
 // Energy bookkeeping of one updated word: add its new count of unsatisfied bonds to
 // lower-colour neighbours to the thread's vertical counter.
+template <int KB>
 __device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t flags,
                                                   const uint32_t (&u)[6], uint32_t b0,
                                                   uint32_t b1, uint32_t b2, uint32_t flip) {
@@ -192,7 +202,7 @@ __device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t 
 }
 
 // One sweep: colour classes in order, all (site, walker-block) words of a class in parallel.
-template <int MAXW>
+template <int MAXW, int KB>
 __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const RunArgs& a,
                                               uint32_t sweep_idx, bool flip_on, bool energy_on,
                                               uint32_t (&cnt)[MAXW][KB]) {
@@ -251,7 +261,8 @@ __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const Run
 }
 
 // Reduce the vertical counters into the bond counts Eacc[p] (per walker); ends synchronised.
-template <int MAXW>
+// The KB transposes of a walker block are independent and run interleaved.
+template <int MAXW, int KB>
 __device__ __forceinline__ void lattice_count_reduce(const LP& P, LatSmem& S,
                                                      uint32_t (&cnt)[MAXW][KB], int p) {
     const int lane = threadIdx.x & 31;
@@ -259,13 +270,13 @@ __device__ __forceinline__ void lattice_count_reduce(const LP& P, LatSmem& S,
 #pragma unroll
     for (int wb = 0; wb < MAXW; ++wb) {
         if (wb >= P.W) break;
+        uint32_t tx[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) tx[j] = warp_transpose32(cnt[wb][j], lane);
         uint32_t acc = 0;
 #pragma unroll
         for (int j = 0; j < KB; ++j) {
-            if (__any_sync(kFull, cnt[wb][j] != 0u)) {
-                const uint32_t tx = warp_transpose32(cnt[wb][j], lane);
-                acc += (uint32_t)__popc(tx) << j;
-            }
+            acc += (uint32_t)__popc(tx[j]) << j;
             cnt[wb][j] = 0u;
         }
         if (acc) atomicAdd(&acc_out[wb * 32 + lane], (int)acc);
@@ -282,9 +293,9 @@ __device__ __forceinline__ void lattice_store_energies(const LP& P, LatSmem& S, 
 }
 
 // One exchange event (Eq. P_swap) on the labels of buffer q with energies E = 2 Ecount - 3N
-// (Ecount != nullptr) or S.E: warp 0 decides every pair and writes the new labels to buffer
-// q^1 and the statistics; then every warp rebuilds its share of the threshold planes from
-// the new slot-of-walker map. The caller synchronises afterwards.
+// (Ecount != nullptr) or S.E: warp 0 decides every pair, writes the new labels to buffer q^1
+// and the statistics, and rebuilds the threshold planes from the new slot-of-walker map.
+// The caller synchronises afterwards.
 __device__ void lattice_exchange(const LP& P, LatSmem& S, const RunArgs& a, long long n_ex,
                                  int q, const int32_t* Ecount) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -317,9 +328,9 @@ __device__ void lattice_exchange(const LP& P, LatSmem& S, const RunArgs& a, long
                 sow_n[wc] = (int16_t)r;
             }
         }
+        __syncwarp();
+        rebuild_planes_warp(P, S, sow_n);
     }
-    __syncthreads();
-    rebuild_planes(P, S, sow_n);
 }
 
 // One proposal event (Algorithm 1, Eq. P_accept) with energies in S.E and labels of buffer q.
@@ -406,7 +417,7 @@ __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
     __syncthreads();
 }
 
-template <int MAXW>
+template <int MAXW, int KB>
 __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict__ insts,
                                                       RunArgs a, int with_pool) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     }
     long long sweeps = I.ctr->sweeps, n_ex = I.ctr->n_ex, n_prop = I.ctr->n_prop;
     __syncthreads();
-    rebuild_planes(P, S, S.sow);
+    if (tid < 32) rebuild_planes_warp(P, S, S.sow);
     __syncthreads();
 
     uint32_t cnt[MAXW][KB];
@@ -460,19 +471,19 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     int q = 0;   // label buffer holding the current slot <-> walker maps
 
     if (a.mode & kModeEnergy) {
-        lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, false, true, cnt);
-        lattice_count_reduce<MAXW>(P, S, cnt, p);
+        lattice_sweep<MAXW, KB>(P, S, a, (uint32_t)sweeps, false, true, cnt);
+        lattice_count_reduce<MAXW, KB>(P, S, cnt, p);
         lattice_store_energies(P, S, p);
         p ^= 1;
         __syncthreads();
     }
     if (a.mode & kModeSweeps) {
         for (int k = 0; k < a.n; ++k) {
-            lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, true, k == a.n - 1, cnt);
+            lattice_sweep<MAXW, KB>(P, S, a, (uint32_t)sweeps, true, k == a.n - 1, cnt);
             ++sweeps;
         }
         if (a.n > 0) {
-            lattice_count_reduce<MAXW>(P, S, cnt, p);
+            lattice_count_reduce<MAXW, KB>(P, S, cnt, p);
             lattice_store_energies(P, S, p);
             p ^= 1;
             __syncthreads();
@@ -491,10 +502,10 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
             for (int m = 0; m < a.M; ++m) {
-                lattice_sweep<MAXW>(P, S, a, (uint32_t)sweeps, true, m == a.M - 1, cnt);
+                lattice_sweep<MAXW, KB>(P, S, a, (uint32_t)sweeps, true, m == a.M - 1, cnt);
                 ++sweeps;
             }
-            lattice_count_reduce<MAXW>(P, S, cnt, p);
+            lattice_count_reduce<MAXW, KB>(P, S, cnt, p);
             ++n_ex;
             if (proposal_due(sweeps, a)) {
                 lattice_store_energies(P, S, p);
@@ -599,19 +610,28 @@ __global__ void lattice_write_kernel(const LatInst* __restrict__ insts, int inst
 // ------------------------------------------------------------------------------------
 // The kernels' dynamic shared-memory limit is raised once, outside any stream capture.
 cudaError_t configure_lattice_kernels(int smem) {
-    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1, 4>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<1, 8>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 4>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 8>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4, 8>, A, smem);
     return e;
 }
 
-cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int threads, size_t smem,
-                           const RunArgs& a, int with_pool, cudaStream_t stream) {
-    switch (maxW) {
-    case 1: lattice_kernel<1><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
-    case 2: lattice_kernel<2><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
-    default: lattice_kernel<4><<<n, threads, smem, stream>>>(d_insts, a, with_pool); break;
-    }
+// kb4: the group's counts fit in 4 bits (at most two words per thread per colour class).
+cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
+                           size_t smem, const RunArgs& a, int with_pool, cudaStream_t stream) {
+    if (maxW == 1 && kb4)
+        lattice_kernel<1, 4><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else if (maxW == 1)
+        lattice_kernel<1, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else if (maxW == 2 && kb4)
+        lattice_kernel<2, 4><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else if (maxW == 2)
+        lattice_kernel<2, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else
+        lattice_kernel<4, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ PT_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct LatLayout {
     size_t tw, spins, itab, beta, dbeta, fbeta, fdbeta, thr, prop, ebits, stage, us, cursor, accr, E, Eacc, st, sow, wos,
-        wsow, total;
+        total;
 };
 
 PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool) {
@@ -42,7 +42,6 @@ PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, b
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
     l.sow = o;    o = align16(o + 2 * WR * 2);
     l.wos = o;    o = align16(o + 2 * WR * 2);
-    l.wsow = o;   o = align16(o + (size_t)nwarps * WR * 2);
     l.total = o;
     return l;
 }
