@@ -210,9 +210,15 @@ def load_traffic(source_hash):
 
 
 def source_hash():
+    """sha256 of the lattice kernel's sources with comments and blank lines removed, so a
+    comment edit does not invalidate the profile's counters."""
+    import re
     h = hashlib.sha256()
     for name in ("pt_lattice.cu", "pt_device.cuh", "pt_layout.h"):
-        h.update((ROOT / "paper_2509_23043_gb300" / "csrc" / name).read_bytes())
+        text = (ROOT / "paper_2509_23043_gb300" / "csrc" / name).read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()
 
 
@@ -346,6 +352,7 @@ def main():
         cpu_pool = mp.get_context("spawn").Pool(min(os.cpu_count() or 1, args.cpu_sample_instances))
     import torch
     import paper_2509_23043_gb300 as pt
+    from paper_2509_23043_gb300 import shard
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -353,7 +360,7 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     B = args.instances
-    first = rank * B
+    first = shard.weak_shard(rank, world, B).start
     insts, betas, prop, ids = workload(args, first, B)
     cfg = make_config(args, args.pool_size)
     ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids,
@@ -389,13 +396,9 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.job_ms(sum(a.elapsed_time(b) for a, b in ev), dist, device="cuda")
     ms_step = ms / args.steps
-    value = attempts_per_step * world * args.steps / (ms * 1e6)
+    value = shard.job_rate(attempts_per_step * args.steps, world, ms)
 
     # ---------------- end to end through the public API: host pool window in, energies out
     e2e = None
@@ -428,8 +431,8 @@ def main():
             ehost.copy_(eout, non_blocking=True)
             ev2[k][1].record(stream)
             torch.cuda.synchronize()
-        ms2 = sum(a.elapsed_time(b) for a, b in ev2)
-        e2e = {"value": attempts_per_step * world * args.steps / (ms2 * 1e6), "unit": "attempts/ns",
+        ms2 = shard.job_ms(sum(a.elapsed_time(b) for a, b in ev2), dist, device="cuda")
+        e2e = {"value": shard.job_rate(attempts_per_step * args.steps, world, ms2), "unit": "attempts/ns",
                "h2d_bytes_per_step": per_step_entries * slab * 4,
                "d2h_bytes_per_step": B * args.R * 4}
 

@@ -87,7 +87,7 @@ typedef struct {
  *                    proposal schedule of pt_run_cycles: after a cycle that ends at sweep
  *                    count s, a proposal event happens iff propose_every > 0, s >= start,
  *                    (stop <= 0 or s <= stop) and (s - start) % propose_every == 0.
- *                    (Fig. 3: start 100, then every sweep; Fig. S5: stop after 100.)
+ *                    (Fig. 3: start 100, then every sweep; Fig. S3: stop after 100.)
  *  pool_size         P, proposal-pool capacity per (instance, slot); 0 = no pools.
  *  seed              64-bit key of every random stream.
  *  threads_per_block 0 = automatic choice; else a multiple of 32 in [32, 512] (lattice
@@ -205,7 +205,7 @@ pt_status pt_write_state(pt_ctx *ctx, int32_t inst, const int8_t *spins,
  * int32 [R] (may be NULL). Synchronises. */
 pt_status pt_read_counters(pt_ctx *ctx, int32_t inst, int64_t counters[3], int32_t *cursors);
 
-/* Acceptance counters of one instance (Figs. S7, S8): swaps accepted/attempted per pair
+/* Acceptance counters of one instance (Figs. S5, S6): swaps accepted/attempted per pair
  * (slot r with r+1) int64 [R-1], proposals accepted/attempted per slot int64 [R]. Any may be
  * NULL. Synchronises. */
 pt_status pt_read_stats(pt_ctx *ctx, int32_t inst, int64_t *swap_acc, int64_t *swap_att,

@@ -22,9 +22,8 @@
 // transposes and popcounts.
 //
 // Per cycle the block synchronises four times: after each colour class, after the energy
-// counts, and after the bit-sliced thresholds are rebuilt. Every warp evaluates the exchange
-// decisions itself (they are deterministic) so that it can rebuild its share of the
-// threshold planes without waiting; warp 0 alone commits the new labels.
+// counts, and after the exchange. Warp 0 decides the exchange pairs, commits the new labels
+// and rebuilds the bit-sliced threshold planes while the other warps wait.
 #include "pt_device.cuh"
 #include "pt_layout.h"
 

@@ -101,7 +101,7 @@ def _gate_instance(Jd, h):
 
 
 def test_and_gate_truth_table():
-    # Fig. S9: states (A,B,C) = 0, 2, 4, 7 (binary order, A most significant) are the four
+    # Fig. S7: states (A,B,C) = 0, 2, 4, 7 (binary order, A most significant) are the four
     # minimum-energy states; the hand value is E = -3, and (1,1,0) has E = +1.
     g = _gate_instance(I.AND_J, I.AND_H)
     E = {}
