@@ -42,7 +42,7 @@ typedef enum {
 
 typedef struct pt_ctx pt_ctx;   /* opaque; owns all device memory of a batch */
 
-/* One Ising instance: the "Ising energy function E" input of Algorithm 1, with its
+/* One Ising instance: the energy-function input of Algorithm 1, with its
  * temperature ladder {beta_r} and proposal-enabled set R_prop.
  *  instance_id   caller's identifier; it keys every random stream of the instance, so an
  *                instance evolves identically whatever batch or position it runs in.
@@ -108,7 +108,7 @@ typedef struct {
 /* Create a batch of n >= 1 instances (all lattice+Metropolis+J=+-1 without field or clamp,
  * or all otherwise: one engine per context), allocate its device memory (cudaMallocAsync
  * on `cuda_stream`, a cudaStream_t or NULL for the legacy stream), draw the random initial
- * state of every replica (Algorithm 1, "Initialize replica states randomly") and compute
+ * state of every replica (Algorithm 1, initialisation) and compute
  * its energies. On success *out owns everything; release it with pt_destroy. */
 pt_status pt_create_instances(pt_ctx **out, const pt_instance_desc *descs, int32_t n,
                               const pt_config *cfg, void *cuda_stream);
@@ -142,7 +142,7 @@ pt_status pt_read_proposals_packed(pt_ctx *ctx, uint32_t *words, int32_t first, 
 pt_status pt_capture_proposals(pt_ctx *dst, const pt_ctx *src, int32_t entry);
 
 /* n_sweeps local sweeps of every replica of every instance (Methods: one sweep updates
- * every free spin once), then the exact energy of every replica ("Compute E(S_r)"). */
+ * every free spin once), then the exact energy of every replica (the energy step of Algorithm 1). */
 pt_status pt_sweep(pt_ctx *ctx, int32_t n_sweeps);
 
 /* One global-proposal event for every instance: for each r in R_prop, take the next pool

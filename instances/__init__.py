@@ -32,7 +32,7 @@ def _rng(*keys: int) -> np.random.Generator:
 
 @dataclass
 class Instance:
-    """One Ising instance as plain arrays (the input of Algorithm 1, "Ising energy function E").
+    """One Ising instance as plain arrays (the energy-function input of Algorithm 1).
 
     edge_i, edge_j, edge_J: undirected couplings, one row per edge (parallel edges allowed).
     h: local fields or None. clamp: per-spin 0 (free) or +-1 (clamped), or None.

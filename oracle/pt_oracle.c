@@ -283,7 +283,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     }
 
     /* state: walker r starts in slot r; spins from the init stream; clamps applied
-     * (Algorithm 1: "Initialize replica states randomly") */
+     * (Algorithm 1, initialisation: uniformly random replicas) */
     o->spins = (int8_t *)xcalloc((size_t)n_replicas * n_spins, 1);
     o->E = (int32_t *)xcalloc((size_t)n_replicas, 4);
     o->walker = (int32_t *)xcalloc((size_t)n_replicas, 4);
@@ -366,7 +366,7 @@ static void one_sweep(or_inst *o) {
 
 void or_sweeps(or_inst *o, int32_t n) {
     for (int32_t k = 0; k < n; ++k) one_sweep(o);
-    recompute_energies(o);  /* Algorithm 1: "Compute E(S_r) for all replicas" */
+    recompute_energies(o);  /* Algorithm 1: exact energy of every replica */
 }
 
 /* Global proposals (Algorithm 1, Eq. P_accept). */

@@ -14,7 +14,7 @@
 // plane k of the 32 walkers' u is one Philox output word, so planes are only drawn while some
 // walker is still undecided (the result is the full 32-bit u < T comparison).
 //
-// Energy (Algorithm 1: "Compute E(S_r)"). E = 2 U - 3N with U the number of unsatisfied
+// Energy (Algorithm 1, the energy step of a cycle). E = 2 U - 3N with U the number of unsatisfied
 // bonds. Every bond joins a site to a neighbour of a lower colour exactly once, so U is
 // counted, from scratch, in the last sweep of a cycle: each site of colour c > 0 counts its
 // bonds to lower-colour neighbours right after its update (its lower neighbours are final).
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     }
 }
 
-// Random initial state (Algorithm 1, "Initialize replica states randomly"): word [wb][site]
+// Random initial state (Algorithm 1, initialisation): word [wb][site]
 // is output word 0 of Philox(site, 0, wb, id), i.e. bit b is walker 32 wb + b's spin.
 __global__ void lattice_init_kernel(const LatInst* __restrict__ insts, uint64_t seed) {
     const LatInst& I = insts[blockIdx.x];
