@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
+    p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--serve-requests", type=int, default=48)
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12")
     p.add_argument("--serve-budget", type=int, default=20000)
@@ -264,6 +266,142 @@ def served_stream(args, stream):
             "slots_per_L": 4}
 
 
+# ------------------------------------------------------------------------------ other workloads
+def _time_ms(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def plain_pt_single(stream):
+    """One EA instance, L=6, 16 slots (beta 0.2 -> 3.0), 10^4 sweeps of plain PT in one launch."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    inst = I.ea_instance(6, index=0)
+    betas = I.geometric_betas(0.2, 3.0, 16)
+    ctx = pt.create_instances([inst], [betas], pt.Config(seed=0x7A972509), instance_ids=[0],
+                              stream=stream.cuda_stream)
+    ms = _time_ms(lambda: pt.run_cycles(ctx, 10_000), 3, stream)
+    att = 16 * 216 * 10_000
+    pt.destroy(ctx)
+    return {"workload": "plain PT, 1 EA instance L=6, R=16, 10^4 sweeps in one launch",
+            "ms": ms, "attempts_per_ns": att / (ms * 1e6)}
+
+
+def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
+    """4096 EA instances, L uniform in {6..16} (even), R uniform in 24..48 on 0.1 -> 3.0,
+    proposals every 10 sweeps from pools of 512 (PT runs of this library, untimed), block
+    sizes autotuned per size class, cycles replayed from a CUDA graph."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    g = np.random.default_rng(3)
+    Ls = g.choice([6, 8, 10, 12, 14, 16], size=n)
+    Rs = g.integers(24, 49, size=n)
+    insts = [I.ea_instance(int(L), index=k) for k, L in enumerate(Ls)]
+    betas = [I.geometric_betas(0.1, 3.0, int(R)) for R in Rs]
+    props = [[1] * (int(R) - 2) + [0, 0] for R in Rs]
+    ids = list(range(n))
+    cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+    t0 = time.perf_counter()
+    ctx = pt.create_instances(insts, betas, cfg, prop_enabled=props, instance_ids=ids,
+                              stream=stream.cuda_stream)
+    gen = pt.create_instances(insts, betas, pt.Config(seed=0x9001),
+                              instance_ids=[1_000_000 + i for i in ids], stream=stream.cuda_stream)
+    pt.run_cycles(gen, 2000)
+    for e in range(P):
+        pt.run_cycles(gen, 4)
+        pt.capture_proposals(ctx, gen, e)
+    pt.destroy(gen)
+    pt.autotune(ctx, probe_cycles=20)
+    prep = time.perf_counter() - t0
+    ms = _time_ms(lambda: pt.run_cycles_graph(ctx, cycles), reps, stream)
+    att = int(sum(int(R) * int(L) ** 3 for L, R in zip(Ls, Rs))) * cycles
+    groups = pt.group_info(ctx)
+    pt.destroy(ctx)
+    return {"workload": f"{n} EA instances, L in {{6..16}}, R in 24..48, proposals every 10 "
+                        f"from pools of {P} (2000 + {4 * P} PT sweeps per instance, untimed), "
+                        f"autotuned, {cycles} graph-replayed cycles per step",
+            "ms_per_step": ms, "attempts_per_ns": att / (ms * 1e6), "size_classes": len(groups),
+            "threads_per_class": sorted({gr["threads"] for gr in groups}), "prep_s": round(prep, 1)}
+
+
+def factorization(stream, sweeps_total, n=1000, R=32, P=64, chunk=1000):
+    """The 8x8-bit multiplier (N = 200) with the product bits clamped to 1000 products of two
+    primes <= 255; R = 32 on 0.05 -> 5.0, Gibbs sweeps, proposals every 10 sweeps on the 23
+    hottest slots from a pool of configurations of the unclamped circuit (one PT run of the
+    universal instance, untimed). Success: some replica decodes to A*B = C with A, B > 1."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    mult = I.multiplier(8)
+    prods = I.draw_prime_products(n)
+    betas = I.geometric_betas(0.05, 5.0, R)
+    prop = [1] * 23 + [0] * (R - 23)
+    # pool: slot configurations of the universal instance (product free), captured every 20 sweeps
+    uni = mult.instance(None)
+    t0 = time.perf_counter()
+    gcfg = pt.Config(update=pt.GIBBS, seed=0x9001)
+    gen = pt.create_instances([uni], [betas], gcfg, instance_ids=[7_000_000], stream=stream.cuda_stream)
+    dst = pt.create_instances([uni], [betas], pt.Config(update=pt.GIBBS, seed=1, pool_size=P),
+                              instance_ids=[0], stream=stream.cuda_stream)
+    pt.run_cycles(gen, 20_000)
+    for e in range(P):
+        pt.run_cycles(gen, 20)
+        pt.capture_proposals(dst, gen, e)
+    nw = (mult.n_spins + 31) // 32
+    one = np.zeros((P, R * nw), dtype=np.uint32)
+    pt.read_proposals_packed(dst, one, 0, P)
+    pt.destroy(gen)
+    pt.destroy(dst)
+    insts = [mult.instance(C) for C, _, _ in prods]
+    cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+    ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
+                              instance_ids=list(range(n)), stream=stream.cuda_stream)
+    pt.load_proposals_packed(ctx, np.ascontiguousarray(np.tile(one, (1, n))), 0, P)
+    prep = time.perf_counter() - t0
+    wA = 1 << np.arange(mult.w)
+    solved_at = np.full(n, -1)
+    done, t_gpu = 0, 0.0
+    checkpoints = {}
+    while done < sweeps_total:
+        step = min(chunk, sweeps_total - done)
+        s, e = _ev_pair()
+        s.record(stream)
+        pt.run_cycles(ctx, step)
+        e.record(stream)
+        e.synchronize()
+        t_gpu += s.elapsed_time(e)
+        done += step
+        for k in np.nonzero(solved_at < 0)[0]:
+            sp, _ = pt.read_state(ctx, int(k))
+            A = (sp[:, mult.A] > 0) @ wA
+            B = (sp[:, mult.B] > 0) @ wA
+            C = prods[k][0]
+            if np.any((A * B == C) & (A > 1) & (B > 1)):
+                solved_at[k] = done
+        checkpoints[done] = int((solved_at >= 0).sum())
+    att = n * R * int((insts[0].clamp == 0).sum())
+    pt.destroy(ctx)
+    return {"workload": f"{n} clamped 8x8-bit multipliers (N={mult.n_spins}), R={R} on 0.05->5.0, "
+                        f"Gibbs, proposals every 10 sweeps from a pool of {P} universal-instance "
+                        f"configurations (untimed, {prep:.1f} s)",
+            "attempts_per_ns": att * done / (t_gpu * 1e6),
+            "solved_of": n, "solved_after_sweeps": checkpoints,
+            "median_sweeps_to_solution": (float(np.median(solved_at[solved_at >= 0]))
+                                          if (solved_at >= 0).any() else None)}
+
+
+def _ev_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
 # ------------------------------------------------------------------------------ CPU oracle
 def _oracle_worker(a):
     L, R, index, sweeps, seed = a
@@ -452,6 +590,11 @@ def main():
     serving = None
     if not args.no_serve and rank == 0:
         serving = served_stream(args, stream.cuda_stream)
+    others = None
+    if not args.no_configs and rank == 0:
+        others = {"plain_pt_single": plain_pt_single(stream),
+                  "ragged_batch": ragged_batch(stream),
+                  "factorization": factorization(stream, args.factor_sweeps)}
 
     cpu = None
     if cpu_pool is not None:
@@ -476,6 +619,7 @@ def main():
                                f"then one capture every {args.pool_gap} sweeps (untimed)",
                        "threads_per_block": pt.info(ctx)["threads"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+            "other_workloads": others,
             "gpu_launches": args.steps, "clocks": clk.summary(),
         }), flush=True)
     if dist:
