@@ -359,7 +359,8 @@ pt_status lattice_host(const pt_instance_desc& d, LatHost& h, int k) {
             uint32_t e16[6];
             for (int dir = 0; dir < 6; ++dir) {
                 if (col[nbr[dir]] < cc) { flags |= 1u << dir; ++nlow; }
-                e16[dir] = (uint32_t)(4 * h.pos[nbr[dir]]) | (Jv[dir] < 0 ? 0x8000u : 0u);
+                // byte offset of the neighbour's word, or of its complement across a -1 bond
+                e16[dir] = (uint32_t)(8 * h.pos[nbr[dir]]) + (Jv[dir] < 0 ? 4u : 0u);
             }
             if (nlow == 6) flags |= 64u;
             h.itab.push_back((uint32_t)i | (flags << 16));
@@ -532,7 +533,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
+    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
@@ -588,6 +589,33 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         }
         if (ncol > 32) return fail(PT_ENOTSUP, "instance %d: colouring needs %d > 32 colours", k, ncol);
         I.ncol = ncol;
+        // Energy fused into the last sweep of a cycle: a free site counts, after its update,
+        // its field and its bonds to clamped neighbours and to free neighbours of a lower
+        // colour (final by then); each free-free bond is counted once, at its higher-colour
+        // end. The clamped spins' own terms are the constant Eclamp.
+        std::vector<int32_t> rowl(N);
+        for (int i = 0; i < N; ++i) {
+            int lo = rowp[i];
+            if (clamp[i] == 0) {
+                for (int a = rowp[i]; a < rowp[i + 1]; ++a) {
+                    const int j = adj[a];
+                    if (clamp[j] != 0 || col[j] < col[i]) {
+                        std::swap(adj[a], adj[lo]);
+                        std::swap(adjJ[a], adjJ[lo]);
+                        ++lo;
+                    }
+                }
+            }
+            rowl[i] = lo;
+        }
+        {
+            long long ec = 0;
+            for (int i = 0; i < N; ++i) if (clamp[i] != 0) ec -= (long long)h[i] * clamp[i];
+            for (int e = 0; e < NE; ++e)
+                if (clamp[d.edge_i[e]] != 0 && clamp[d.edge_j[e]] != 0)
+                    ec -= (long long)d.edge_J[e] * clamp[d.edge_i[e]] * clamp[d.edge_j[e]];
+            I.Eclamp = (int32_t)ec;
+        }
         std::vector<int32_t> cs;
         I.col_off[0] = 0;
         for (int cc = 0; cc < ncol; ++cc) {
@@ -615,6 +643,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].spins = A.zeros((size_t)N * R4);
         o[k].clamp = A.add(clamp.data(), N);
         o[k].rowp = A.add(rowp.data(), rowp.size() * 4);
+        o[k].rowl = A.add(rowl.data(), rowl.size() * 4);
         o[k].adj = A.add(adj.data(), adj.size() * 4);
         o[k].adjJ = A.add(adjJ.data(), adjJ.size() * 4);
         o[k].h = A.add(h.data(), h.size() * 4);
@@ -663,6 +692,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.spins = (int8_t*)(b + o[k].spins);
         I.clamp = (const int8_t*)(b + o[k].clamp);
         I.rowp = (const int32_t*)(b + o[k].rowp);
+        I.rowl = (const int32_t*)(b + o[k].rowl);
         I.adj = (const int32_t*)(b + o[k].adj);
         I.adjJ = (const int32_t*)(b + o[k].adjJ);
         I.h = (const int32_t*)(b + o[k].h);

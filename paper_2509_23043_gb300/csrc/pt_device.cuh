@@ -117,9 +117,10 @@ struct LatInst {
                            // Eight 16-bit fields:
                            //   x.lo  site index
                            //   x.hi  bits 0-5: neighbour d has a lower colour; bit 6: all six
-                           //   y,z,w six neighbours (+x,-x,+y,-y,+z,-z): bits 0-14 byte offset
-                           //         of the neighbour's word in colour-major order, bit 15 set
-                           //         iff the bond is -1
+                           //   y,z,w six neighbours (+x,-x,+y,-y,+z,-z): byte offset into
+                           //         the shared {word, complement} pairs (8 bytes per site,
+                           //         colour-major) of the neighbour's word, or of its
+                           //         complement (+4) when the bond is -1
     const uint16_t* pos;   // [N] colour-major position of each site
     const int32_t* active; // nonzero: the instance takes part in launches
     int32_t* E;            // [W*32] per walker
@@ -140,10 +141,13 @@ struct LatInst {
 struct GraphInst {
     uint32_t iid;
     int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
+    int32_t Eclamp;          // energy of the clamped spins: their fields and mutual bonds
     int32_t col_off[33];
     int8_t* spins;           // [N][R4]
     const int8_t* clamp;     // [N]: 0 free, +-1 clamped
     const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
+    const int32_t* rowl;     // [N] a free site's row lists first its "counted" neighbours
+                             // (clamped or of a lower colour), rowp[i] .. rowl[i]-1
     const int32_t* adj;      // [2 NE] neighbour index
     const int32_t* adjJ;     // [2 NE] coupling
     const int32_t* h;        // [N]

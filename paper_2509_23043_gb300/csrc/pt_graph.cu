@@ -16,6 +16,7 @@ struct GraphSmem {
     int8_t* spins;
     uint32_t* thr;
     int32_t* rowp;
+    int32_t* rowl;
     int32_t* adj;
     int32_t* adjJ;
     int32_t* h;
@@ -35,6 +36,7 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     S.spins = reinterpret_cast<int8_t*>(base + l.spins);
     S.thr = reinterpret_cast<uint32_t*>(base + l.thr);
     S.rowp = reinterpret_cast<int32_t*>(base + l.rowp);
+    S.rowl = reinterpret_cast<int32_t*>(base + l.rowl);
     S.adj = reinterpret_cast<int32_t*>(base + l.adj);
     S.adjJ = reinterpret_cast<int32_t*>(base + l.adjJ);
     S.h = reinterpret_cast<int32_t*>(base + l.h);
@@ -52,24 +54,43 @@ __device__ __forceinline__ int sbyte(uint32_t w, int k) {
     return (int)(int8_t)((w >> (8 * k)) & 0xFFu);
 }
 
-// One sweep: every free site of every colour class, four walkers per thread.
+// One sweep: every free site of every colour class, four walkers per thread. Item q of a
+// class is (site q / Q, quad q % Q); the item stride Ts is a multiple of Q, so a thread keeps
+// one quad for the whole sweep and neighbouring lanes read neighbouring words of one row.
+// With energy_on (the last sweep of a cycle) each thread adds, for its quad, the energy terms
+// of the free sites it updates: -m (h + the bonds to its counted neighbours, rowp..rowl),
+// which sum with Eclamp to the exact energy (each bond counted once, at the end updated
+// last); graph_energy_finish turns them into E.
 __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
-                            uint32_t sweep_idx, int update) {
+                            uint32_t sweep_idx, int update, bool energy_on) {
     const int Q = I.R4 >> 2;
     const int tw = 2 * I.Imax + 1;
+    const int Ts = (blockDim.x / Q) * Q;
+    const int tid = threadIdx.x;
+    const int quad = tid % Q;
     uint32_t* sp = reinterpret_cast<uint32_t*>(S.spins);
+    int e0 = 0, e1 = 0, e2 = 0, e3 = 0;
     for (int c = 0; c < I.ncol; ++c) {
         const int base = I.col_off[c];
         const int nc = I.col_off[c + 1] - base;
         const int nitems = nc * Q;
-        for (int q = threadIdx.x; q < nitems; q += blockDim.x) {
-            const int quad = q / nc;
-            const int site = S.csites[base + (q - quad * nc)];
+        for (int q = tid; q < nitems && tid < Ts; q += Ts) {
+            const int site = S.csites[base + q / Q];
             const int hs = S.h[site];
-            int f0 = hs, f1 = hs, f2 = hs, f3 = hs;
-            for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
-                const uint32_t wd = sp[S.adj[a] * Q + quad];
-                const int J = S.adjJ[a];
+            int g0 = 0, g1 = 0, g2 = 0, g3 = 0;        // counted neighbours
+            const int split = S.rowl[site], end = S.rowp[site + 1];
+            for (int a2 = S.rowp[site]; a2 < split; ++a2) {
+                const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                const int J = S.adjJ[a2];
+                g0 += J * sbyte(wd, 0);
+                g1 += J * sbyte(wd, 1);
+                g2 += J * sbyte(wd, 2);
+                g3 += J * sbyte(wd, 3);
+            }
+            int f0 = hs + g0, f1 = hs + g1, f2 = hs + g2, f3 = hs + g3;
+            for (int a2 = split; a2 < end; ++a2) {
+                const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                const int J = S.adjJ[a2];
                 f0 += J * sbyte(wd, 0);
                 f1 += J * sbyte(wd, 1);
                 f2 += J * sbyte(wd, 2);
@@ -80,13 +101,15 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                                                  (kDomWord << 24) | (uint32_t)quad, I.iid), a);
             const int f[4] = {f0, f1, f2, f3};
             const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+            int nmv[4];
             uint32_t out = own;
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
                 const int w = quad * 4 + k4;
-                if (w >= I.R) break;
-                const int slot = S.sow[w];
                 const int m = sbyte(own, k4);
+                nmv[k4] = m;
+                if (w >= I.R) continue;
+                const int slot = S.sow[w];
                 int nm;
                 if (update == 1) {
                     nm = (u[k4] < S.thr[slot * tw + f[k4] + I.Imax]) ? 1 : -1;
@@ -94,12 +117,36 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                     const int mI = m * f[k4];   // dE = 2 m I
                     nm = (mI <= 0 || u[k4] < S.thr[slot * tw + mI + I.Imax]) ? -m : m;
                 }
+                nmv[k4] = nm;
                 out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(uint8_t)(int8_t)nm << (8 * k4));
             }
             if (out != own) sp[site * Q + quad] = out;
+            if (energy_on) {
+                e0 -= nmv[0] * (hs + g0);
+                e1 -= nmv[1] * (hs + g1);
+                e2 -= nmv[2] * (hs + g2);
+                e3 -= nmv[3] * (hs + g3);
+            }
+        }
+        if (energy_on && c == I.ncol - 1 && tid < Ts) {
+            const int w = quad * 4;
+            if (e0) atomicAdd(&S.Eacc[w + 0], e0);
+            if (e1) atomicAdd(&S.Eacc[w + 1], e1);
+            if (e2) atomicAdd(&S.Eacc[w + 2], e2);
+            if (e3) atomicAdd(&S.Eacc[w + 3], e3);
         }
         __syncthreads();
     }
+}
+
+// E = Eclamp + the terms the last sweep accumulated; clears the accumulators. Ends
+// synchronised.
+__device__ void graph_energy_finish(const GraphInst& I, GraphSmem& S) {
+    for (int w = threadIdx.x; w < I.R4; w += blockDim.x) {
+        S.E[w] = I.Eclamp + S.Eacc[w];
+        S.Eacc[w] = 0;
+    }
+    __syncthreads();
 }
 
 // Exact energies of every walker: E = -1/2 sum_i m_i (I_i + h_i), lanes = walkers.
@@ -219,6 +266,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     const int tw = 2 * I.Imax + 1;
     for (int i = tid; i < R * tw; i += T) S.thr[i] = I.thr[i];
     for (int i = tid; i <= N; i += T) S.rowp[i] = I.rowp[i];
+    for (int i = tid; i < N; i += T) S.rowl[i] = I.rowl[i];
     for (int i = tid; i < 2 * I.NE; i += T) { S.adj[i] = I.adj[i]; S.adjJ[i] = I.adjJ[i]; }
     for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
     for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
@@ -232,10 +280,10 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeEnergy) graph_energy(I, S);
     if (a.mode & kModeSweeps) {
         for (int k = 0; k < a.n; ++k) {
-            graph_sweep(I, S, a, (uint32_t)sweeps, a.update);
+            graph_sweep(I, S, a, (uint32_t)sweeps, a.update, k == a.n - 1);
             ++sweeps;
         }
-        if (a.n > 0) graph_energy(I, S);
+        if (a.n > 0) graph_energy_finish(I, S);
     }
     if (a.mode & kModePropose) {
         ++n_prop;
@@ -249,10 +297,10 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
             for (int m = 0; m < a.M; ++m) {
-                graph_sweep(I, S, a, (uint32_t)sweeps, a.update);
+                graph_sweep(I, S, a, (uint32_t)sweeps, a.update, m == a.M - 1);
                 ++sweeps;
             }
-            graph_energy(I, S);
+            graph_energy_finish(I, S);
             if (proposal_due(sweeps, a)) {
                 ++n_prop;
                 if (with_pool) graph_propose(I, S, k0, k1, n_prop);

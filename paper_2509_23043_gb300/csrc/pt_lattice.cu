@@ -7,9 +7,11 @@
 // labels (sow / wos) instead of moving spins, which gives the same chain as swapping
 // configurations (Eq. P_swap) since the random numbers of a local move are keyed by the walker.
 //
-// Local move (Methods: local sweeps; Metropolis rule). For a site word s and its six
-// neighbour words n_d, the bond d of every walker is unsatisfied iff s ^ n_d ^ Jneg_d; the
-// bit-sliced count c of unsatisfied bonds (0..6) gives dE = 12 - 4c. c >= 3 always flips;
+// Local move (Methods: local sweeps; Metropolis rule). Shared memory holds every spin word
+// next to its complement, and the table points a neighbour across a negative bond at the
+// complement, so the word read is n_d ^ Jneg_d and the bond d of every walker is unsatisfied
+// iff s differs from it; the bit-sliced count c of unsatisfied bonds (0..6) gives
+// dE = 12 - 4c. c >= 3 always flips;
 // c = 0, 1, 2 flips iff u < T(beta_slot, dE). The comparison runs MSB first over bit planes:
 // plane k of the 32 walkers' u is one Philox output word, so planes are only drawn while some
 // walker is still undecided (the result is the full 32-bit u < T comparison).
@@ -49,7 +51,7 @@ __device__ __forceinline__ LP load_lp(const LatInst& I) {
 
 struct LatSmem {
     uint4* tw;         // [W*32] bit-sliced thresholds {T4, T8, T12} per plane
-    uint32_t* spins;   // [W*N]
+    uint2* spins;      // [W*N] {spin word, its complement}, colour-major
     uint4* itab;       // [N]
     double* beta;      // [R]
     double* dbeta;     // [R] beta[r+1] - beta[r] in FP64 (0 for the last slot)
@@ -74,7 +76,7 @@ __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I
     const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool);
     LatSmem S;
     S.tw = reinterpret_cast<uint4*>(base + l.tw);
-    S.spins = reinterpret_cast<uint32_t*>(base + l.spins);
+    S.spins = reinterpret_cast<uint2*>(base + l.spins);
     S.itab = reinterpret_cast<uint4*>(base + l.itab);
     S.beta = reinterpret_cast<double*>(base + l.beta);
     S.dbeta = reinterpret_cast<double*>(base + l.dbeta);
@@ -150,35 +152,36 @@ __device__ __forceinline__ uint32_t nb_word(const uint8_t* base, uint32_t off) {
     return *reinterpret_cast<const uint32_t*>(base + off);
 }
 
-// PTX prmt in its generic mode: a selector nibble with its top bit set replicates the sign
-// bit of the selected byte over the output byte. (CUDA's __byte_perm documents only the low
-// three selector bits, so the mode is requested through PTX.)
-template <unsigned SEL>
-__device__ __forceinline__ uint32_t prmt_sign(uint32_t x) {
-    uint32_t r;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(SEL));
-    return r;
-}
-
-// The six "bond unsatisfied" words s ^ n_d ^ Jneg_d of a table entry. A bond's sign is the
-// top bit of its 16-bit field (byte 1 or byte 3 of the word); replicating that byte's sign
-// over all four bytes gives the all-ones / all-zeros word Jneg_d in one operation.
-__device__ __forceinline__ void bond_words(const uint8_t* sp, const uint4& it, uint32_t s,
-                                           uint32_t (&u)[6]) {
-    u[0] = s ^ nb_word(sp, it.y & 0x7FFFu) ^ prmt_sign<0x9999u>(it.y);
-    u[1] = s ^ nb_word(sp, (it.y >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.y);
-    u[2] = s ^ nb_word(sp, it.z & 0x7FFFu) ^ prmt_sign<0x9999u>(it.z);
-    u[3] = s ^ nb_word(sp, (it.z >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.z);
-    u[4] = s ^ nb_word(sp, it.w & 0x7FFFu) ^ prmt_sign<0x9999u>(it.w);
-    u[5] = s ^ nb_word(sp, (it.w >> 16) & 0x7FFFu) ^ prmt_sign<0xBBBBu>(it.w);
+// Count of unsatisfied bonds of a site word s, bit-sliced (b2 b1 b0), from the six words
+// m_d = n_d ^ Jneg_d its table entry points at (16-bit byte offsets). With u_d = s ^ m_d the
+// first adder stage over (u0, u1, u2) has sum s ^ X1 and carry s ^ M1, X1 and M1 being the
+// parity and majority of (m0, m1, m2) (a majority commutes with complementing all inputs), so
+// s enters only where the two halves meet.
+__device__ __forceinline__ void bond_count(const uint8_t* sp, const uint4& it, uint32_t s,
+                                           uint32_t (&m)[6], uint32_t& b0, uint32_t& b1,
+                                           uint32_t& b2) {
+    m[0] = nb_word(sp, it.y & 0xFFFFu);
+    m[1] = nb_word(sp, it.y >> 16);
+    m[2] = nb_word(sp, it.z & 0xFFFFu);
+    m[3] = nb_word(sp, it.z >> 16);
+    m[4] = nb_word(sp, it.w & 0xFFFFu);
+    m[5] = nb_word(sp, it.w >> 16);
+    const uint32_t X1 = m[0] ^ m[1] ^ m[2], M1 = maj3(m[0], m[1], m[2]);
+    const uint32_t X2 = m[3] ^ m[4] ^ m[5], M2 = maj3(m[3], m[4], m[5]);
+    const uint32_t t = (s ^ X1) & (s ^ X2);        // carry of the two sum bits
+    const uint32_t e = M1 ^ M2;                    // the two carries differ
+    b0 = X1 ^ X2;
+    b1 = e ^ t;
+    b2 = mux(e, t, s ^ M1);                        // majority of (s^M1, s^M2, t)
 }
 
 // Energy bookkeeping of one updated word: add its new count of unsatisfied bonds to
 // lower-colour neighbours to the thread's vertical counter.
 template <int KB>
 __device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t flags,
-                                                  const uint32_t (&u)[6], uint32_t b0,
-                                                  uint32_t b1, uint32_t b2, uint32_t flip) {
+                                                  const uint32_t (&m)[6], uint32_t s_new,
+                                                  uint32_t b0, uint32_t b1, uint32_t b2,
+                                                  uint32_t flip) {
     uint32_t n0, n1, n2;
     if (flags & 64u) {
         // all six neighbours are lower: the new count is 6 - c where flipped
@@ -189,7 +192,7 @@ __device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t 
         uint32_t v[6];
 #pragma unroll
         for (int dir = 0; dir < 6; ++dir)
-            v[dir] = (u[dir] ^ flip) & (0u - ((flags >> dir) & 1u));
+            v[dir] = (s_new ^ m[dir]) & (0u - ((flags >> dir) & 1u));
         const uint32_t e1 = v[0] ^ v[1] ^ v[2], f1 = maj3(v[0], v[1], v[2]);
         const uint32_t e2 = v[3] ^ v[4] ^ v[5], f2 = maj3(v[3], v[4], v[5]);
         n0 = e1 ^ e2;
@@ -215,21 +218,17 @@ __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const Run
 #pragma unroll
         for (int wb = 0; wb < MAXW; ++wb) {
             if (wb >= P.W) break;
-            uint8_t* sp = reinterpret_cast<uint8_t*>(S.spins + wb * P.N);
-            uint32_t* own_p = S.spins + wb * P.N + base;
+            const uint8_t* sp = reinterpret_cast<const uint8_t*>(S.spins + wb * P.N);
+            uint2* own_p = S.spins + wb * P.N + base;
             const int rem = P.R - wb * 32;
             const uint32_t vmask = rem >= 32 ? kFull : ((1u << rem) - 1u);
             const uint32_t ctr2 = (kDomPlane << 24) | (uint32_t)wb;
             const uint4* tw = S.tw + wb * 32;
             for (int k = tid; k < nc; k += T) {
                 const uint4 it = S.itab[base + k];
-                const uint32_t s = own_p[k];
-                uint32_t u[6];
-                bond_words(sp, it, s, u);
-                const uint32_t s1 = u[0] ^ u[1] ^ u[2], c1 = maj3(u[0], u[1], u[2]);
-                const uint32_t s2 = u[3] ^ u[4] ^ u[5], c2 = maj3(u[3], u[4], u[5]);
-                const uint32_t b0 = s1 ^ s2, t = s1 & s2;
-                const uint32_t b1 = c1 ^ c2 ^ t, b2 = maj3(c1, c2, t);
+                const uint32_t s = own_p[k].x;
+                uint32_t m[6], b0, b1, b2;
+                bond_count(sp, it, s, m, b0, b1, b2);
                 uint32_t flip = 0;
                 if (flip_on) {
                     const uint32_t always = b2 | (b1 & b0);   // count >= 3: dE <= 0
@@ -250,9 +249,9 @@ __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const Run
                         }
                     }
                     flip = (always | lt) & vmask;
-                    if (flip) own_p[k] = s ^ flip;
+                    if (flip) own_p[k] = make_uint2(s ^ flip, ~(s ^ flip));
                 }
-                if (acc) count_lower_bonds(cnt[wb], it.x >> 16, u, b0, b1, b2, flip);
+                if (acc) count_lower_bonds(cnt[wb], it.x >> 16, m, s ^ flip, b0, b1, b2, flip);
             }
         }
         __syncthreads();
@@ -402,14 +401,15 @@ __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
         const int r = (w < R) ? S.accr[w] : -1;
         const uint32_t am = __ballot_sync(kFull, r >= 0);
         if (!am) continue;
-        uint32_t* sp = S.spins + wb * N;
+        uint2* sp = S.spins + wb * N;
         for (int g = warp; g < NW; g += nwarps) {
             const uint32_t row = r >= 0 ? S.stage[r * NW + g] : 0u;
             const uint32_t col = warp_transpose32(row, lane);
             const int site = 32 * g + lane;
             if (site < N) {
                 const int ps = I.pos[site];
-                sp[ps] = (col & am) | (sp[ps] & ~am);
+                const uint32_t v = (col & am) | (sp[ps].x & ~am);
+                sp[ps] = make_uint2(v, ~v);
             }
         }
     }
@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     // state in (spins to colour-major order)
     for (int i = tid; i < W * N; i += T) {
         const int wb = i / N, site = i - wb * N;
-        S.spins[wb * N + I.pos[site]] = I.spins[i];
+        const uint32_t v = I.spins[i];
+        S.spins[wb * N + I.pos[site]] = make_uint2(v, ~v);
     }
     for (int i = tid; i < N; i += T) S.itab[i] = I.itab[i];
     for (int i = tid; i < WR; i += T) {
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     // state out (back to site order)
     for (int i = tid; i < W * N; i += T) {
         const int wb = i / N, site = i - wb * N;
-        I.spins[i] = S.spins[wb * N + I.pos[site]];
+        I.spins[i] = S.spins[wb * N + I.pos[site]].x;
     }
     for (int i = tid; i < WR; i += T) {
         I.E[i] = S.E[i];

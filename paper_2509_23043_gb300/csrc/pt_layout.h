@@ -24,7 +24,7 @@ PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, b
     const size_t WR = (size_t)W * 32;
     size_t o = 0;
     l.tw = o;     o = align16(o + WR * 16);
-    l.spins = o;  o = align16(o + WR / 32 * N * 4);
+    l.spins = o;  o = align16(o + WR / 32 * N * 8);   // word and complement
     l.itab = o;   o = align16(o + (size_t)N * 16);
     l.beta = o;   o = align16(o + (size_t)R * 8);
     l.dbeta = o;  o = align16(o + (size_t)R * 8);
@@ -47,7 +47,7 @@ PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, b
 }
 
 struct GraphLayout {
-    size_t spins, thr, rowp, adj, adjJ, h, csites, E, Eacc, st, sow, wos, pbuf, total;
+    size_t spins, thr, rowp, rowl, adj, adjJ, h, csites, E, Eacc, st, sow, wos, pbuf, total;
 };
 
 PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
@@ -57,6 +57,7 @@ PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, in
     l.spins = o;  o = align16(o + (size_t)N * R4);
     l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
     l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
+    l.rowl = o;   o = align16(o + (size_t)N * 4);
     l.adj = o;    o = align16(o + (size_t)2 * NE * 4);
     l.adjJ = o;   o = align16(o + (size_t)2 * NE * 4);
     l.h = o;      o = align16(o + (size_t)N * 4);

@@ -42,11 +42,11 @@ def test_noalloc_read_matches_graph_engine():
 
 
 def test_noalloc_rejects_sizes_beyond_its_buffer():
-    inst = I.ea_instance(20, index=1)                 # N = 8000, R = 64: 512000 bytes
-    ctx = pt.create_instances([inst], [I.geometric_betas(0.2, 2.0, 64)], pt.Config(seed=1))
+    inst = I.ea_instance(18, index=1)                 # N = 5832, R = 48: 279936 bytes
+    ctx = pt.create_instances([inst], [I.geometric_betas(0.2, 2.0, 48)], pt.Config(seed=1))
     with pytest.raises(pt.PTError) as e:
         pt.read_state_noalloc(ctx, 0)
     assert e.value.status == pt.PT_ENOTSUP
     assert "exceeds" in str(e.value)
     s, E = pt.read_state(ctx, 0)                      # the allocating path still serves it
-    assert s.shape == (64, 8000)
+    assert s.shape == (48, 5832)
