@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
+    p.add_argument("--workloads", default="plain,ragged,factor",
+                   help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--serve-requests", type=int, default=48)
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12")
@@ -592,9 +594,14 @@ def main():
         serving = served_stream(args, stream.cuda_stream)
     others = None
     if not args.no_configs and rank == 0:
-        others = {"plain_pt_single": plain_pt_single(stream),
-                  "ragged_batch": ragged_batch(stream),
-                  "factorization": factorization(stream, args.factor_sweeps)}
+        wl = set(args.workloads.split(","))
+        others = {}
+        if "plain" in wl:
+            others["plain_pt_single"] = plain_pt_single(stream)
+        if "ragged" in wl:
+            others["ragged_batch"] = ragged_batch(stream)
+        if "factor" in wl:
+            others["factorization"] = factorization(stream, args.factor_sweeps)
 
     cpu = None
     if cpu_pool is not None:

@@ -533,7 +533,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
+    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
@@ -608,6 +608,19 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
             }
             rowl[i] = lo;
         }
+        // Packed local fields: four walkers' sums of J * [spin = -1] as bytes of one word
+        // (biased by 128), valid while every site's sum of |J| is at most 127.
+        bool packed = true;
+        for (int i = 0; i < N && packed; ++i) {
+            int sa = 0;
+            for (int a = rowp[i]; a < rowp[i + 1]; ++a) sa += std::abs(adjJ[a]);
+            if (sa > 127) packed = false;
+        }
+        std::vector<int32_t> adjp(2 * (size_t)NE, 0);
+        if (packed)
+            for (size_t a = 0; a < adjp.size(); ++a)
+                adjp[a] = (int32_t)(((uint32_t)adj[a] * (uint32_t)(R4 / 4)) << 8 | ((uint32_t)adjJ[a] & 0xFFu));
+        I.packed = packed ? 1 : 0;
         {
             long long ec = 0;
             for (int i = 0; i < N; ++i) if (clamp[i] != 0) ec -= (long long)h[i] * clamp[i];
@@ -646,6 +659,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].rowl = A.add(rowl.data(), rowl.size() * 4);
         o[k].adj = A.add(adj.data(), adj.size() * 4);
         o[k].adjJ = A.add(adjJ.data(), adjJ.size() * 4);
+        o[k].adjp = A.add(adjp.data(), adjp.size() * 4);
         o[k].h = A.add(h.data(), h.size() * 4);
         o[k].cs = A.add(cs.data(), std::max<size_t>(cs.size(), 1) * 4);
         o[k].ei = A.add(d.edge_i, (size_t)NE * 4);
@@ -666,7 +680,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         c->slab_off[k] = c->slab;
         c->slab += (size_t)R * NW;
         c->NWmax = std::max(c->NWmax, NW);
-        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, T / 32, c->with_pool != 0);
+        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, T / 32, c->with_pool != 0, I.packed != 0);
         maxsmem = std::max(maxsmem, l.total);
     }
     if (maxsmem > (size_t)c->optin)
@@ -695,6 +709,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.rowl = (const int32_t*)(b + o[k].rowl);
         I.adj = (const int32_t*)(b + o[k].adj);
         I.adjJ = (const int32_t*)(b + o[k].adjJ);
+        I.adjp = (const int32_t*)(b + o[k].adjp);
         I.h = (const int32_t*)(b + o[k].h);
         I.csites = (const int32_t*)(b + o[k].cs);
         I.ei = (const int32_t*)(b + o[k].ei);
@@ -898,7 +913,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, T / 32, ctx->with_pool != 0);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, T / 32, ctx->with_pool != 0, I.packed != 0);
                     smem = std::max(smem, l.total);
                 }
                 (void)I0;
@@ -924,7 +939,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, bestT / 32, ctx->with_pool != 0);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, bestT / 32, ctx->with_pool != 0, I.packed != 0);
                     smem = std::max(smem, l.total);
                 }
                 g.T = bestT;

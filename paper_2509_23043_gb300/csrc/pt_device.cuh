@@ -150,6 +150,9 @@ struct GraphInst {
                              // (clamped or of a lower colour), rowp[i] .. rowl[i]-1
     const int32_t* adj;      // [2 NE] neighbour index
     const int32_t* adjJ;     // [2 NE] coupling
+    const int32_t* adjp;     // [2 NE] packed = (neighbour * R4/4) << 8 | (uint8) coupling, used
+                             // when `packed` (every |coupling| and every site's sum of them <= 127)
+    int32_t packed;
     const int32_t* h;        // [N]
     const int32_t* csites;   // [nfree] free sites in colour order
     const int32_t* ei;       // [NE]

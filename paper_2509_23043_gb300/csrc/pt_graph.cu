@@ -19,6 +19,7 @@ struct GraphSmem {
     int32_t* rowl;
     int32_t* adj;
     int32_t* adjJ;
+    int32_t* adjp;
     int32_t* h;
     int32_t* csites;
     int32_t* E;
@@ -31,7 +32,8 @@ struct GraphSmem {
 
 __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst& I, int nwarps,
                                                  bool with_pool) {
-    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, nwarps, with_pool);
+    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, nwarps, with_pool,
+                                 I.packed != 0);
     GraphSmem S;
     S.spins = reinterpret_cast<int8_t*>(base + l.spins);
     S.thr = reinterpret_cast<uint32_t*>(base + l.thr);
@@ -39,6 +41,7 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     S.rowl = reinterpret_cast<int32_t*>(base + l.rowl);
     S.adj = reinterpret_cast<int32_t*>(base + l.adj);
     S.adjJ = reinterpret_cast<int32_t*>(base + l.adjJ);
+    S.adjp = reinterpret_cast<int32_t*>(base + l.adjp);
     S.h = reinterpret_cast<int32_t*>(base + l.h);
     S.csites = reinterpret_cast<int32_t*>(base + l.csites);
     S.E = reinterpret_cast<int32_t*>(base + l.E);
@@ -69,6 +72,14 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
     const int tid = threadIdx.x;
     const int quad = tid % Q;
     uint32_t* sp = reinterpret_cast<uint32_t*>(S.spins);
+    // the thread's four walkers: threshold rows of their slots (fixed during a sweep), -1 for
+    // walkers beyond R
+    int trow[4];
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+        const int w = quad * 4 + k4;
+        trow[k4] = (w < I.R) ? S.sow[w] * tw + I.Imax : -1;
+    }
     int e0 = 0, e1 = 0, e2 = 0, e3 = 0;
     for (int c = 0; c < I.ncol; ++c) {
         const int base = I.col_off[c];
@@ -77,55 +88,77 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
         for (int q = tid; q < nitems && tid < Ts; q += Ts) {
             const int site = S.csites[base + q / Q];
             const int hs = S.h[site];
-            int g0 = 0, g1 = 0, g2 = 0, g3 = 0;        // counted neighbours
+            int g[4], f[4];                            // counted-neighbour sums, local fields
             const int split = S.rowl[site], end = S.rowp[site + 1];
-            for (int a2 = S.rowp[site]; a2 < split; ++a2) {
-                const uint32_t wd = sp[S.adj[a2] * Q + quad];
-                const int J = S.adjJ[a2];
-                g0 += J * sbyte(wd, 0);
-                g1 += J * sbyte(wd, 1);
-                g2 += J * sbyte(wd, 2);
-                g3 += J * sbyte(wd, 3);
-            }
-            int f0 = hs + g0, f1 = hs + g1, f2 = hs + g2, f3 = hs + g3;
-            for (int a2 = split; a2 < end; ++a2) {
-                const uint32_t wd = sp[S.adj[a2] * Q + quad];
-                const int J = S.adjJ[a2];
-                f0 += J * sbyte(wd, 0);
-                f1 += J * sbyte(wd, 1);
-                f2 += J * sbyte(wd, 2);
-                f3 += J * sbyte(wd, 3);
+            if (I.packed) {
+                // bytes of ac / ar: 128 + sum of J over the neighbours whose spin is -1
+                uint32_t ac = 0x80808080u, ar = 0x80808080u;
+                int sjc = 0, sjr = 0;
+                for (int a2 = S.rowp[site]; a2 < split; ++a2) {
+                    const uint32_t pk = (uint32_t)S.adjp[a2];
+                    const int J = (int)(int8_t)(pk & 0xFFu);
+                    const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
+                    ac += (uint32_t)J * neg;
+                    sjc += J;
+                }
+                for (int a2 = split; a2 < end; ++a2) {
+                    const uint32_t pk = (uint32_t)S.adjp[a2];
+                    const int J = (int)(int8_t)(pk & 0xFFu);
+                    const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
+                    ar += (uint32_t)J * neg;
+                    sjr += J;
+                }
+                // sum J m = sum J - 2 sum_{m=-1} J
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    g[k4] = sjc - 2 * ((int)((ac >> (8 * k4)) & 0xFFu) - 128);
+                    f[k4] = hs + g[k4] + sjr - 2 * ((int)((ar >> (8 * k4)) & 0xFFu) - 128);
+                }
+            } else {
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) g[k4] = 0;
+                for (int a2 = S.rowp[site]; a2 < split; ++a2) {
+                    const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                    const int J = S.adjJ[a2];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) g[k4] += J * sbyte(wd, k4);
+                }
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) f[k4] = hs + g[k4];
+                for (int a2 = split; a2 < end; ++a2) {
+                    const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                    const int J = S.adjJ[a2];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) f[k4] += J * sbyte(wd, k4);
+                }
             }
             const uint32_t own = sp[site * Q + quad];
             const uint4 r = philox_rk(make_uint4((uint32_t)site, sweep_idx,
                                                  (kDomWord << 24) | (uint32_t)quad, I.iid), a);
-            const int f[4] = {f0, f1, f2, f3};
             const uint32_t u[4] = {r.x, r.y, r.z, r.w};
             int nmv[4];
             uint32_t out = own;
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
-                const int w = quad * 4 + k4;
                 const int m = sbyte(own, k4);
                 nmv[k4] = m;
-                if (w >= I.R) continue;
-                const int slot = S.sow[w];
+                if (trow[k4] < 0) continue;
                 int nm;
                 if (update == 1) {
-                    nm = (u[k4] < S.thr[slot * tw + f[k4] + I.Imax]) ? 1 : -1;
+                    nm = (u[k4] < S.thr[trow[k4] + f[k4]]) ? 1 : -1;
                 } else {
                     const int mI = m * f[k4];   // dE = 2 m I
-                    nm = (mI <= 0 || u[k4] < S.thr[slot * tw + mI + I.Imax]) ? -m : m;
+                    nm = (mI <= 0 || u[k4] < S.thr[trow[k4] + mI]) ? -m : m;
                 }
                 nmv[k4] = nm;
                 out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(uint8_t)(int8_t)nm << (8 * k4));
             }
             if (out != own) sp[site * Q + quad] = out;
             if (energy_on) {
-                e0 -= nmv[0] * (hs + g0);
-                e1 -= nmv[1] * (hs + g1);
-                e2 -= nmv[2] * (hs + g2);
-                e3 -= nmv[3] * (hs + g3);
+                e0 -= nmv[0] * (hs + g[0]);
+                e1 -= nmv[1] * (hs + g[1]);
+                e2 -= nmv[2] * (hs + g[2]);
+                e3 -= nmv[3] * (hs + g[3]);
             }
         }
         if (energy_on && c == I.ncol - 1 && tid < Ts) {
@@ -159,8 +192,15 @@ __device__ void graph_energy(const GraphInst& I, GraphSmem& S) {
             for (int site = warp; site < I.N; site += nwarps) {
                 const int hs = S.h[site];
                 int f = hs;
-                for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a)
-                    f += S.adjJ[a] * (int)S.spins[S.adj[a] * I.R4 + w];
+                if (I.packed) {
+                    for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
+                        const uint32_t pk = (uint32_t)S.adjp[a];
+                        f += (int)(int8_t)(pk & 0xFFu) * (int)S.spins[(pk >> 8) * 4 + w];
+                    }
+                } else {
+                    for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a)
+                        f += S.adjJ[a] * (int)S.spins[S.adj[a] * I.R4 + w];
+                }
                 acc += (int)S.spins[site * I.R4 + w] * (f + hs);
             }
             atomicAdd(&S.Eacc[w], acc);
@@ -267,7 +307,14 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     for (int i = tid; i < R * tw; i += T) S.thr[i] = I.thr[i];
     for (int i = tid; i <= N; i += T) S.rowp[i] = I.rowp[i];
     for (int i = tid; i < N; i += T) S.rowl[i] = I.rowl[i];
-    for (int i = tid; i < 2 * I.NE; i += T) { S.adj[i] = I.adj[i]; S.adjJ[i] = I.adjJ[i]; }
+    if (I.packed) {
+        for (int i = tid; i < 2 * I.NE; i += T) S.adjp[i] = I.adjp[i];
+    } else {
+        for (int i = tid; i < 2 * I.NE; i += T) {
+            S.adj[i] = I.adj[i];
+            S.adjJ[i] = I.adjJ[i];
+        }
+    }
     for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
     for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
     for (int i = tid; i < R4; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
