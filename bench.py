@@ -580,14 +580,18 @@ def main():
     words_per_step = B * args.L ** 3 * ((args.R + 31) // 32) * spc
     ops = alu_ops_per_word(e_blocks) * words_per_step
     achieved = ops / (ms_step * 1e-3) / 1e12
-    peak = SM_COUNT * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    nominal = SM_COUNT * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    measured, _ = pt.calibrate_int(0)
+    peak = measured / 1e12
     tr = load_traffic(source_hash())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                 "kernel": "lattice_kernel", "alu_ops_per_attempt": alu_ops_per_word(e_blocks) / 32,
                 "plane_blocks_per_word": e_blocks,
-                "peak_basis": "152 SMs x 64 integer-ALU lanes x 2070 MHz (nominal)"}
+                "peak_basis": "measured in this run by pt_calibrate_int (independent lop3.b32 "
+                              "on every SM); nominal 152 SMs x 64 ALU lanes x 2070 MHz = "
+                              f"{nominal:.2f} TOP/s"}
 
     serving = None
     if not args.no_serve and rank == 0:

@@ -242,6 +242,14 @@ pt_status pt_set_active(pt_ctx *ctx, int32_t inst, int32_t active);
 /* Change the stream of all later calls. */
 pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
 
+/* Calibration of the integer pipes (no counterpart in the paper): the sustained rate, in
+ * operations per second, of independent 32-bit lop3 operations (kind 0, the integer ALU pipe
+ * that bounds the lattice sweep) or 32-bit multiply-adds (kind 1, the pipe of Philox's
+ * products), measured on the current device by a full-occupancy kernel on the legacy stream;
+ * *ms (may be NULL) receives the best launch time. It allocates and frees a small device
+ * buffer and synchronises. PT_EINVAL for another kind or a NULL ops_per_s. */
+pt_status pt_calibrate_int(int32_t kind, double *ops_per_s, double *ms);
+
 /* Release all device memory (stream ordered) and the context. NULL is allowed. */
 pt_status pt_destroy(pt_ctx *ctx);
 

@@ -50,7 +50,7 @@ EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed
            "pt_read_state_noalloc",
            "pt_read_walkers", "pt_write_state", "pt_read_counters", "pt_read_stats", "pt_info",
            "pt_group_info", "pt_autotune", "pt_run_cycles_graph", "pt_set_instance",
-           "pt_set_active", "pt_set_stream", "pt_destroy", "pt_last_error"]
+           "pt_set_active", "pt_set_stream", "pt_calibrate_int", "pt_destroy", "pt_last_error"]
 
 _lib = None
 
@@ -82,6 +82,7 @@ def lib():
         "pt_run_cycles_graph": [vp, i32], "pt_set_instance": [vp, i32, C.POINTER(_Desc)],
         "pt_set_active": [vp, i32, i32],
         "pt_set_stream": [vp, vp], "pt_destroy": [vp],
+        "pt_calibrate_int": [i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -353,6 +354,14 @@ def set_active(ctx: Context, inst: int, active: bool):
 
 def set_stream(ctx: Context, stream):
     _check(lib().pt_set_stream(ctx.handle, C.c_void_p(stream)))
+
+
+def calibrate_int(kind: int = 0) -> tuple[float, float]:
+    """pt_calibrate_int: (operations per second, best launch ms) of independent lop3 (kind 0)
+    or multiply-add (kind 1) operations on the current device."""
+    v, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().pt_calibrate_int(kind, C.byref(v), C.byref(ms)))
+    return v.value, ms.value
 
 
 def destroy(ctx: Context):

@@ -15,6 +15,7 @@
 #include "../../include/pt.h"
 #include "pt_device.cuh"
 #include "pt_layout.h"
+#include "pt_graph.cuh"
 
 namespace pt {
 cudaError_t launch_lattice(const LatInst*, int, int, int, int, size_t, const RunArgs&, int, cudaStream_t);

@@ -1,0 +1,75 @@
+// Integer-pipe calibration: the measured peak that the roofline of the lattice kernel is
+// quoted against. The lattice sweep is bound by the integer ALU pipe (three-input logic,
+// integer add, shift, compare), so the peak is the rate of independent lop3.b32 operations the
+// GPU sustains; the multiply pipe (Philox's 32x32 products) is measured alongside.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "pt.h"
+
+namespace pt {
+
+constexpr int kChains = 8;     // independent dependency chains per thread
+constexpr int kUnroll = 16;    // operations per chain per loop iteration
+
+// kind 0: lop3.b32 (xor of three), kind 1: mad.lo.u32 (the multiply pipe)
+template <int KIND>
+__global__ void __launch_bounds__(512) calib_kernel(uint32_t seed, int iters, uint32_t* out) {
+    uint32_t x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = seed + threadIdx.x * 977u + blockIdx.x * 131u + c;
+    const uint32_t k1 = seed ^ 0x9E3779B9u, k2 = seed ^ 0xBB67AE85u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) {
+                // the second operand is another chain's value, so no chain can be folded
+                if (KIND == 0)
+                    asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(x[(c + 1) % kChains]), "r"(k1));
+                else
+                    asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[c]) : "r"(k1), "r"(k2));
+            }
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc ^= x[c];
+    if (acc == 0x12345678u) out[blockIdx.x] = acc;   // keeps the chains live
+}
+
+}  // namespace pt
+
+extern "C" pt_status pt_calibrate_int(int32_t kind, double* ops_per_s, double* ms_out) {
+    using namespace pt;
+    if (!ops_per_s || (kind != 0 && kind != 1)) return PT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PT_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PT_ECUDA;
+    const int threads = 512, blocks = sms * 4, iters = 4096;
+    uint32_t* out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    pt_status st = PT_OK;
+    if (cudaMalloc(&out, sizeof(uint32_t) * blocks) != cudaSuccess) return PT_ENOMEM;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) st = PT_ECUDA;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && st == PT_OK; ++rep) {   // the first launch warms up
+        cudaEventRecord(a, 0);
+        if (kind == 0) calib_kernel<0><<<blocks, threads>>>(0x2509u + rep, iters, out);
+        else calib_kernel<1><<<blocks, threads>>>(0x2509u + rep, iters, out);
+        cudaEventRecord(b, 0);
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaGetLastError() != cudaSuccess) { st = PT_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    if (st == PT_OK) {
+        const double ops = (double)blocks * threads * iters * kUnroll * kChains;
+        *ops_per_s = ops / (best * 1e-3);
+        if (ms_out) *ms_out = best;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(out);
+    return st;
+}

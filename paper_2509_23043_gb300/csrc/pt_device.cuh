@@ -137,42 +137,6 @@ struct LatInst {
     unsigned long long* stats;  // [4][R]: swap acc, swap att, prop acc, prop att
 };
 
-// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spins int8 [N][R4].
-struct GraphInst {
-    uint32_t iid;
-    int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
-    int32_t Eclamp;          // energy of the clamped spins: their fields and mutual bonds
-    int32_t col_off[33];
-    int8_t* spins;           // [N][R4]
-    const int8_t* clamp;     // [N]: 0 free, +-1 clamped
-    const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
-    const int32_t* rowl;     // [N] a free site's row lists first its "counted" neighbours
-                             // (clamped or of a lower colour), rowp[i] .. rowl[i]-1
-    const int32_t* adj;      // [2 NE] neighbour index
-    const int32_t* adjJ;     // [2 NE] coupling
-    const int32_t* adjp;     // [2 NE] packed = (neighbour * R4/4) << 8 | (uint8) coupling, used
-                             // when `packed` (every |coupling| and every site's sum of them <= 127)
-    int32_t packed;
-    const int32_t* h;        // [N]
-    const int32_t* csites;   // [nfree] free sites in colour order
-    const int32_t* ei;       // [NE]
-    const int32_t* ej;       // [NE]
-    const int32_t* eJ;       // [NE]
-    const uint32_t* cbits;   // [2][NW]: clamped mask, clamp value (+1) bits
-    int32_t* E;              // [R4] per walker
-    int16_t* sow;            // [R4]
-    int16_t* wos;            // [R]
-    const uint32_t* thr;     // [R][2*Imax+1]
-    const double* beta;      // [R]
-    const uint8_t* prop;     // [R]
-    int32_t* cursor;         // [R]
-    const uint32_t* pool;    // entry e, slot r at pool + e * pstride + r * NW
-    long long pstride;
-    Counters* ctr;
-    unsigned long long* stats;
-    const int32_t* active;   // nonzero: the instance takes part in launches
-};
-
 // Kernel modes
 enum : int32_t {
     kModeSweeps = 1,     // n sweeps then energies

@@ -9,6 +9,7 @@
 // permutes slot <-> walker labels, thresholds are looked up by the walker's current slot.
 #include "pt_device.cuh"
 #include "pt_layout.h"
+#include "pt_graph.cuh"
 
 namespace pt {
 

@@ -1,0 +1,73 @@
+// Graph engine: the per-instance descriptor and the shared-memory layout of graph_kernel,
+// shared by the host (pt_api.cu) and the kernel (pt_graph.cu).
+#pragma once
+#include "pt_device.cuh"
+#include "pt_layout.h"
+
+namespace pt {
+
+// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spins int8 [N][R4].
+struct GraphInst {
+    uint32_t iid;
+    int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
+    int32_t Eclamp;          // energy of the clamped spins: their fields and mutual bonds
+    int32_t col_off[33];
+    int8_t* spins;           // [N][R4]
+    const int8_t* clamp;     // [N]: 0 free, +-1 clamped
+    const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
+    const int32_t* rowl;     // [N] a free site's row lists first its "counted" neighbours
+                             // (clamped or of a lower colour), rowp[i] .. rowl[i]-1
+    const int32_t* adj;      // [2 NE] neighbour index
+    const int32_t* adjJ;     // [2 NE] coupling
+    const int32_t* adjp;     // [2 NE] packed = (neighbour * R4/4) << 8 | (uint8) coupling, used
+                             // when `packed` (every |coupling| and every site's sum of them <= 127)
+    int32_t packed;
+    const int32_t* h;        // [N]
+    const int32_t* csites;   // [nfree] free sites in colour order
+    const int32_t* ei;       // [NE]
+    const int32_t* ej;       // [NE]
+    const int32_t* eJ;       // [NE]
+    const uint32_t* cbits;   // [2][NW]: clamped mask, clamp value (+1) bits
+    int32_t* E;              // [R4] per walker
+    int16_t* sow;            // [R4]
+    int16_t* wos;            // [R]
+    const uint32_t* thr;     // [R][2*Imax+1]
+    const double* beta;      // [R]
+    const uint8_t* prop;     // [R]
+    int32_t* cursor;         // [R]
+    const uint32_t* pool;    // entry e, slot r at pool + e * pstride + r * NW
+    long long pstride;
+    Counters* ctr;
+    unsigned long long* stats;
+    const int32_t* active;   // nonzero: the instance takes part in launches
+};
+
+struct GraphLayout {
+    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, csites, E, Eacc, st, sow, wos, pbuf, total;
+};
+
+// Packed instances keep only the packed rows (adjp); the others only adj and adjJ.
+PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
+                                      int nwarps, bool with_pool, bool packed) {
+    GraphLayout l;
+    size_t o = 0;
+    l.spins = o;  o = align16(o + (size_t)N * R4);
+    l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
+    l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
+    l.rowl = o;   o = align16(o + (size_t)N * 4);
+    l.adj = o;    o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
+    l.adjJ = o;   o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
+    l.adjp = o;   o = align16(o + (packed ? (size_t)2 * NE * 4 : 0));
+    l.h = o;      o = align16(o + (size_t)N * 4);
+    l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
+    l.E = o;      o = align16(o + (size_t)R4 * 4);
+    l.Eacc = o;   o = align16(o + (size_t)R4 * 4);
+    l.st = o;     o = align16(o + (size_t)4 * R * 4);
+    l.sow = o;    o = align16(o + (size_t)R4 * 2);
+    l.wos = o;    o = align16(o + (size_t)R * 2);
+    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
+    l.total = o;
+    return l;
+}
+
+}  // namespace pt

@@ -46,32 +46,4 @@ PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, b
     return l;
 }
 
-struct GraphLayout {
-    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, csites, E, Eacc, st, sow, wos, pbuf, total;
-};
-
-// Packed instances keep only the packed rows (adjp); the others only adj and adjJ.
-PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
-                                      int nwarps, bool with_pool, bool packed) {
-    GraphLayout l;
-    size_t o = 0;
-    l.spins = o;  o = align16(o + (size_t)N * R4);
-    l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
-    l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
-    l.rowl = o;   o = align16(o + (size_t)N * 4);
-    l.adj = o;    o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
-    l.adjJ = o;   o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
-    l.adjp = o;   o = align16(o + (packed ? (size_t)2 * NE * 4 : 0));
-    l.h = o;      o = align16(o + (size_t)N * 4);
-    l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
-    l.E = o;      o = align16(o + (size_t)R4 * 4);
-    l.Eacc = o;   o = align16(o + (size_t)R4 * 4);
-    l.st = o;     o = align16(o + (size_t)4 * R * 4);
-    l.sow = o;    o = align16(o + (size_t)R4 * 2);
-    l.wos = o;    o = align16(o + (size_t)R * 2);
-    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
-    l.total = o;
-    return l;
-}
-
 }  // namespace pt
