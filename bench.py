@@ -87,6 +87,13 @@ def workload(args, first: int, count: int):
     return insts, betas, prop, ids
 
 
+def workload_name(args) -> str:
+    return (f"batched TAPT: {args.instances} EA +-J instances per GPU, L={args.L} "
+            f"(N={args.L ** 3}), R={args.R} beta 0.1->3.0 geometric, proposals every 10 sweeps "
+            f"on {args.R - 2} slots from pools of {args.pool_size}, {args.sweeps_per_step} "
+            f"cycles per step")
+
+
 def make_config(args, pool_size):
     import paper_2509_23043_gb300 as pt
     return pt.Config(update=pt.METROPOLIS, sweeps_per_cycle=1, propose_every=10,
@@ -469,8 +476,9 @@ def run_reference(args):
         "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/u32 spins, f64 acceptance",
         "data": "synthetic",
-        "config": {"workload": f"batched TAPT, {args.instances} EA +-J L={args.L} instances, "
-                               f"R={args.R}, 100 sweeps per step (oracle sample)"},
+        "config": {"workload": workload_name(args), "global_batch": args.instances,
+                   "timed": "a bounded sample of the workload per step, on the host cores "
+                            "(see cpu_baseline.sample)"},
         "cpu_baseline": {"value": v, "unit": "attempts/ns", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "attempts/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -620,10 +628,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32 bit-packed spins, int32 energies, f64 acceptance",
             "data": "synthetic",
-            "config": {"workload": f"batched TAPT: {B} EA +-J instances per GPU, L={args.L} "
-                                   f"(N={args.L ** 3}), R={args.R} beta 0.1->3.0 geometric, "
-                                   f"proposals every 10 sweeps on 30 slots from pools of "
-                                   f"{args.pool_size}, {spc} cycles per step",
+            "config": {"workload": workload_name(args),
                        "global_batch": B * world, "l2": "flushed between timed steps",
                        "pool_generation_s": round(t_pool, 2),
                        "pool": f"PT runs of this library: {args.pool_burnin} burn-in sweeps, "

@@ -58,20 +58,26 @@ __device__ __forceinline__ int sbyte(uint32_t w, int k) {
     return (int)(int8_t)((w >> (8 * k)) & 0xFFu);
 }
 
-// One sweep: every free site of every colour class, four walkers per thread. Item q of a
-// class is (site q / Q, quad q % Q); the item stride Ts is a multiple of Q, so a thread keeps
-// one quad for the whole sweep and neighbouring lanes read neighbouring words of one row.
+// One sweep: every free site of every colour class, four walkers per thread. Thread t takes
+// quad t % Q of the sites t / Q, t / Q + Ts / Q, ... of each class (Ts, the threads used, a
+// multiple of Q), so it keeps one quad for the whole sweep and neighbouring lanes read
+// neighbouring words of one row.
 // With energy_on (the last sweep of a cycle) each thread adds, for its quad, the energy terms
 // of the free sites it updates: -m (h + the bonds to its counted neighbours, rowp..rowl),
 // which sum with Eclamp to the exact energy (each bond counted once, at the end updated
 // last); graph_energy_finish turns them into E.
 __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                             uint32_t sweep_idx, int update, bool energy_on) {
-    const int Q = I.R4 >> 2;
-    const int tw = 2 * I.Imax + 1;
+    // the instance's scalars in registers: the descriptor lives in global memory, and the
+    // shared-memory stores below would otherwise force it to be read again
+    const int Q = I.R4 >> 2, R = I.R, Imax = I.Imax, ncol = I.ncol;
+    const bool packed = I.packed != 0;
+    const uint32_t iid = I.iid;
+    const int tw = 2 * Imax + 1;
     const int Ts = (blockDim.x / Q) * Q;
     const int tid = threadIdx.x;
     const int quad = tid % Q;
+    const int s0 = tid / Q, sstep = Ts / Q;         // the thread's first site, site stride
     uint32_t* sp = reinterpret_cast<uint32_t*>(S.spins);
     // the thread's four walkers: threshold rows of their slots (fixed during a sweep), -1 for
     // walkers beyond R
@@ -79,19 +85,20 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
 #pragma unroll
     for (int k4 = 0; k4 < 4; ++k4) {
         const int w = quad * 4 + k4;
-        trow[k4] = (w < I.R) ? S.sow[w] * tw + I.Imax : -1;
+        trow[k4] = (w < R) ? S.sow[w] * tw + Imax : -1;
     }
     int e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-    for (int c = 0; c < I.ncol; ++c) {
-        const int base = I.col_off[c];
-        const int nc = I.col_off[c + 1] - base;
-        const int nitems = nc * Q;
-        for (int q = tid; q < nitems && tid < Ts; q += Ts) {
-            const int site = S.csites[base + q / Q];
+    int cbeg = I.col_off[0];
+    for (int c = 0; c < ncol; ++c) {
+        const int base = cbeg;
+        cbeg = I.col_off[c + 1];
+        const int nc = cbeg - base;
+        for (int si = s0; si < nc && tid < Ts; si += sstep) {
+            const int site = S.csites[base + si];
             const int hs = S.h[site];
             int g[4], f[4];                            // counted-neighbour sums, local fields
             const int split = S.rowl[site], end = S.rowp[site + 1];
-            if (I.packed) {
+            if (packed) {
                 // bytes of ac / ar: 128 + sum of J over the neighbours whose spin is -1
                 uint32_t ac = 0x80808080u, ar = 0x80808080u;
                 int sjc = 0, sjr = 0;
@@ -135,7 +142,7 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
             }
             const uint32_t own = sp[site * Q + quad];
             const uint4 r = philox_rk(make_uint4((uint32_t)site, sweep_idx,
-                                                 (kDomWord << 24) | (uint32_t)quad, I.iid), a);
+                                                 (kDomWord << 24) | (uint32_t)quad, iid), a);
             const uint32_t u[4] = {r.x, r.y, r.z, r.w};
             int nmv[4];
             uint32_t out = own;
@@ -162,7 +169,7 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                 e3 -= nmv[3] * (hs + g[3]);
             }
         }
-        if (energy_on && c == I.ncol - 1 && tid < Ts) {
+        if (energy_on && c == ncol - 1 && tid < Ts) {
             const int w = quad * 4;
             if (e0) atomicAdd(&S.Eacc[w + 0], e0);
             if (e1) atomicAdd(&S.Eacc[w + 1], e1);
