@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,ragged,factor",
+    p.add_argument("--workloads", default="plain,ragged,factor,ladder",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--serve-requests", type=int, default=48)
@@ -406,6 +406,30 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=64, chunk=1000):
                                           if (solved_at >= 0).any() else None)}
 
 
+def ladder_workload(stream, n=64, R=32, iterations=6, sweeps=2000):
+    """Ladder optimisation for uniform swap acceptance on the EA L=10 family (a shared
+    ladder, R=32 on 0.1 -> 3.0, starting geometric): swap acceptance per pair before and
+    after, from the library's own exchange statistics."""
+    import instances as I
+    from paper_2509_23043_gb300 import ladder as LD
+    insts = [I.ea_instance(10, seed=0x1ADD, index=k) for k in range(n)]
+    b0 = I.geometric_betas(0.1, 3.0, R)
+    t0 = time.perf_counter()
+    b, hist = LD.optimise_ladder(insts, b0, iterations=iterations, sweeps=sweeps,
+                                 stream=stream.cuda_stream)
+    _, last = LD.optimise_ladder(insts, b, iterations=1, sweeps=sweeps, seed=0x2ADD,
+                                 stream=stream.cuda_stream)
+    wall = time.perf_counter() - t0
+    a0, a1 = hist[0]["acceptance"], last[0]["acceptance"]
+    return {"workload": f"{n} EA L=10 instances, R={R} on 0.1->3.0, {iterations} rounds of "
+                        f"{sweeps} PT sweeps, then one check round",
+            "acceptance_geometric": {"min": float(a0.min()), "max": float(a0.max()),
+                                     "mean": float(a0.mean())},
+            "acceptance_optimised": {"min": float(a1.min()), "max": float(a1.max()),
+                                     "mean": float(a1.mean())},
+            "betas": [round(float(x), 4) for x in b], "wall_s": round(wall, 2)}
+
+
 def _ev_pair():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -614,6 +638,8 @@ def main():
             others["ragged_batch"] = ragged_batch(stream)
         if "factor" in wl:
             others["factorization"] = factorization(stream, args.factor_sweeps)
+        if "ladder" in wl:
+            others["ladder"] = ladder_workload(stream)
 
     cpu = None
     if cpu_pool is not None:

@@ -92,6 +92,12 @@ typedef struct {
  *  seed              64-bit key of every random stream.
  *  threads_per_block 0 = automatic choice; else a multiple of 32 in [32, 512] (lattice
  *                    engine) or [32, 1024] (graph engine).
+ *  proposal_rule     acceptance of a global proposal: 0 = the paper's Delta-E-only rule
+ *                    min[1, exp(beta_r (E_r - E^T))] (Eq. 2, an optimization heuristic);
+ *                    1 = always accept, which is the independent Metropolis-Hastings move
+ *                    when the pool entries are exact draws from the slot's Boltzmann law (the
+ *                    proposal-probability correction then cancels the Boltzmann ratio;
+ *                    Supplementary S2). Other values: PT_EINVAL.
  */
 typedef struct {
     int32_t update;
@@ -102,7 +108,7 @@ typedef struct {
     int32_t pool_size;
     uint64_t seed;
     int32_t threads_per_block;
-    int32_t reserved;
+    int32_t proposal_rule;
 } pt_config;
 
 /* Create a batch of n >= 1 instances (all lattice+Metropolis+J=+-1 without field or clamp,

@@ -114,6 +114,7 @@ struct or_inst {
     double *beta;
     uint8_t *prop;
     int32_t update, M, every, start, stop;
+    int32_t rule;             /* proposal rule: 0 Delta-E-only, 1 always accept */
     uint64_t seed;
     int32_t P;
     /* adjacency: for site i, neighbours adj_j[adj_off[i] .. adj_off[i+1]) with couplings */
@@ -219,9 +220,10 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_replicas, const double *beta, const uint8_t *prop_enabled,
                    int32_t update, int32_t sweeps_per_cycle, int32_t propose_every,
                    int32_t propose_start, int32_t propose_stop, uint64_t seed,
-                   int32_t pool_size) {
+                   int32_t pool_size, int32_t proposal_rule) {
     if (n_spins <= 0 || n_edges < 0 || n_replicas <= 0 || sweeps_per_cycle <= 0) return NULL;
     if (update != 0 && update != 1) return NULL;
+    if (proposal_rule != 0 && proposal_rule != 1) return NULL;
     if (lattice_L > 0 && lattice_L * lattice_L * lattice_L != n_spins) return NULL;
     for (int32_t e = 0; e < n_edges; ++e)
         if (ei[e] < 0 || ei[e] >= n_spins || ej[e] < 0 || ej[e] >= n_spins || ei[e] == ej[e])
@@ -232,6 +234,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     o->id = instance_id; o->N = n_spins; o->L = lattice_L; o->NE = n_edges; o->R = n_replicas;
     o->update = update; o->M = sweeps_per_cycle; o->every = propose_every;
     o->start = propose_start; o->stop = propose_stop; o->seed = seed;
+    o->rule = proposal_rule;
     o->P = pool_size > 0 ? pool_size : 0;
     o->ei = (int32_t *)xcalloc((size_t)n_edges, 4);
     o->ej = (int32_t *)xcalloc((size_t)n_edges, 4);
@@ -382,7 +385,7 @@ void or_propose(or_inst *o) {
         double x = o->beta[r] * (double)(o->E[r] - ET);
         uint32_t u = philox_word(o->seed, (uint32_t)r, (uint32_t)o->n_prop, 4u << 24, o->id, 0);
         o->prop_att[r]++;
-        if (or_accept(x, u)) {
+        if (o->rule == 1 || or_accept(x, u)) {
             memcpy(o->spins + (size_t)r * o->N, cand, (size_t)o->N);
             o->E[r] = ET;
             o->prop_acc[r]++;

@@ -48,6 +48,9 @@ int64_t or_energy(int32_t n, int32_t n_edges, const int32_t *ei, const int32_t *
 
 /* Create one instance. Inputs are copied. update: 0 Metropolis, 1 Gibbs.
  * propose_every = 0 disables proposals in or_run_cycles; propose_stop <= 0 means never stop.
+ * proposal_rule: 0 = the Delta-E-only rule of Eq. 2; 1 = always accept (the independent
+ * Metropolis-Hastings move for proposals drawn exactly from the slot's Boltzmann law, whose
+ * correction cancels the Boltzmann ratio; Supplementary S2).
  * Returns NULL on invalid input. */
 or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_edges, const int32_t *ei, const int32_t *ej, const int32_t *eJ,
@@ -55,7 +58,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_replicas, const double *beta, const uint8_t *prop_enabled,
                    int32_t update, int32_t sweeps_per_cycle, int32_t propose_every,
                    int32_t propose_start, int32_t propose_stop, uint64_t seed,
-                   int32_t pool_size);
+                   int32_t pool_size, int32_t proposal_rule);
 void or_destroy(or_inst *o);
 
 /* Store `count` configurations (+-1) for replica slot r at pool positions first.. */

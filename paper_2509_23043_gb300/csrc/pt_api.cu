@@ -191,6 +191,7 @@ RunArgs make_args(const pt_ctx* c, int mode, int nn) {
     a.start = c->cfg.propose_start;
     a.stop = c->cfg.propose_stop;
     a.update = c->cfg.update;
+    a.prule = c->cfg.proposal_rule;
     // Philox round keys: key bumped by the Weyl constants before each round after the first
     uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     for (int i = 0; i < 10; ++i) {
@@ -792,6 +793,8 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     if (cfg->sweeps_per_cycle < 1) return fail(PT_EINVAL, "sweeps_per_cycle must be >= 1");
     if (cfg->pool_size < 0) return fail(PT_EINVAL, "pool_size must be >= 0");
     if (cfg->propose_every < 0) return fail(PT_EINVAL, "propose_every must be >= 0");
+    if (cfg->proposal_rule != 0 && cfg->proposal_rule != 1)
+        return fail(PT_EINVAL, "proposal_rule must be 0 or 1");
     for (int k = 0; k < n; ++k) {
         pt_status s = validate(descs[k], k);
         if (s != PT_OK) return s;

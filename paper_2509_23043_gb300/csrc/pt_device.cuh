@@ -152,7 +152,7 @@ struct RunArgs {
     int32_t n;
     int32_t M, every, start, stop;
     int32_t update;      // graph engine: 0 Metropolis, 1 Gibbs
-    int32_t pad;
+    int32_t prule;       // proposal rule: 0 Delta-E-only, 1 always accept
     uint32_t rk0[10];    // Philox round keys of the seed (kernel parameters, so the rounds
     uint32_t rk1[10];    // read them as constant operands)
 };

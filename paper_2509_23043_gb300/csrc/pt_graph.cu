@@ -251,7 +251,7 @@ __device__ void graph_exchange(const GraphInst& I, GraphSmem& S, uint32_t k0, ui
 }
 
 __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
-                              long long n_prop) {
+                              long long n_prop, int rule) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int N = I.N, NW = I.NW;
     uint32_t* buf = S.pbuf + warp * NW;
@@ -275,7 +275,7 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
         int acc = 0;
         if (lane == 0) {
             const int dE = S.E[w] - ET;
-            acc = dE >= 0 || I.beta[r] == 0.0;
+            acc = rule == 1 || dE >= 0 || I.beta[r] == 0.0;
             if (!acc) {
                 const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid),
                                        k0, k1);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     }
     if (a.mode & kModePropose) {
         ++n_prop;
-        if (with_pool) graph_propose(I, S, k0, k1, n_prop);
+        if (with_pool) graph_propose(I, S, k0, k1, n_prop, a.prule);
         __syncthreads();
     }
     if (a.mode & kModeExchange) {
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
             graph_energy_finish(I, S);
             if (proposal_due(sweeps, a)) {
                 ++n_prop;
-                if (with_pool) graph_propose(I, S, k0, k1, n_prop);
+                if (with_pool) graph_propose(I, S, k0, k1, n_prop, a.prule);
                 __syncthreads();
             }
             ++n_ex;

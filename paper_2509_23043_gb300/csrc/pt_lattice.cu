@@ -382,7 +382,7 @@ __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
         const int w = wos[r];
         const int ET = 2 * S.us[r] - 3 * N;
         const int dE = S.E[w] - ET;                   // x = beta_r (E_r - E^T)
-        bool acc = dE >= 0 || S.beta[r] == 0.0;
+        bool acc = a.prule == 1 || dE >= 0 || S.beta[r] == 0.0;
         if (!acc) {
             const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid), a);
             acc = accept_ratio(S.beta[r], S.fbeta[r], dE, u.x);

@@ -164,3 +164,36 @@ def test_delta_e_only_biases_cold_replica_and_oracle_matches_exact_chain():
         assert tv < 4 * noise + 0.003, (r, tv, noise)
         if r < 2:   # the exact biased law, not Boltzmann, is what the oracle samples
             assert 0.5 * np.abs(q - pis[r]).sum() > 4 * noise + 0.003
+
+
+@pytest.mark.slow
+def test_always_accept_rule_oracle_keeps_boltzmann():
+    """With proposal_rule = 1 (the Metropolis-Hastings move for exact equilibrium proposals,
+    Supplementary S2), the oracle's marginals are the Boltzmann laws, as the exact chain's."""
+    m, pis, E = _stationary("always")
+    inst = _fa()
+    S = _states()
+    g = np.random.default_rng(2510)
+    P = 40000
+    o = O.Oracle(inst, BETAS, prop_enabled=[1, 1, 0], update=1, propose_every=1,
+                 seed=4343, pool_size=P, proposal_rule=1)
+    for r in range(2):
+        draw = g.choice(32, size=P, p=_pi(E, BETAS[r]))
+        o.load_pool(r, S[draw].astype(np.int8))
+    o.run_cycles(500)
+    n = 60000
+    hist = np.zeros((3, 32))
+    weights = 1 << np.arange(5)
+    for _ in range(n):
+        o.run_cycles(1)
+        s, _, _ = o.read()
+        for r in range(3):
+            hist[r, int(((s[r] > 0) * weights).sum())] += 1
+    for r in range(3):
+        q = hist[r] / n
+        tv = 0.5 * np.abs(q - pis[r]).sum()
+        noise = 0.5 * np.sum(np.sqrt(2 * pis[r] * (1 - pis[r]) / (np.pi * n / 3)))
+        assert tv < 4 * noise + 0.003, (r, tv, noise)
+    # every proposal is accepted
+    _, _, pa, ptot = o.stats()
+    assert pa[0] == ptot[0] and pa[1] == ptot[1] and ptot[0] > 0
