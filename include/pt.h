@@ -154,12 +154,12 @@ pt_status pt_sweep(pt_ctx *ctx, int32_t n_sweeps);
 /* One global-proposal event for every instance: for each r in R_prop, take the next pool
  * entry S^T_r (cursor advances by one mod P whether or not it is accepted), overwrite its
  * clamped spins, compute E^T_r exactly, and accept with min[1, exp(beta_r (E_r - E^T_r))]
- * (Eq. P_accept, evaluated in FP64). Uses the energies of the last sweep. */
+ * (Eq. 2, evaluated in FP64). Uses the energies of the last sweep. */
 pt_status pt_global_propose(pt_ctx *ctx);
 
 /* One replica-exchange event for every instance: event n (1-based) pairs slots (0,1),(2,3)..
  * when n is odd and (1,2),(3,4).. when n is even, and swaps the configurations and energies
- * of a pair with min[1, exp((beta_{r+1}-beta_r)(E_{r+1}-E_r))] (Eq. P_swap, FP64). */
+ * of a pair with min[1, exp((beta_{r+1}-beta_r)(E_{r+1}-E_r))] (Eq. 1, FP64). */
 pt_status pt_exchange(pt_ctx *ctx);
 
 /* n_cycles cycles of Algorithm 1, fused on the device: M sweeps, energies, a proposal event

@@ -372,7 +372,7 @@ void or_sweeps(or_inst *o, int32_t n) {
     recompute_energies(o);  /* Algorithm 1: exact energy of every replica */
 }
 
-/* Global proposals (Algorithm 1, Eq. P_accept). */
+/* Global proposals (Algorithm 1, Eq. 2). */
 void or_propose(or_inst *o) {
     o->n_prop++;
     if (o->P <= 0) return;
@@ -395,7 +395,7 @@ void or_propose(or_inst *o) {
     free(cand);
 }
 
-/* Replica exchange (Algorithm 1, Eq. P_swap): odd events pair slots (0,1),(2,3)...,
+/* Replica exchange (Algorithm 1, Eq. 1): odd events pair slots (0,1),(2,3)...,
  * even events pair (1,2),(3,4)...; a swap exchanges configurations and energies. */
 void or_exchange(or_inst *o) {
     o->n_ex++;

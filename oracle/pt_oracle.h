@@ -14,8 +14,8 @@
  *     (Methods, Gibbs update; u uniform 32-bit);
  *   - Metropolis: flip iff dE <= 0 or u < T_M(beta, dE), T_M = floor(2^32 exp(-beta dE));
  *     both thresholds are capped at 2^32 - 1;
- *   - replica exchange with P_swap = min[1, exp(dbeta dE)] (Eq. P_swap) and global proposal
- *     with P_accept = min[1, exp(beta_r (E_r - E^T))] (Eq. P_accept): accept iff x >= 0 or
+ *   - replica exchange with P_swap = min[1, exp(dbeta dE)] (Eq. 1) and global proposal
+ *     with P_accept = min[1, exp(beta_r (E_r - E^T))] (Eq. 2): accept iff x >= 0 or
  *     u + 1 <= 2^32 exp(x), evaluated in FP64;
  *   - random numbers from Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed,
  *     counters as documented in pt_oracle.c.

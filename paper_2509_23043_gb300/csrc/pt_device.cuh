@@ -24,7 +24,7 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
-// Global-move decision (Eq. P_swap and Eq. P_accept): accept with min[1, exp(x)] using a
+// Global-move decision (Eq. 1 and Eq. 2): accept with min[1, exp(x)] using a
 // 32-bit uniform u, i.e. iff x >= 0 or u + 1 <= 2^32 exp(x), decided as in FP64.
 // The FP64 exponential is only evaluated near a tie: a float evaluation is within a relative
 // 1.7e-6 of 2^32 exp(x) (|x| <= 22.2 rounded to float: 1.4e-6; expf within 2 ulp: 2.4e-7;
@@ -41,7 +41,7 @@ __device__ __forceinline__ bool accept_fp64(double x, uint32_t u) {
 }
 
 // The same decision for x = b * dE (b >= 0 an FP64 inverse-temperature difference or value,
-// dE an integer energy difference), the FP64 ratio of Eq. P_swap / Eq. P_accept. x >= 0 is
+// dE an integer energy difference), the FP64 ratio of Eq. 1 / Eq. 2. x >= 0 is
 // read off the signs; otherwise a float product of b and dE (relative error <= 3 * 2^-24 from
 // the FP64 product) feeds the float filter, and only near-ties evaluate the FP64 product and
 // exponential.

@@ -5,7 +5,7 @@
 // [wb][site] holds spin `site` of walkers 32*wb .. 32*wb+31, bit b set iff spin = +1. A
 // walker keeps its lane for the whole run; replica exchange permutes the slot <-> walker
 // labels (sow / wos) instead of moving spins, which gives the same chain as swapping
-// configurations (Eq. P_swap) since the random numbers of a local move are keyed by the walker.
+// configurations (Eq. 1) since the random numbers of a local move are keyed by the walker.
 //
 // Local move (Methods: local sweeps; Metropolis rule). Shared memory holds every spin word
 // next to its complement, and the table points a neighbour across a negative bond at the
@@ -290,7 +290,7 @@ __device__ __forceinline__ void lattice_store_energies(const LP& P, LatSmem& S, 
     }
 }
 
-// One exchange event (Eq. P_swap) on the labels of buffer q with energies E = 2 Ecount - 3N
+// One exchange event (Eq. 1) on the labels of buffer q with energies E = 2 Ecount - 3N
 // (Ecount != nullptr) or S.E: warp 0 decides every pair, writes the new labels to buffer q^1
 // and the statistics, and rebuilds the threshold planes from the new slot-of-walker map.
 // The caller synchronises afterwards.
@@ -331,7 +331,7 @@ __device__ void lattice_exchange(const LP& P, LatSmem& S, const RunArgs& a, long
     }
 }
 
-// One proposal event (Algorithm 1, Eq. P_accept) with energies in S.E and labels of buffer q.
+// One proposal event (Algorithm 1, Eq. 2) with energies in S.E and labels of buffer q.
 // A: stage the next pool entry of every proposal-enabled slot; B: count its unsatisfied
 // bonds (funnel shifts along x, y, z with the wrap masks; E^T = 2U - 3N); C: one thread per
 // slot decides in FP64 and advances the cursor; D: merge accepted entries into their walkers'
