@@ -50,7 +50,8 @@ def lib():
         L.or_create.argtypes = [C.c_uint32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                 C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
-                                C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_int32]
+                                C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_int32,
+                                C.c_int32, C.c_int32, C.c_int32]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_load_pool.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]
@@ -113,7 +114,8 @@ class Oracle:
     def __init__(self, inst, betas, *, instance_id: int = 0, prop_enabled=None,
                  update: int = 0, sweeps_per_cycle: int = 1, propose_every: int = 0,
                  propose_start: int = 0, propose_stop: int = 0, seed: int = 0,
-                 pool_size: int = 0, proposal_rule: int = 0):
+                 pool_size: int = 0, proposal_rule: int = 0, proposal_source: int = 0,
+                 context_log2: int = 1, context_sweeps: int = 1):
         self.inst = inst
         self.N = int(inst.n_spins)
         self.R = len(betas)
@@ -129,7 +131,8 @@ class Oracle:
                                  _ptr(ej), _ptr(eJ), _ptr(h), _ptr(cl), self.R, _ptr(b),
                                  _ptr(pe), update, sweeps_per_cycle, propose_every,
                                  propose_start, propose_stop, seed & 0xFFFFFFFFFFFFFFFF,
-                                 pool_size, proposal_rule)
+                                 pool_size, proposal_rule, proposal_source, context_log2,
+                                 context_sweeps)
         if not self.h:
             raise ValueError("oracle rejected the instance")
 

@@ -115,6 +115,8 @@ struct or_inst {
     uint8_t *prop;
     int32_t update, M, every, start, stop;
     int32_t rule;             /* proposal rule: 0 Delta-E-only, 1 always accept */
+    int32_t source;           /* proposal source: 0 pool, 1 contextual */
+    int32_t ctx_log2, ctx_sweeps;
     uint64_t seed;
     int32_t P;
     /* adjacency: for site i, neighbours adj_j[adj_off[i] .. adj_off[i+1]) with couplings */
@@ -220,10 +222,14 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_replicas, const double *beta, const uint8_t *prop_enabled,
                    int32_t update, int32_t sweeps_per_cycle, int32_t propose_every,
                    int32_t propose_start, int32_t propose_stop, uint64_t seed,
-                   int32_t pool_size, int32_t proposal_rule) {
+                   int32_t pool_size, int32_t proposal_rule, int32_t proposal_source,
+                   int32_t context_log2, int32_t context_sweeps) {
     if (n_spins <= 0 || n_edges < 0 || n_replicas <= 0 || sweeps_per_cycle <= 0) return NULL;
     if (update != 0 && update != 1) return NULL;
     if (proposal_rule != 0 && proposal_rule != 1) return NULL;
+    if (proposal_source != 0 && proposal_source != 1) return NULL;
+    if (proposal_source == 1 && (context_log2 < 1 || context_log2 > 3 || context_sweeps < 1))
+        return NULL;
     if (lattice_L > 0 && lattice_L * lattice_L * lattice_L != n_spins) return NULL;
     for (int32_t e = 0; e < n_edges; ++e)
         if (ei[e] < 0 || ei[e] >= n_spins || ej[e] < 0 || ej[e] >= n_spins || ei[e] == ej[e])
@@ -235,6 +241,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     o->update = update; o->M = sweeps_per_cycle; o->every = propose_every;
     o->start = propose_start; o->stop = propose_stop; o->seed = seed;
     o->rule = proposal_rule;
+    o->source = proposal_source; o->ctx_log2 = context_log2; o->ctx_sweeps = context_sweeps;
     o->P = pool_size > 0 ? pool_size : 0;
     o->ei = (int32_t *)xcalloc((size_t)n_edges, 4);
     o->ej = (int32_t *)xcalloc((size_t)n_edges, 4);
@@ -261,6 +268,11 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     o->prop = (uint8_t *)xcalloc((size_t)n_replicas, 1);
     if (prop_enabled) memcpy(o->prop, prop_enabled, (size_t)n_replicas);
     o->bitplane = (lattice_L > 0 && update == 0 && !has_h && !has_clamp && unit_J);
+    if (proposal_source == 1) {
+        int32_t n_en = 0;
+        for (int32_t r = 0; r < n_replicas; ++r) n_en += o->prop[r] != 0;
+        if (!o->bitplane || n_en > 32) { or_destroy(o); return NULL; }
+    }
 
     /* adjacency lists (each edge seen from both ends; parallel edges kept apart) */
     o->adj_off = (int32_t *)xcalloc((size_t)n_spins + 1, 4);
@@ -372,9 +384,76 @@ void or_sweeps(or_inst *o, int32_t n) {
     recompute_energies(o);  /* Algorithm 1: exact energy of every replica */
 }
 
+/* Contextual proposals (Supplementary S3). The enabled slots, in ascending order, are
+ * numbered j = 0, 1, ...; the random numbers of proposal j are bit j of these Philox words:
+ *  - site i is kept (clamped) iff bits j of output words 0 .. context_log2-1 of
+ *    Philox(i, event, 5 << 24 | 0xFF << 16, id) are all set (probability 2^-context_log2);
+ *  - refill sweep t = (event - 1) * context_sweeps + k draws its 32-bit uniform at site i
+ *    from the bit planes of Philox(i, t, 5 << 24 | (plane / 4) << 16, id), plane 0 the most
+ *    significant bit, as the local moves of the walkers do. */
+static uint32_t ctx_uniform(const or_inst *o, int32_t site, uint32_t t, int32_t j) {
+    uint32_t u = 0;
+    for (int k = 0; k < 32; ++k) {
+        uint32_t c2 = (5u << 24) | ((uint32_t)(k >> 2) << 16);
+        uint32_t word = philox_word(o->seed, (uint32_t)site, t, c2, o->id, k & 3);
+        u |= ((word >> j) & 1u) << (31 - k);
+    }
+    return u;
+}
+
+static void context_candidate(const or_inst *o, int32_t r, int32_t j, int8_t *cand) {
+    const int8_t *cur = o->spins + (size_t)r * o->N;
+    memcpy(cand, cur, (size_t)o->N);
+    uint8_t *kept = (uint8_t *)xcalloc((size_t)o->N, 1);
+    for (int32_t i = 0; i < o->N; ++i) {
+        int all = 1;
+        for (int q = 0; q < o->ctx_log2; ++q) {
+            uint32_t word = philox_word(o->seed, (uint32_t)i, (uint32_t)o->n_prop,
+                                        (5u << 24) | (0xFFu << 16), o->id, q);
+            all &= (int)((word >> j) & 1u);
+        }
+        kept[i] = (uint8_t)all;
+    }
+    for (int32_t k = 0; k < o->ctx_sweeps; ++k) {
+        uint32_t t = (uint32_t)((o->n_prop - 1) * o->ctx_sweeps + k);
+        for (int32_t c = 0; c < o->ncol; ++c) {
+            for (int32_t i = 0; i < o->N; ++i) {
+                if (o->colour[i] != c || kept[i]) continue;
+                int32_t I = o->h[i];
+                for (int32_t a = o->adj_off[i]; a < o->adj_off[i + 1]; ++a)
+                    I += o->adj_J[a] * cand[o->adj_j[a]];
+                int32_t dE = 2 * cand[i] * I;
+                if (dE <= 0 || ctx_uniform(o, i, t, j) < or_metropolis_threshold(o->beta[r], dE))
+                    cand[i] = (int8_t)-cand[i];
+            }
+        }
+    }
+    free(kept);
+}
+
 /* Global proposals (Algorithm 1, Eq. 2). */
 void or_propose(or_inst *o) {
     o->n_prop++;
+    if (o->source == 1) {
+        int8_t *cand = (int8_t *)xcalloc((size_t)o->N, 1);
+        int32_t j = 0;
+        for (int32_t r = 0; r < o->R; ++r) {
+            if (!o->prop[r]) continue;
+            context_candidate(o, r, j, cand);   /* from the slot's state before this event */
+            ++j;
+            int32_t ET = energy_of(o, cand);
+            double x = o->beta[r] * (double)(o->E[r] - ET);
+            uint32_t u = philox_word(o->seed, (uint32_t)r, (uint32_t)o->n_prop, 4u << 24, o->id, 0);
+            o->prop_att[r]++;
+            if (o->rule == 1 || or_accept(x, u)) {
+                memcpy(o->spins + (size_t)r * o->N, cand, (size_t)o->N);
+                o->E[r] = ET;
+                o->prop_acc[r]++;
+            }
+        }
+        free(cand);
+        return;
+    }
     if (o->P <= 0) return;
     int8_t *cand = (int8_t *)xcalloc((size_t)o->N, 1);
     for (int32_t r = 0; r < o->R; ++r) {

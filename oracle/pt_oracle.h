@@ -51,6 +51,10 @@ int64_t or_energy(int32_t n, int32_t n_edges, const int32_t *ei, const int32_t *
  * proposal_rule: 0 = the Delta-E-only rule of Eq. 2; 1 = always accept (the independent
  * Metropolis-Hastings move for proposals drawn exactly from the slot's Boltzmann law, whose
  * correction cancels the Boltzmann ratio; Supplementary S2).
+ * proposal_source: 0 = the pool; 1 = contextual proposals (Supplementary S3): a copy of the
+ * slot's configuration with every spin kept (clamped) with probability 2^-context_log2
+ * (1..3) and the others refilled by context_sweeps (>= 1) Metropolis sweeps at the slot's
+ * beta. Contextual proposals need the bit-plane lattice case and at most 32 enabled slots.
  * Returns NULL on invalid input. */
 or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_edges, const int32_t *ei, const int32_t *ej, const int32_t *eJ,
@@ -58,7 +62,8 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t n_replicas, const double *beta, const uint8_t *prop_enabled,
                    int32_t update, int32_t sweeps_per_cycle, int32_t propose_every,
                    int32_t propose_start, int32_t propose_stop, uint64_t seed,
-                   int32_t pool_size, int32_t proposal_rule);
+                   int32_t pool_size, int32_t proposal_rule, int32_t proposal_source,
+                   int32_t context_log2, int32_t context_sweeps);
 void or_destroy(or_inst *o);
 
 /* Store `count` configurations (+-1) for replica slot r at pool positions first.. */

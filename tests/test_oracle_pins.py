@@ -380,3 +380,48 @@ def test_checkpoint_resume_is_exact():
     c.run_cycles(20)
     for x, y in zip(a.read(), c.read()):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("log2", [1, 2, 3])
+def test_contextual_proposal_keeps_the_stated_fraction(log2):
+    # Supplementary S3 contextual proposals: at beta = 0 every refilled spin flips (Metropolis
+    # at beta = 0 accepts every move) and every proposal is accepted, so one proposal event
+    # flips exactly the spins that were not kept: a fraction 1 - 2^-log2 of them.
+    inst = I.ea_instance(10, index=3)
+    o = O.Oracle(inst, [0.0, 0.0], prop_enabled=[1, 1], seed=17, proposal_source=1,
+                 context_log2=log2, context_sweeps=1)
+    changed, total = 0, 0
+    for _ in range(20):
+        before, _, _ = o.read()
+        o.propose()
+        after, _, _ = o.read()
+        changed += int((before != after).sum())
+        total += before.size
+    f = changed / total
+    expect = 1.0 - 2.0 ** -log2
+    assert abs(f - expect) < 4 * np.sqrt(expect * (1 - expect) / total), (f, expect)
+
+
+def test_always_accepted_contextual_proposals_keep_boltzmann():
+    # Copying a replica, freezing a random subset chosen independently of the state and
+    # running Metropolis sweeps on the rest leaves pi_beta invariant, so with every proposal
+    # accepted (proposal_rule 1) the slot marginals stay Boltzmann. A mistake in the refill
+    # (a wrong sign, a wrong beta, a frozen spin moved) would not.
+    inst = I.ea_instance(2, index=5)
+    betas = np.array([0.35, 0.9])
+    o = O.Oracle(inst, betas, prop_enabled=[1, 1], propose_every=1, seed=23,
+                 proposal_rule=1, proposal_source=1, context_log2=1, context_sweeps=2)
+    N = inst.n_spins
+    hist = np.zeros((2, 2 ** N))
+    weights = 1 << np.arange(N)
+    o.run_cycles(200)
+    for _ in range(40000):
+        o.run_cycles(1)
+        s, _, _ = o.read()
+        for r in range(2):
+            hist[r, int(((s[r] > 0) * weights).sum())] += 1
+    for r in range(2):
+        p, E = _boltzmann(inst, betas[r])
+        _assert_matches(p, hist[r] / hist[r].sum(), 40000, E)
+    _, _, pa, pt_ = o.stats()
+    assert np.array_equal(pa, pt_) and pt_[0] > 0
