@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,ragged,factor,ladder",
+    p.add_argument("--workloads", default="plain,ragged,factor,ladder,context",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--serve-requests", type=int, default=48)
@@ -430,6 +430,59 @@ def ladder_workload(stream, n=64, R=32, iterations=6, sweeps=2000):
             "betas": [round(float(x), 4) for x in b], "wall_s": round(wall, 2)}
 
 
+def context_ablation(stream, n=64, L=10, R=32, sweeps=3000, chunk=500):
+    """Supplementary S3-style comparison on n EA L=10 instances, R=32 on 0.1 -> 3.0: plain PT,
+    pool proposals (PT-run pools, as in the main workload) and contextual proposals keeping
+    50 / 25 / 12.5 % of the spins (2 refill sweeps), every 10 sweeps from sweep 100 on the 30
+    hottest slots. Reported: mean residual energy per spin of the best slot against a long
+    PT reference (2e5 sweeps, untimed), at checkpoints, and the device time of each run."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    from paper_2509_23043_gb300 import serve as SV
+    insts = [I.ea_instance(L, seed=0xC0DE, index=k) for k in range(n)]
+    betas = I.geometric_betas(0.1, 3.0, R)
+    prop = [1] * (R - 2) + [0, 0]
+    ids = list(range(n))
+    eref = np.array(SV.reference_energies(insts, [betas] * n, ids, sweeps=200_000, chunk=5000,
+                                          stream=stream.cuda_stream))
+    pools = SV.make_pools(insts, [betas] * n, ids, 256, burnin=20_000, gap=40,
+                          stream=stream.cuda_stream)
+    N = L ** 3
+    modes = {"plain_pt": dict(),
+             "pool": dict(propose_every=10, propose_start=100, pool_size=256),
+             "context_50": dict(propose_every=10, propose_start=100, proposal_source=1,
+                                context_log2=1, context_sweeps=2),
+             "context_25": dict(propose_every=10, propose_start=100, proposal_source=1,
+                                context_log2=2, context_sweeps=2),
+             "context_12": dict(propose_every=10, propose_start=100, proposal_source=1,
+                                context_log2=3, context_sweeps=2)}
+    out = {}
+    for name, kw in modes.items():
+        ctx = pt.create_instances(insts, [betas] * n, pt.Config(seed=0xAB1A, **kw),
+                                  prop_enabled=[prop] * n, instance_ids=ids,
+                                  stream=stream.cuda_stream)
+        if kw.get("pool_size"):
+            for k in range(n):
+                pt.load_proposals_inst_packed(ctx, k, pools[k])
+        best = np.full(n, 10 ** 9)
+        curve, t_ms, done = {}, 0.0, 0
+        while done < sweeps:
+            s, e = _ev_pair()
+            s.record(stream)
+            pt.run_cycles(ctx, chunk)
+            e.record(stream)
+            e.synchronize()
+            t_ms += s.elapsed_time(e)
+            done += chunk
+            best = np.minimum(best, np.array([x.min() for x in pt.energies(ctx)]))
+            curve[done] = float(np.mean((best - eref) / N))
+        pt.destroy(ctx)
+        out[name] = {"residual_per_spin": curve, "device_ms": round(t_ms, 2)}
+    return {"workload": f"{n} EA L={L} instances, R={R} on 0.1->3.0, {sweeps} sweeps, proposals "
+                        f"every 10 from sweep 100 on {R - 2} slots; reference: best of 2e5 PT "
+                        f"sweeps", "modes": out}
+
+
 def _ev_pair():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -640,6 +693,8 @@ def main():
             others["factorization"] = factorization(stream, args.factor_sweeps)
         if "ladder" in wl:
             others["ladder"] = ladder_workload(stream)
+        if "context" in wl:
+            others["context_ablation"] = context_ablation(stream)
 
     cpu = None
     if cpu_pool is not None:

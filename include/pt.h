@@ -98,6 +98,14 @@ typedef struct {
  *                    when the pool entries are exact draws from the slot's Boltzmann law (the
  *                    proposal-probability correction then cancels the Boltzmann ratio;
  *                    Supplementary S2). Other values: PT_EINVAL.
+ *  proposal_source   0 = proposals from the pools (pt_load_proposals...); 1 = contextual
+ *                    proposals (Supplementary S3), lattice engine only: at each event every
+ *                    proposal-enabled slot (at most 32 per instance) copies its configuration,
+ *                    keeps each site with probability 2^-context_log2 (1, 2 or 3: 50, 25 or
+ *                    12.5 %), refills the other sites by context_sweeps (>= 1) Metropolis
+ *                    sweeps at its beta, and the result is accepted by proposal_rule. Pools
+ *                    are not used. Violations: PT_EINVAL, or PT_ENOTSUP for the graph engine
+ *                    or more than 32 enabled slots.
  */
 typedef struct {
     int32_t update;
@@ -109,6 +117,9 @@ typedef struct {
     uint64_t seed;
     int32_t threads_per_block;
     int32_t proposal_rule;
+    int32_t proposal_source;
+    int32_t context_log2;
+    int32_t context_sweeps;
 } pt_config;
 
 /* Create a batch of n >= 1 instances (all lattice+Metropolis+J=+-1 without field or clamp,

@@ -22,6 +22,7 @@ _STATUS = {0: "PT_OK", 1: "PT_EINVAL", 2: "PT_ENOMEM", 3: "PT_ECUDA", 4: "PT_ETI
            5: "PT_ESTATE", 6: "PT_ENOTSUP"}
 METROPOLIS, GIBBS = 0, 1
 DELTA_E_ONLY, ALWAYS_ACCEPT = 0, 1     # proposal rules
+POOL, CONTEXT = 0, 1                   # proposal sources
 
 
 class PTError(RuntimeError):
@@ -41,7 +42,9 @@ class _Config(C.Structure):
     _fields_ = [("update", C.c_int32), ("sweeps_per_cycle", C.c_int32),
                 ("propose_every", C.c_int32), ("propose_start", C.c_int32),
                 ("propose_stop", C.c_int32), ("pool_size", C.c_int32), ("seed", C.c_uint64),
-                ("threads_per_block", C.c_int32), ("proposal_rule", C.c_int32)]
+                ("threads_per_block", C.c_int32), ("proposal_rule", C.c_int32),
+                ("proposal_source", C.c_int32), ("context_log2", C.c_int32),
+                ("context_sweeps", C.c_int32)]
 
 
 EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed",
@@ -139,12 +142,16 @@ class Config:
     seed: int = 0
     threads_per_block: int = 0
     proposal_rule: int = DELTA_E_ONLY
+    proposal_source: int = POOL
+    context_log2: int = 1
+    context_sweeps: int = 1
 
     def _c(self) -> _Config:
         return _Config(self.update, self.sweeps_per_cycle, self.propose_every,
                        self.propose_start, self.propose_stop, self.pool_size,
                        self.seed & 0xFFFFFFFFFFFFFFFF, self.threads_per_block,
-                       self.proposal_rule)
+                       self.proposal_rule, self.proposal_source, self.context_log2,
+                       self.context_sweeps)
 
 
 class Context:

@@ -144,6 +144,7 @@ struct pt_ctx {
     pt_config cfg{};
     cudaStream_t stream = nullptr;
     int with_pool = 0;
+    int with_ctx = 0;         // contextual proposals (lattice engine)
     int NWmax = 0;
     int uniformN = -1;        // N when all instances share it, else -1
     int optin = 0;            // device limit on dynamic shared memory per block
@@ -192,6 +193,8 @@ RunArgs make_args(const pt_ctx* c, int mode, int nn) {
     a.stop = c->cfg.propose_stop;
     a.update = c->cfg.update;
     a.prule = c->cfg.proposal_rule;
+    a.ctx_log2 = c->cfg.context_log2;
+    a.ctx_sweeps = c->cfg.context_sweeps;
     // Philox round keys: key bumped by the Weyl constants before each round after the first
     uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     for (int i = 0; i < 10; ++i) {
@@ -211,8 +214,9 @@ cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, i
         const int per_thread = (g.maxitems / std::max(g.maxW, 1) + g.T - 1) / g.T;
         const int counting = (c->L[g.members[0]] % 2 == 0) ? 1 : 2;
         const int kb4 = 6 * per_thread * counting < 16 ? 1 : 0;
+        const int flags = (c->with_pool ? kWithPool : 0) | (c->with_ctx ? kWithContext : 0);
         return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, kb4, g.T, g.smem, a,
-                              c->with_pool, s);
+                              flags, s);
     }
     return launch_graph(static_cast<const GraphInst*>(d_insts), count, g.T, g.smem, a, c->with_pool, s);
 }
@@ -418,7 +422,8 @@ pt_status lattice_group_shape(pt_ctx* c, Group& g, int T) {
         return fail(PT_ENOTSUP, "too many words per thread (%d); raise threads_per_block", (g.maxitems + T - 1) / T);
     size_t smem = 0;
     for (int k : g.members) {
-        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0);
+        const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0,
+                                           c->with_ctx != 0);
         smem = std::max(smem, l.total);
     }
     if (smem > (size_t)c->optin)
@@ -435,6 +440,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     c->loff.resize(n);
     std::vector<int> maxitems(n);
     c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
+    c->with_ctx = c->cfg.proposal_source == 1 ? 1 : 0;
     for (int k = 0; k < n; ++k) {
         const pt_instance_desc& d = descs[k];
         LatHost h;
@@ -784,6 +790,16 @@ extern "C" {
 
 const char* pt_last_error(void) { return g_err.c_str(); }
 
+// Contextual proposals hold one scratch lane per enabled slot: at most 32 per instance.
+pt_status context_slots_ok(const pt_instance_desc& d, int k) {
+    int nen = 0;
+    if (d.prop_enabled)
+        for (int r = 0; r < d.n_replicas; ++r) nen += d.prop_enabled[r] != 0;
+    if (nen > 32)
+        return fail(PT_ENOTSUP, "instance %d: %d proposal-enabled slots; contextual proposals take at most 32", k, nen);
+    return PT_OK;
+}
+
 pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32_t n,
                               const pt_config* cfg, void* cuda_stream) {
     if (!out || !descs || !cfg) return fail(PT_EINVAL, "NULL argument");
@@ -795,6 +811,20 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     if (cfg->propose_every < 0) return fail(PT_EINVAL, "propose_every must be >= 0");
     if (cfg->proposal_rule != 0 && cfg->proposal_rule != 1)
         return fail(PT_EINVAL, "proposal_rule must be 0 or 1");
+    if (cfg->proposal_source != 0 && cfg->proposal_source != 1)
+        return fail(PT_EINVAL, "proposal_source must be 0 or 1");
+    if (cfg->proposal_source == 1) {
+        if (cfg->context_log2 < 1 || cfg->context_log2 > 3)
+            return fail(PT_EINVAL, "context_log2 must be 1, 2 or 3");
+        if (cfg->context_sweeps < 1) return fail(PT_EINVAL, "context_sweeps must be >= 1");
+        for (int k = 0; k < n; ++k) {
+            if (!is_lattice_desc(descs[k], *cfg))
+                return fail(PT_ENOTSUP, "instance %d: contextual proposals are implemented for the "
+                                        "lattice engine (Metropolis, J = +-1, no field or clamp)", k);
+            pt_status s = context_slots_ok(descs[k], k);
+            if (s != PT_OK) return s;
+        }
+    }
     for (int k = 0; k < n; ++k) {
         pt_status s = validate(descs[k], k);
         if (s != PT_OK) return s;
@@ -1012,6 +1042,10 @@ pt_status pt_set_instance(pt_ctx* ctx, int32_t inst, const pt_instance_desc* des
     s = validate(*desc, inst);
     if (s != PT_OK) return s;
     if (!is_lattice_desc(*desc, ctx->cfg)) return fail(PT_EINVAL, "the new instance needs the lattice engine");
+    if (ctx->with_ctx) {
+        s = context_slots_ok(*desc, inst);
+        if (s != PT_OK) return s;
+    }
     if (desc->lattice_L != ctx->L[inst] || desc->n_replicas != ctx->R[inst])
         return fail(PT_EINVAL, "slot %d holds L=%d, R=%d; the new instance must have the same shape",
                     inst, ctx->L[inst], ctx->R[inst]);

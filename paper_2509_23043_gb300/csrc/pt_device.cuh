@@ -8,7 +8,8 @@ namespace pt {
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // Random-stream domains: the top byte of counter word 2 (see the kernels for the layout).
-constexpr uint32_t kDomInit = 0u, kDomPlane = 1u, kDomWord = 2u, kDomExch = 3u, kDomProp = 4u;
+constexpr uint32_t kDomInit = 0u, kDomPlane = 1u, kDomWord = 2u, kDomExch = 3u, kDomProp = 4u,
+                   kDomCtx = 5u;
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64-bit
 // multiplies with xors, key bumped by the Weyl constants between rounds.
@@ -137,6 +138,9 @@ struct LatInst {
     unsigned long long* stats;  // [4][R]: swap acc, swap att, prop acc, prop att
 };
 
+// Lattice kernel flags: pool proposals, contextual proposals
+constexpr int kWithPool = 1, kWithContext = 2;
+
 // Kernel modes
 enum : int32_t {
     kModeSweeps = 1,     // n sweeps then energies
@@ -153,6 +157,8 @@ struct RunArgs {
     int32_t M, every, start, stop;
     int32_t update;      // graph engine: 0 Metropolis, 1 Gibbs
     int32_t prule;       // proposal rule: 0 Delta-E-only, 1 always accept
+    int32_t ctx_log2;    // contextual proposals: a site is kept with probability 2^-ctx_log2
+    int32_t ctx_sweeps;  // contextual proposals: refill sweeps
     uint32_t rk0[10];    // Philox round keys of the seed (kernel parameters, so the rounds
     uint32_t rk1[10];    // read them as constant operands)
 };

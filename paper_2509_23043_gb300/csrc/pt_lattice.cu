@@ -69,11 +69,16 @@ struct LatSmem {
     uint32_t* st;      // [4][R]   statistics of this launch
     int16_t* sow;      // [2][W*32] slot of walker, double-buffered
     int16_t* wos;      // [2][W*32] walker of slot, double-buffered
+    // contextual proposals only: spins and tw hold one more block (the scratch lanes)
+    uint32_t* cm;      // [N]  lanes whose site is kept in this event
+    int16_t* cslot;    // [32] slot of scratch lane j (the enabled slots in order)
+    int32_t* ccnt;     // [32] bond counts of the scratch lanes
+    int32_t* cmisc;    // [2]  number of enabled slots, mask of accepted lanes
 };
 
 __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I, int nwarps,
-                                                 bool with_pool) {
-    const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool);
+                                                 bool with_pool, bool with_ctx) {
+    const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool, with_ctx);
     LatSmem S;
     S.tw = reinterpret_cast<uint4*>(base + l.tw);
     S.spins = reinterpret_cast<uint2*>(base + l.spins);
@@ -94,6 +99,10 @@ __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I
     S.st = reinterpret_cast<uint32_t*>(base + l.st);
     S.sow = reinterpret_cast<int16_t*>(base + l.sow);
     S.wos = reinterpret_cast<int16_t*>(base + l.wos);
+    S.cm = reinterpret_cast<uint32_t*>(base + l.cm);
+    S.cslot = reinterpret_cast<int16_t*>(base + l.cslot);
+    S.ccnt = reinterpret_cast<int32_t*>(base + l.ccnt);
+    S.cmisc = reinterpret_cast<int32_t*>(base + l.cmisc);
     return S;
 }
 
@@ -416,14 +425,152 @@ __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
     __syncthreads();
 }
 
-template <int MAXW, int KB>
+// Threshold planes of the scratch lanes: lane j takes the thresholds of slot cslot[j]; lanes
+// beyond the enabled slots get zero thresholds (they are masked out anyway). One warp.
+__device__ __forceinline__ void build_context_planes(const LP& P, LatSmem& S) {
+    const int lane = threadIdx.x & 31;
+    const int slot = lane < S.cmisc[0] ? S.cslot[lane] : -1;
+    const uint4 t = slot >= 0 ? S.thr[slot] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t x = warp_transpose32(__brev(t.x), lane);
+    const uint32_t y = warp_transpose32(__brev(t.y), lane);
+    const uint32_t z = warp_transpose32(__brev(t.z), lane);
+    S.tw[P.W * 32 + lane] = make_uint4(x, y, z, 0u);
+}
+
+// One contextual proposal event (Supplementary S3) for every enabled slot at once, with
+// energies in S.E and labels of buffer q. Scratch lane j carries the proposal of the j-th
+// enabled slot:
+//  A: copy each slot's configuration into its lane and draw the kept sites (lane j keeps a
+//     site iff bits j of Philox words 0 .. ctx_log2-1 of (site, event, 5 << 24 | 0xFF << 16)
+//     are set);
+//  B: ctx_sweeps Metropolis sweeps of the scratch block at each lane's slot temperature,
+//     kept sites frozen: the walkers' word update with a per-word lane mask, uniforms from the
+//     bit planes of Philox(site, (event - 1) ctx_sweeps + k, 5 << 24 | plane block << 16);
+//     the last sweep counts the lanes' unsatisfied bonds (E^T = 2U - 3N);
+//  C: one thread per enabled slot decides (the uniform as for pool proposals);
+//  D: accepted lanes are copied bit by bit into their walkers. Ends synchronised.
+template <int KB>
+__device__ void lattice_context_propose(const LP& P, LatSmem& S, const RunArgs& a,
+                                        long long n_prop, int q) {
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    const int N = P.N, W = P.W, WR = W * 32, R = P.R;
+    const int16_t* wos = S.wos + q * WR;
+    const int nen = S.cmisc[0];
+    const uint32_t lanes = nen >= 32 ? kFull : ((1u << nen) - 1u);
+    uint2* scr = S.spins + W * N;
+    const uint8_t* scr_b = reinterpret_cast<const uint8_t*>(scr);
+    // A
+    for (int p = tid; p < N; p += T) {
+        uint32_t word = 0;
+        for (int j = 0; j < nen; ++j) {
+            const int w = wos[S.cslot[j]];
+            word |= ((S.spins[(w >> 5) * N + p].x >> (w & 31)) & 1u) << j;
+        }
+        scr[p] = make_uint2(word, ~word);
+        const uint32_t site = S.itab[p].x & 0xFFFFu;
+        const uint4 r = philox_rk(make_uint4(site, (uint32_t)n_prop, (kDomCtx << 24) | (0xFFu << 16),
+                                             P.iid), a);
+        uint32_t kept = r.x;
+        if (a.ctx_log2 >= 2) kept &= r.y;
+        if (a.ctx_log2 >= 3) kept &= r.z;
+        S.cm[p] = kept;
+    }
+    if (tid == 0) S.cmisc[1] = 0;
+    __syncthreads();
+    // B
+    uint32_t cnt[KB];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) cnt[j] = 0u;
+    const uint4* tw = S.tw + W * 32;
+    for (int k = 0; k < a.ctx_sweeps; ++k) {
+        const uint32_t t = (uint32_t)((n_prop - 1) * a.ctx_sweeps + k);
+        const bool last = k == a.ctx_sweeps - 1;
+        for (int c = 0; c < P.ncol; ++c) {
+            const int base = P.cb[c];
+            const int nc = P.cb[c + 1] - base;
+            for (int kk = tid; kk < nc; kk += T) {
+                const int pp = base + kk;
+                const uint4 it = S.itab[pp];
+                const uint32_t s = scr[pp].x;
+                uint32_t m[6], b0, b1, b2;
+                bond_count(scr_b, it, s, m, b0, b1, b2);
+                const uint32_t movable = lanes & ~S.cm[pp];
+                const uint32_t always = b2 | (b1 & b0);    // count >= 3: dE <= 0
+                uint32_t und = ~always & movable, lt = 0;
+                const uint32_t site = it.x & 0xFFFFu;
+                for (uint32_t qb = 0; qb < 8 && und; ++qb) {
+                    const uint4 r = philox_rk(make_uint4(site, t, (kDomCtx << 24) | (qb << 16), P.iid), a);
+                    compare4(r, tw + 4 * qb, b0, b1, und, lt);
+                }
+                const uint32_t flip = (always | lt) & movable;
+                if (flip) scr[pp] = make_uint2(s ^ flip, ~(s ^ flip));
+                if (last && c > 0) count_lower_bonds(cnt, it.x >> 16, m, s ^ flip, b0, b1, b2, flip);
+            }
+            __syncthreads();
+        }
+    }
+    {
+        uint32_t tx[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) tx[j] = warp_transpose32(cnt[j], lane);
+        uint32_t accu = 0;
+#pragma unroll
+        for (int j = 0; j < KB; ++j) accu += (uint32_t)__popc(tx[j]) << j;
+        if (accu) atomicAdd(&S.ccnt[lane], (int)accu);
+    }
+    __syncthreads();
+    // C (every lane's count is cleared for the next event)
+    const int cj = tid < 32 ? S.ccnt[tid] : 0;
+    if (tid < 32) S.ccnt[tid] = 0;
+    if (tid < nen) {
+        const int j = tid, r = S.cslot[j], w = wos[r];
+        const int ET = 2 * cj - 3 * N;
+        const int dE = S.E[w] - ET;                   // x = beta_r (E_r - E^T)
+        bool acc = a.prule == 1 || dE >= 0 || S.beta[r] == 0.0;
+        if (!acc) {
+            const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, P.iid), a);
+            acc = accept_ratio(S.beta[r], S.fbeta[r], dE, u.x);
+        }
+        S.st[3 * R + r] += 1u;
+        if (acc) {
+            S.st[2 * R + r] += 1u;
+            S.E[w] = ET;
+            atomicOr(reinterpret_cast<unsigned*>(&S.cmisc[1]), 1u << j);
+        }
+    }
+    __syncthreads();
+    // D
+    const uint32_t am = (uint32_t)S.cmisc[1];
+    if (am) {
+        for (int i = tid; i < W * N; i += T) {
+            const int wb = i / N, p = i - wb * N;
+            uint32_t word = S.spins[wb * N + p].x;
+            const uint32_t src = scr[p].x;
+            for (uint32_t rest = am; rest; rest &= rest - 1) {
+                const int j = __ffs(rest) - 1;
+                const int w = wos[S.cslot[j]];
+                if ((w >> 5) != wb) continue;
+                const uint32_t b = 1u << (w & 31);
+                word = (word & ~b) | (((src >> j) & 1u) << (w & 31));
+            }
+            S.spins[wb * N + p] = make_uint2(word, ~word);
+        }
+    }
+    __syncthreads();
+}
+
+// CTX: built with the contextual-proposal step (a separate instantiation, so the kernels
+// without it keep their code and registers).
+template <int MAXW, int KB, bool CTX>
 __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict__ insts,
-                                                      RunArgs a, int with_pool) {
+                                                      RunArgs a, int flags) {
     extern __shared__ __align__(16) uint8_t smem[];
     const LatInst& I = insts[blockIdx.x];
     if (!*I.active) return;   // a free serving slot: the whole block leaves at once
     const int nwarps = blockDim.x >> 5;
-    LatSmem S = carve_lattice(smem, I, nwarps, with_pool != 0);
+    const bool with_pool = (flags & kWithPool) != 0;
+    constexpr bool with_ctx = CTX;
+    LatSmem S = carve_lattice(smem, I, nwarps, with_pool, with_ctx);
     const int tid = threadIdx.x, T = blockDim.x;
     const LP P = load_lp(I);
     const int N = P.N, W = P.W, R = P.R, WR = W * 32;
@@ -457,9 +604,20 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
         for (int i = tid; i < 6 * I.NW; i += T) S.ebits[i] = I.ebits[i];
         for (int i = tid; i < R; i += T) S.cursor[i] = I.cursor[i];
     }
+    if (with_ctx && tid == 0) {
+        int nen = 0;
+        for (int r = 0; r < R; ++r)
+            if (S.prop[r]) S.cslot[nen++] = (int16_t)r;
+        S.cmisc[0] = nen;
+    }
+    if (with_ctx)
+        for (int j = tid; j < 32; j += T) S.ccnt[j] = 0;
     long long sweeps = I.ctr->sweeps, n_ex = I.ctr->n_ex, n_prop = I.ctr->n_prop;
     __syncthreads();
-    if (tid < 32) rebuild_planes_warp(P, S, S.sow);
+    if (tid < 32) {
+        rebuild_planes_warp(P, S, S.sow);
+        if constexpr (CTX) build_context_planes(P, S);
+    }
     __syncthreads();
 
     uint32_t cnt[MAXW][KB];
@@ -491,7 +649,8 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     }
     if (a.mode & kModePropose) {
         ++n_prop;
-        if (with_pool) lattice_propose(I, S, a, n_prop, q);
+        if constexpr (CTX) lattice_context_propose<KB>(P, S, a, n_prop, q);
+        else if (with_pool) lattice_propose(I, S, a, n_prop, q);
     }
     if (a.mode & kModeExchange) {
         ++n_ex;
@@ -511,7 +670,8 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
                 lattice_store_energies(P, S, p);
                 __syncthreads();
                 ++n_prop;
-                if (with_pool) lattice_propose(I, S, a, n_prop, q);
+                if (with_ctx) lattice_context_propose<KB>(P, S, a, n_prop, q);
+                else if (with_pool) lattice_propose(I, S, a, n_prop, q);
                 lattice_exchange(P, S, a, n_ex, q, nullptr);
             } else {
                 lattice_exchange(P, S, a, n_ex, q, S.Eacc + p * WR);
@@ -611,28 +771,41 @@ __global__ void lattice_write_kernel(const LatInst* __restrict__ insts, int inst
 // The kernels' dynamic shared-memory limit is raised once, outside any stream capture.
 cudaError_t configure_lattice_kernels(int smem) {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1, 4>, A, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<1, 8>, A, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 4>, A, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 8>, A, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4, 8>, A, smem);
+    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1, 4, false>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<1, 8, false>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 4, false>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 8, false>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4, 8, false>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<1, 4, true>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<1, 8, true>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 4, true>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 8, true>, A, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4, 8, true>, A, smem);
     return e;
 }
 
 // kb4: the group's counts fit in 4 bits (at most two words per thread per colour class).
-cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
-                           size_t smem, const RunArgs& a, int with_pool, cudaStream_t stream) {
+template <bool CTX>
+cudaError_t launch_lattice_t(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
+                             size_t smem, const RunArgs& a, int flags, cudaStream_t stream) {
     if (maxW == 1 && kb4)
-        lattice_kernel<1, 4><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+        lattice_kernel<1, 4, CTX><<<n, threads, smem, stream>>>(d_insts, a, flags);
     else if (maxW == 1)
-        lattice_kernel<1, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+        lattice_kernel<1, 8, CTX><<<n, threads, smem, stream>>>(d_insts, a, flags);
     else if (maxW == 2 && kb4)
-        lattice_kernel<2, 4><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+        lattice_kernel<2, 4, CTX><<<n, threads, smem, stream>>>(d_insts, a, flags);
     else if (maxW == 2)
-        lattice_kernel<2, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+        lattice_kernel<2, 8, CTX><<<n, threads, smem, stream>>>(d_insts, a, flags);
     else
-        lattice_kernel<4, 8><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+        lattice_kernel<4, 8, CTX><<<n, threads, smem, stream>>>(d_insts, a, flags);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
+                           size_t smem, const RunArgs& a, int flags, cudaStream_t stream) {
+    if (flags & kWithContext)
+        return launch_lattice_t<true>(d_insts, n, maxW, kb4, threads, smem, a, flags, stream);
+    return launch_lattice_t<false>(d_insts, n, maxW, kb4, threads, smem, a, flags, stream);
 }
 
 cudaError_t launch_lattice_init(const LatInst* d, int n, uint64_t seed, cudaStream_t s) {

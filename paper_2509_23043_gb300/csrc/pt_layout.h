@@ -16,15 +16,19 @@ PT_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct LatLayout {
     size_t tw, spins, itab, beta, dbeta, fbeta, fdbeta, thr, prop, ebits, stage, us, cursor, accr, E, Eacc, st, sow, wos,
-        total;
+        cm, cslot, ccnt, cmisc, total;
 };
 
-PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool) {
+// with_ctx (contextual proposals): one more walker block of spins and threshold planes (the
+// scratch lanes), the kept-site masks and the per-lane bookkeeping.
+PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool,
+                                      bool with_ctx) {
     LatLayout l;
     const size_t WR = (size_t)W * 32;
+    const size_t WB = (size_t)W + (with_ctx ? 1 : 0);   // walker blocks held, scratch included
     size_t o = 0;
-    l.tw = o;     o = align16(o + WR * 16);
-    l.spins = o;  o = align16(o + WR / 32 * N * 8);   // word and complement
+    l.tw = o;     o = align16(o + WB * 32 * 16);
+    l.spins = o;  o = align16(o + WB * N * 8);          // word and complement
     l.itab = o;   o = align16(o + (size_t)N * 16);
     l.beta = o;   o = align16(o + (size_t)R * 8);
     l.dbeta = o;  o = align16(o + (size_t)R * 8);
@@ -42,6 +46,10 @@ PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, b
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
     l.sow = o;    o = align16(o + 2 * WR * 2);
     l.wos = o;    o = align16(o + 2 * WR * 2);
+    l.cm = o;     o = align16(o + (with_ctx ? (size_t)N * 4 : 0));
+    l.cslot = o;  o = align16(o + (with_ctx ? 32 * 2 : 0));
+    l.ccnt = o;   o = align16(o + (with_ctx ? 32 * 4 : 0));
+    l.cmisc = o;  o = align16(o + (with_ctx ? 2 * 4 : 0));
     l.total = o;
     return l;
 }
