@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12")
     p.add_argument("--serve-budget", type=int, default=20000)
     p.add_argument("--serve-gap-ms", type=float, default=4.0)
+    p.add_argument("--serve-hbm-frac", type=float, default=0.5,
+                   help="device-memory budget of admitted requests, as a fraction of all slots")
     p.add_argument("--cpu-sample-instances", type=int, default=16)
     p.add_argument("--cpu-sample-sweeps", type=int, default=60)
     return p.parse_args()
@@ -261,7 +263,8 @@ def served_stream(args, stream):
     mk = lambda k, a: S.Request(ids[k], insts[k], betas, prop, pools[k], eref[k], arrival=float(a))
     cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
     slots = {L: 4 for L in Ls}
-    srv = S.TaptServer(slots, betas, prop, cfg, hbm_budget=None, tick_cycles=100, stream=stream)
+    budget = int(args.serve_hbm_frac * sum(4 * S.footprint_bytes(L, R, P) for L in Ls))
+    srv = S.TaptServer(slots, betas, prop, cfg, hbm_budget=budget, tick_cycles=100, stream=stream)
     served = srv.serve([mk(k, arrivals[k]) for k in range(n)], budget_sweeps=args.serve_budget)
     cfg_pt = pt.Config(seed=0x7A972509, propose_every=0, pool_size=0)
     alone = [S.run_alone(mk(k, 0.0), cfg_pt, budget_sweeps=args.serve_budget, tick_cycles=100,
@@ -272,7 +275,8 @@ def served_stream(args, stream):
                         f"pools P={P} from 1e4+{20 * P}-sweep PT runs (untimed, {prep_s:.1f} s)",
             "served_tapt": S.summarize(served),
             "plain_pt_one_instance_per_launch": S.summarize(alone),
-            "slots_per_L": 4}
+            "slots_per_L": 4, "hbm_budget_bytes": budget, "peak_bytes_admitted": srv.peak_used,
+            "peak_requests_in_flight": srv.peak_active}
 
 
 # ------------------------------------------------------------------------------ other workloads

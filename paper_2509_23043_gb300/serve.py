@@ -158,6 +158,8 @@ class TaptServer:
         self.ticks_of: dict[int, int] = {}
         self.budget = hbm_budget
         self.used = 0
+        self.peak_used = 0        # largest footprint admitted at once (bytes)
+        self.peak_active = 0      # most requests in flight at once
 
     def _fp(self, req: Request) -> int:
         return footprint_bytes(req.L, self.R, self.cfg.pool_size)
@@ -174,6 +176,8 @@ class TaptServer:
         self.active[k] = req
         self.ticks_of[k] = 0
         self.used += self._fp(req)
+        self.peak_used = max(self.peak_used, self.used)
+        self.peak_active = max(self.peak_active, len(self.active))
         req.admitted = now
         return True
 
