@@ -68,10 +68,12 @@ def parse():
     p.add_argument("--workloads", default="plain,ragged,factor,ladder,context",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
-    p.add_argument("--serve-requests", type=int, default=48)
-    p.add_argument("--serve-L", default="6,7,8,9,10,11,12")
-    p.add_argument("--serve-budget", type=int, default=20000)
+    p.add_argument("--serve-requests", type=int, default=66)
+    p.add_argument("--serve-L", default="6,7,8,9,10,11,12,13,14,15,16")
+    p.add_argument("--serve-budget", type=int, default=100_000)
     p.add_argument("--serve-gap-ms", type=float, default=4.0)
+    p.add_argument("--serve-pool-burnin", type=int, default=100_000)
+    p.add_argument("--serve-pool-gap", type=int, default=100)
     p.add_argument("--serve-hbm-frac", type=float, default=0.5,
                    help="device-memory budget of admitted requests, as a fraction of all slots")
     p.add_argument("--cpu-sample-instances", type=int, default=16)
@@ -255,7 +257,8 @@ def served_stream(args, stream):
     insts = [I.ea_instance(L, seed=0x5E5E, index=k) for k, L in enumerate(req_L)]
     ids = [10_000 + k for k in range(n)]
     t0 = time.perf_counter()
-    pools = S.make_pools(insts, [betas] * n, ids, P, burnin=10_000, gap=20, stream=stream)
+    pools = S.make_pools(insts, [betas] * n, ids, P, burnin=args.serve_pool_burnin,
+                         gap=args.serve_pool_gap, stream=stream)
     eref = S.reference_energies(insts, [betas] * n, ids, sweeps=200_000, chunk=2000, stream=stream)
     prep_s = time.perf_counter() - t0
     arrivals = np.cumsum(g.exponential(args.serve_gap_ms * 1e-3, size=n))
@@ -267,13 +270,21 @@ def served_stream(args, stream):
     srv = S.TaptServer(slots, betas, prop, cfg, hbm_budget=budget, tick_cycles=100, stream=stream)
     served = srv.serve([mk(k, arrivals[k]) for k in range(n)], budget_sweeps=args.serve_budget)
     cfg_pt = pt.Config(seed=0x7A972509, propose_every=0, pool_size=0)
+    # the same server without proposals: separates the gain of batching from that of TAPT
+    srv_pt = S.TaptServer(slots, betas, prop, cfg_pt, hbm_budget=budget, tick_cycles=100,
+                          stream=stream)
+    served_pt = srv_pt.serve([S.Request(ids[k], insts[k], betas, prop, None, eref[k],
+                                        arrival=float(arrivals[k])) for k in range(n)],
+                             budget_sweeps=args.serve_budget)
     alone = [S.run_alone(mk(k, 0.0), cfg_pt, budget_sweeps=args.serve_budget, tick_cycles=100,
                          stream=stream) for k in range(n)]
     return {"workload": f"{n} requests, L uniform in {{{args.serve_L}}}, R={R}, Poisson arrivals "
                         f"(mean gap {args.serve_gap_ms} ms), target E_ref + 0.1%|E_ref| "
                         f"(E_ref: best of a 2e5-sweep PT run), budget {args.serve_budget} sweeps, "
-                        f"pools P={P} from 1e4+{20 * P}-sweep PT runs (untimed, {prep_s:.1f} s)",
+                        f"pools P={P} from PT runs of {args.serve_pool_burnin} + "
+                        f"{args.serve_pool_gap * P} sweeps (untimed, {prep_s:.1f} s)",
             "served_tapt": S.summarize(served),
+            "served_plain_pt": S.summarize(served_pt),
             "plain_pt_one_instance_per_launch": S.summarize(alone),
             "slots_per_L": 4, "hbm_budget_bytes": budget, "peak_bytes_admitted": srv.peak_used,
             "peak_requests_in_flight": srv.peak_active}
@@ -555,7 +566,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "attempts/ns",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32/u32 spins, f64 acceptance",
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8",
+        "dtype_detail": "int8 spins, int32 energies, f64 acceptance (the oracle)",
         "data": "synthetic",
         "config": {"workload": workload_name(args), "global_batch": args.instances,
                    "timed": "a bounded sample of the workload per step, on the host cores "
@@ -728,7 +740,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "attempts/ns", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32 bit-packed spins, int32 energies, f64 acceptance",
+            "dtype": "u32",
+            "dtype_detail": "u32 bit-packed spins (32 walkers per word), int32 energies, f64 acceptance",
             "data": "synthetic",
             "config": {"workload": workload_name(args),
                        "global_batch": B * world, "l2": "flushed between timed steps",

@@ -174,6 +174,14 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const RunArgs& a) {
     return c;
 }
 
+// 4-byte asynchronous global -> shared copies (cp.async, sm_80 and later).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ bool proposal_due(long long s, const RunArgs& a) {
     if (a.every <= 0 || s < a.start) return false;
     if (a.stop > 0 && s > a.stop) return false;

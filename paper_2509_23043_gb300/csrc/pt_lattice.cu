@@ -340,21 +340,41 @@ __device__ void lattice_exchange(const LP& P, LatSmem& S, const RunArgs& a, long
     }
 }
 
+// Copy the next pool entry of every proposal-enabled slot into the staging buffer with
+// cp.async, at the start of a cycle that ends with a proposal event: the cursors only move at
+// events, so the entries are known a cycle ahead and the copy overlaps the sweeps (the pools
+// live in device memory, so this hides a DRAM round trip). Each thread waits for its own
+// copies in lattice_propose; the barrier there publishes them.
+__device__ __forceinline__ void stage_proposals_async(const LatInst& I, LatSmem& S) {
+    const int NW = I.NW, R = I.R;
+    for (int idx = threadIdx.x; idx < R * NW; idx += blockDim.x) {
+        const int r = idx / NW, k = idx - r * NW;
+        if (S.prop[r])
+            cp_async4(S.stage + idx, I.pool + (size_t)S.cursor[r] * I.pstride + (size_t)r * NW + k);
+    }
+    cp_async_commit();
+}
+
 // One proposal event (Algorithm 1, Eq. 2) with energies in S.E and labels of buffer q.
+// `staged`: the entries were prefetched by stage_proposals_async.
 // A: stage the next pool entry of every proposal-enabled slot; B: count its unsatisfied
 // bonds (funnel shifts along x, y, z with the wrap masks; E^T = 2U - 3N); C: one thread per
 // slot decides in FP64 and advances the cursor; D: merge accepted entries into their walkers'
 // lanes 32 sites at a time by a warp bit transpose. Ends synchronised.
 __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunArgs& a,
-                                long long n_prop, int q) {
+                                long long n_prop, int q, bool staged) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nwarps = T >> 5;
     const int L = I.L, N = I.N, NW = I.NW, R = I.R, WR = I.W * 32;
     const int16_t* wos = S.wos + q * WR;
-    for (int idx = tid; idx < R * NW; idx += T) {
-        const int r = idx / NW, k = idx - r * NW;
-        if (S.prop[r])
-            S.stage[idx] = __ldg(I.pool + (size_t)S.cursor[r] * I.pstride + (size_t)r * NW + k);
+    if (staged) {
+        cp_async_wait_all();
+    } else {
+        for (int idx = tid; idx < R * NW; idx += T) {
+            const int r = idx / NW, k = idx - r * NW;
+            if (S.prop[r])
+                S.stage[idx] = __ldg(I.pool + (size_t)S.cursor[r] * I.pstride + (size_t)r * NW + k);
+        }
     }
     for (int r = tid; r < R; r += T) S.us[r] = 0;
     for (int w = tid; w < WR; w += T) S.accr[w] = -1;
@@ -650,7 +670,7 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     if (a.mode & kModePropose) {
         ++n_prop;
         if constexpr (CTX) lattice_context_propose<KB>(P, S, a, n_prop, q);
-        else if (with_pool) lattice_propose(I, S, a, n_prop, q);
+        else if (with_pool) lattice_propose(I, S, a, n_prop, q, false);
     }
     if (a.mode & kModeExchange) {
         ++n_ex;
@@ -660,18 +680,20 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
     }
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
+            const bool due = proposal_due(sweeps + a.M, a);
+            if (!CTX && due && with_pool) stage_proposals_async(I, S);
             for (int m = 0; m < a.M; ++m) {
                 lattice_sweep<MAXW, KB>(P, S, a, (uint32_t)sweeps, true, m == a.M - 1, cnt);
                 ++sweeps;
             }
             lattice_count_reduce<MAXW, KB>(P, S, cnt, p);
             ++n_ex;
-            if (proposal_due(sweeps, a)) {
+            if (due) {
                 lattice_store_energies(P, S, p);
                 __syncthreads();
                 ++n_prop;
-                if (with_ctx) lattice_context_propose<KB>(P, S, a, n_prop, q);
-                else if (with_pool) lattice_propose(I, S, a, n_prop, q);
+                if constexpr (CTX) lattice_context_propose<KB>(P, S, a, n_prop, q);
+                else if (with_pool) lattice_propose(I, S, a, n_prop, q, true);
                 lattice_exchange(P, S, a, n_ex, q, nullptr);
             } else {
                 lattice_exchange(P, S, a, n_ex, q, S.Eacc + p * WR);
