@@ -197,3 +197,16 @@ def test_always_accept_rule_oracle_keeps_boltzmann():
     # every proposal is accepted
     _, _, pa, ptot = o.stats()
     assert pa[0] == ptot[0] and pa[1] == ptot[1] and ptot[0] > 0
+
+
+def test_swap_matrix_is_stochastic_and_keeps_the_product_law():
+    # W_swap (Supplementary S2): each column sums to one, and pi_lo x pi_hi is invariant,
+    # i.e. the swap rule of Eq. 1 satisfies detailed balance for the pair.
+    inst = _fa()
+    E = _energy(inst, _states())
+    for b_lo, b_hi in ((0.5, 1.7), (1.7, 4.6)):
+        W = _w_swap(E, b_lo, b_hi)
+        assert np.allclose(W.sum(axis=(0, 1)), 1.0, atol=1e-12)
+        p = np.outer(_pi(E, b_lo), _pi(E, b_hi))
+        q = np.tensordot(W, p, axes=([2, 3], [0, 1]))
+        assert np.allclose(q, p, atol=1e-14)
