@@ -65,9 +65,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,ragged,factor,ladder,context",
+    p.add_argument("--workloads", default="plain,ragged,factor,ladder,context,tts",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
+    p.add_argument("--factor-pool-size", type=int, default=512)
+    p.add_argument("--factor-pool-burnin", type=int, default=100_000)
+    p.add_argument("--factor-pool-gap", type=int, default=25)
     p.add_argument("--serve-requests", type=int, default=66)
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12,13,14,15,16")
     p.add_argument("--serve-budget", type=int, default=100_000)
@@ -356,69 +359,154 @@ def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
             "threads_per_class": sorted({gr["threads"] for gr in groups}), "prep_s": round(prep, 1)}
 
 
-def factorization(stream, sweeps_total, n=1000, R=32, P=64, chunk=1000):
-    """The 8x8-bit multiplier (N = 200) with the product bits clamped to 1000 products of two
-    primes <= 255; R = 32 on 0.05 -> 5.0, Gibbs sweeps, proposals every 10 sweeps on the 23
-    hottest slots from a pool of configurations of the unclamped circuit (one PT run of the
-    universal instance, untimed). Success: some replica decodes to A*B = C with A, B > 1."""
+def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=25, chunk=1000):
+    """The 8x8-bit multiplier (N = 200) with the product bits clamped to n products of two
+    primes <= 255; R = 32 on 0.05 -> 5.0, proposals every 10 sweeps on the 23 hottest slots,
+    Gibbs (the paper's rule) and Metropolis. Per-product pools: P configurations of each
+    product's own clamped instance, captured every `gap` sweeps of one PT run after `burn`
+    sweeps (untimed), shared by both rules. Success: some replica decodes to A*B = C with
+    A, B > 1."""
     import instances as I
     import paper_2509_23043_gb300 as pt
     mult = I.multiplier(8)
     prods = I.draw_prime_products(n)
     betas = I.geometric_betas(0.05, 5.0, R)
     prop = [1] * 23 + [0] * (R - 23)
-    # pool: slot configurations of the universal instance (product free), captured every 20 sweeps
-    uni = mult.instance(None)
-    t0 = time.perf_counter()
-    gcfg = pt.Config(update=pt.GIBBS, seed=0x9001)
-    gen = pt.create_instances([uni], [betas], gcfg, instance_ids=[7_000_000], stream=stream.cuda_stream)
-    dst = pt.create_instances([uni], [betas], pt.Config(update=pt.GIBBS, seed=1, pool_size=P),
-                              instance_ids=[0], stream=stream.cuda_stream)
-    pt.run_cycles(gen, 20_000)
-    for e in range(P):
-        pt.run_cycles(gen, 20)
-        pt.capture_proposals(dst, gen, e)
-    nw = (mult.n_spins + 31) // 32
-    one = np.zeros((P, R * nw), dtype=np.uint32)
-    pt.read_proposals_packed(dst, one, 0, P)
-    pt.destroy(gen)
-    pt.destroy(dst)
     insts = [mult.instance(C) for C, _, _ in prods]
-    cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
-    ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
-                              instance_ids=list(range(n)), stream=stream.cuda_stream)
-    pt.load_proposals_packed(ctx, np.ascontiguousarray(np.tile(one, (1, n))), 0, P)
+    ctxs = {}
+    for name, upd in (("gibbs", pt.GIBBS), ("metropolis", pt.METROPOLIS)):
+        cfg = pt.Config(update=upd, seed=0x7A972509, propose_every=10, propose_start=0,
+                        pool_size=P)
+        ctxs[name] = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
+                                         instance_ids=list(range(n)), stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    gen = pt.create_instances(insts, [betas] * n, pt.Config(update=pt.GIBBS, seed=0x9001),
+                              instance_ids=[7_000_000 + k for k in range(n)],
+                              stream=stream.cuda_stream)
+    left = burn
+    while left > 0:
+        pt.run_cycles(gen, min(left, 10_000))
+        left -= 10_000
+    for e in range(P):
+        pt.run_cycles(gen, gap)
+        for ctx in ctxs.values():
+            pt.capture_proposals(ctx, gen, e)
+    pt.destroy(gen)
+    stream.synchronize()
     prep = time.perf_counter() - t0
     wA = 1 << np.arange(mult.w)
-    solved_at = np.full(n, -1)
-    done, t_gpu = 0, 0.0
-    checkpoints = {}
-    while done < sweeps_total:
-        step = min(chunk, sweeps_total - done)
-        s, e = _ev_pair()
-        s.record(stream)
-        pt.run_cycles(ctx, step)
-        e.record(stream)
-        e.synchronize()
-        t_gpu += s.elapsed_time(e)
-        done += step
-        for k in np.nonzero(solved_at < 0)[0]:
-            sp, _ = pt.read_state(ctx, int(k))
-            A = (sp[:, mult.A] > 0) @ wA
-            B = (sp[:, mult.B] > 0) @ wA
-            C = prods[k][0]
-            if np.any((A * B == C) & (A > 1) & (B > 1)):
-                solved_at[k] = done
-        checkpoints[done] = int((solved_at >= 0).sum())
     att = n * R * int((insts[0].clamp == 0).sum())
-    pt.destroy(ctx)
-    return {"workload": f"{n} clamped 8x8-bit multipliers (N={mult.n_spins}), R={R} on 0.05->5.0, "
-                        f"Gibbs, proposals every 10 sweeps from a pool of {P} universal-instance "
-                        f"configurations (untimed, {prep:.1f} s)",
-            "attempts_per_ns": att * done / (t_gpu * 1e6),
-            "solved_of": n, "solved_after_sweeps": checkpoints,
-            "median_sweeps_to_solution": (float(np.median(solved_at[solved_at >= 0]))
-                                          if (solved_at >= 0).any() else None)}
+    out = {"workload": f"{n} clamped 8x8-bit multipliers (N={mult.n_spins}), R={R} on "
+                       f"0.05->5.0, proposals every 10 sweeps on 23 slots from per-product pools "
+                       f"of {P} (a clamped PT run of {burn} + {P}x{gap} sweeps, untimed, "
+                       f"{prep:.1f} s)"}
+    for name, ctx in ctxs.items():
+        solved_at = np.full(n, -1)
+        done, t_gpu = 0, 0.0
+        checkpoints = {}
+        while done < sweeps_total:
+            step = min(chunk, sweeps_total - done)
+            s, e = _ev_pair()
+            s.record(stream)
+            pt.run_cycles(ctx, step)
+            e.record(stream)
+            e.synchronize()
+            t_gpu += s.elapsed_time(e)
+            done += step
+            for k in np.nonzero(solved_at < 0)[0]:
+                sp, _ = pt.read_state(ctx, int(k))
+                A = (sp[:, mult.A] > 0) @ wA
+                B = (sp[:, mult.B] > 0) @ wA
+                C = prods[k][0]
+                if np.any((A * B == C) & (A > 1) & (B > 1)):
+                    solved_at[k] = done
+            checkpoints[done] = int((solved_at >= 0).sum())
+        pt.destroy(ctx)
+        out[name] = {"attempts_per_ns": att * done / (t_gpu * 1e6),
+                     "solved_of": n, "solved_after_sweeps": checkpoints,
+                     "median_sweeps_to_solution": (float(np.median(solved_at[solved_at >= 0]))
+                                                   if (solved_at >= 0).any() else None)}
+    return out
+
+
+def factorization_tts(stream, n_products=32, runs=32, R=32, P=1024, t_max=50000, check=1000):
+    """Time to solution of Supplementary S5 on the 8x8 multiplier (16-bit products): every
+    product is run `runs` times independently by plain PT and by TAPT, which proposes once per
+    sweep on the 23 hottest of 32 slots from a pre-generated bank (untimed). Every run has its
+    own bank, captured from its own long PT run of this library: of the universal (unclamped)
+    circuit, or of the run's clamped instance. s(t_a) per product from its runs; TTS*_MCS =
+    min over t_a of t_a * ceil(log 0.01 / log(1 - s(t_a))), converted to seconds with the
+    measured device time per run and sweep. Reported: medians over the products."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    from paper_2509_23043_gb300 import tts as TT
+    mult = I.multiplier(8)
+    prods = I.draw_prime_products(n_products, seed=0x7755)
+    betas = I.geometric_betas(0.05, 5.0, R)
+    prop = [1] * 23 + [0] * (R - 23)
+    burn, gap = 100_000, 25
+    insts = [mult.instance(C) for C, _, _ in prods for _ in range(runs)]
+    ids = [1000 * k + j for k in range(n_products) for j in range(runs)]
+    n = len(insts)
+    wA = 1 << np.arange(mult.w)
+    checks = list(range(check // 10, check, check // 10)) + list(range(check, t_max + 1, check))
+    out = {}
+    prep = 0.0
+    for name in ("plain_pt", "tapt_universal_bank", "tapt_instance_bank"):
+        kw = {} if name == "plain_pt" else dict(propose_every=1, propose_start=0, pool_size=P)
+        cfg = pt.Config(update=pt.GIBBS, seed=0x7A97, **kw)
+        ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
+                                  instance_ids=ids, stream=stream.cuda_stream)
+        if kw:
+            t0 = time.perf_counter()
+            src = [mult.instance(None)] * n if name == "tapt_universal_bank" else insts
+            gen = pt.create_instances(src, [betas] * n, pt.Config(update=pt.GIBBS, seed=0x9003),
+                                      instance_ids=[5_000_000 + i for i in ids],
+                                      stream=stream.cuda_stream)
+            pt.run_cycles(gen, burn)
+            for e in range(P):
+                pt.run_cycles(gen, gap)
+                pt.capture_proposals(ctx, gen, e)
+            pt.destroy(gen)
+            stream.synchronize()
+            prep += time.perf_counter() - t0
+        solved_at = np.full(n, -1)
+        t_ms, done = 0.0, 0
+        for t in checks:
+            a_, b_ = _ev_pair()
+            a_.record(stream)
+            pt.run_cycles(ctx, t - done)
+            b_.record(stream)
+            b_.synchronize()
+            t_ms += a_.elapsed_time(b_)
+            done = t
+            for k in np.nonzero(solved_at < 0)[0]:
+                sp, _ = pt.read_state(ctx, int(k))
+                A = (sp[:, mult.A] > 0) @ wA
+                B = (sp[:, mult.B] > 0) @ wA
+                C = prods[k // runs][0]
+                if np.any((A * B == C) & (A > 1) & (B > 1)):
+                    solved_at[k] = t
+        pt.destroy(ctx)
+        per_sweep_s = t_ms * 1e-3 / (n * t_max)          # device time per run and sweep
+        best = np.array([TT.optimal_tts(checks, TT.success_curve(
+            solved_at[k * runs:(k + 1) * runs], checks)) for k in range(n_products)])
+        tts_mcs = best[:, 0]
+        finite = np.isfinite(tts_mcs)
+        med = float(np.median(tts_mcs))
+        out[name] = {"median_tts_sweeps": med if np.isfinite(med) else None,
+                     "median_tts_s": med * per_sweep_s if np.isfinite(med) else None,
+                     "median_best_run_length": float(np.median(best[finite, 1])) if finite.any() else None,
+                     "products_with_finite_tts": int(finite.sum()),
+                     "runs_solved": int((solved_at >= 0).sum()),
+                     "us_per_run_sweep": round(per_sweep_s * 1e6, 4),
+                     "device_ms": round(t_ms, 1)}
+    return {"workload": f"{n_products} products of two primes <= 255 on the 8x8 multiplier, "
+                        f"{runs} independent runs each, R={R} on 0.05->5.0, Gibbs, {t_max} sweeps "
+                        f"checked every {check // 10} up to {check}, then every {check}; TAPT proposes every sweep on 23 slots, each run "
+                        f"from its own bank of {P} (a PT run of {burn} + {P}x{gap} sweeps, "
+                        f"untimed, {prep:.1f} s for both banks)",
+            "target_success": TT.P_TARGET, "modes": out}
 
 
 def ladder_workload(stream, n=64, R=32, iterations=6, sweeps=2000):
@@ -723,9 +811,14 @@ def main():
         if "ragged" in wl:
             others["ragged_batch"] = ragged_batch(stream)
         if "factor" in wl:
-            others["factorization"] = factorization(stream, args.factor_sweeps)
+            others["factorization"] = factorization(stream, args.factor_sweeps,
+                                                    P=args.factor_pool_size,
+                                                    burn=args.factor_pool_burnin,
+                                                    gap=args.factor_pool_gap)
         if "ladder" in wl:
             others["ladder"] = ladder_workload(stream)
+        if "tts" in wl:
+            others["factorization_tts"] = factorization_tts(stream)
         if "context" in wl:
             others["context_ablation"] = context_ablation(stream)
 

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -541,7 +542,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, cs, ei, ej, eJ, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
+    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, cs, pe_ab, pe_J, ph_i, ph_h, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
@@ -551,6 +552,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     for (int k = 0; k < n; ++k) {
         const pt_instance_desc& d = descs[k];
         const int N = d.n_spins, R = d.n_replicas, R4 = (R + 3) & ~3, NW = (N + 31) / 32, NE = d.n_edges;
+        if (N > 65535) return fail(PT_ENOTSUP, "instance %d: graph engine supports N <= 65535", k);
         c->N[k] = N; c->R[k] = R; c->W[k] = (R + 31) / 32; c->NW[k] = NW; c->R4[k] = R4;
         GraphInst& I = c->gr[k];
         memset(&I, 0, sizeof I);
@@ -670,9 +672,38 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].adjp = A.add(adjp.data(), adjp.size() * 4);
         o[k].h = A.add(h.data(), h.size() * 4);
         o[k].cs = A.add(cs.data(), std::max<size_t>(cs.size(), 1) * 4);
-        o[k].ei = A.add(d.edge_i, (size_t)NE * 4);
-        o[k].ej = A.add(d.edge_j, (size_t)NE * 4);
-        o[k].eJ = A.add(d.edge_J, (size_t)NE * 4);
+        // proposal-energy blocks: edges grouped by coupling, sites of nonzero field by field,
+        // each group padded to a multiple of 32 with the index N
+        std::vector<uint32_t> pe_ab;
+        std::vector<int32_t> pe_J, ph_i, ph_h;
+        {
+            std::map<int32_t, std::vector<uint32_t>> byJ;
+            for (int e = 0; e < NE; ++e)
+                byJ[d.edge_J[e]].push_back((uint32_t)d.edge_i[e] | ((uint32_t)d.edge_j[e] << 16));
+            std::map<int32_t, std::vector<int32_t>> byh;
+            for (int i = 0; i < N; ++i) if (h[i] != 0) byh[h[i]].push_back(i);
+            const uint32_t padab = (uint32_t)N | ((uint32_t)N << 16);
+            long long K = 0;
+            for (auto& [J, v] : byJ) {
+                K -= (long long)J * (long long)v.size();
+                v.resize((v.size() + 31) / 32 * 32, padab);
+                pe_ab.insert(pe_ab.end(), v.begin(), v.end());
+                pe_J.insert(pe_J.end(), v.size() / 32, J);
+            }
+            for (auto& [hv, v] : byh) {
+                K += (long long)hv * (long long)v.size();
+                v.resize((v.size() + 31) / 32 * 32, N);
+                ph_i.insert(ph_i.end(), v.begin(), v.end());
+                ph_h.insert(ph_h.end(), v.size() / 32, hv);
+            }
+            I.nEb = (int)pe_J.size();
+            I.nHb = (int)ph_h.size();
+            I.Kprop = (int32_t)K;
+        }
+        o[k].pe_ab = A.add(pe_ab.data(), std::max<size_t>(pe_ab.size(), 1) * 4);
+        o[k].pe_J = A.add(pe_J.data(), std::max<size_t>(pe_J.size(), 1) * 4);
+        o[k].ph_i = A.add(ph_i.data(), std::max<size_t>(ph_i.size(), 1) * 4);
+        o[k].ph_h = A.add(ph_h.data(), std::max<size_t>(ph_h.size(), 1) * 4);
         o[k].cb = A.add(cb.data(), cb.size() * 4);
         o[k].E = A.zeros((size_t)R4 * 4);
         o[k].sow = A.add(sow.data(), sow.size() * 2);
@@ -688,7 +719,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         c->slab_off[k] = c->slab;
         c->slab += (size_t)R * NW;
         c->NWmax = std::max(c->NWmax, NW);
-        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, T / 32, c->with_pool != 0, I.packed != 0);
+        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, c->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
         maxsmem = std::max(maxsmem, l.total);
     }
     if (maxsmem > (size_t)c->optin)
@@ -720,9 +751,10 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.adjp = (const int32_t*)(b + o[k].adjp);
         I.h = (const int32_t*)(b + o[k].h);
         I.csites = (const int32_t*)(b + o[k].cs);
-        I.ei = (const int32_t*)(b + o[k].ei);
-        I.ej = (const int32_t*)(b + o[k].ej);
-        I.eJ = (const int32_t*)(b + o[k].eJ);
+        I.pe_ab = (const uint32_t*)(b + o[k].pe_ab);
+        I.pe_J = (const int32_t*)(b + o[k].pe_J);
+        I.ph_i = (const int32_t*)(b + o[k].ph_i);
+        I.ph_h = (const int32_t*)(b + o[k].ph_h);
         I.cbits = (const uint32_t*)(b + o[k].cb);
         I.E = (int32_t*)(b + o[k].E);
         I.sow = (int16_t*)(b + o[k].sow);
@@ -947,7 +979,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, T / 32, ctx->with_pool != 0, I.packed != 0);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
                     smem = std::max(smem, l.total);
                 }
                 (void)I0;
@@ -973,7 +1005,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, bestT / 32, ctx->with_pool != 0, I.packed != 0);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
                     smem = std::max(smem, l.total);
                 }
                 g.T = bestT;

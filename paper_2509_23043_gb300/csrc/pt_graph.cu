@@ -29,12 +29,17 @@ struct GraphSmem {
     int16_t* sow;
     int16_t* wos;
     uint32_t* pbuf;
+    uint32_t* pM;
+    uint32_t* pe_ab;
+    int32_t* pe_J;
+    int32_t* ph_i;
+    int32_t* ph_h;
 };
 
-__device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst& I, int nwarps,
+__device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst& I,
                                                  bool with_pool) {
-    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, nwarps, with_pool,
-                                 I.packed != 0);
+    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, with_pool,
+                                 I.packed != 0, I.nEb, I.nHb);
     GraphSmem S;
     S.spins = reinterpret_cast<int8_t*>(base + l.spins);
     S.thr = reinterpret_cast<uint32_t*>(base + l.thr);
@@ -51,6 +56,11 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     S.sow = reinterpret_cast<int16_t*>(base + l.sow);
     S.wos = reinterpret_cast<int16_t*>(base + l.wos);
     S.pbuf = reinterpret_cast<uint32_t*>(base + l.pbuf);
+    S.pM = reinterpret_cast<uint32_t*>(base + l.pM);
+    S.pe_ab = reinterpret_cast<uint32_t*>(base + l.pe_ab);
+    S.pe_J = reinterpret_cast<int32_t*>(base + l.pe_J);
+    S.ph_i = reinterpret_cast<int32_t*>(base + l.ph_i);
+    S.ph_h = reinterpret_cast<int32_t*>(base + l.ph_h);
     return S;
 }
 
@@ -250,30 +260,65 @@ __device__ void graph_exchange(const GraphInst& I, GraphSmem& S, uint32_t k0, ui
     __syncthreads();
 }
 
+// One proposal event (Eq. 2) for every enabled slot at once.
+//  1. All threads stage the current pool entry of every enabled slot, clamps applied.
+//  2. Transpose to one word per site and group of 32 slots: bit l of pM[g][i] is spin i of
+//     slot 32 g + l's entry (1 = +1).
+//  3. Energies: with x = [m_a != m_b] and b = [m_i = +1], E = Kprop + 2 (sum_e J_e x_e -
+//     sum_i h_i b_i). A block of 32 edges of one coupling gives one xor word per lane (its
+//     edge, bit = slot); a warp transpose turns it into one word per slot (bit = edge), whose
+//     popcount times the block's coupling is the slot's share. Sites of one field likewise.
+//  4. The decision of each slot, one thread per slot.
+//  5. Accepted entries are copied into their walkers' columns.
+// Eacc (zero between events) holds the sums, then the decisions, and is cleared again.
 __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uint32_t k1,
                               long long n_prop, int rule) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int N = I.N, NW = I.NW;
-    uint32_t* buf = S.pbuf + warp * NW;
-    for (int r = warp; r < I.R; r += nwarps) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = T >> 5;
+    const int N = I.N, NW = I.NW, R = I.R, G = (R + 31) >> 5, N1 = N + 1;
+    const int nEb = I.nEb, nB = I.nEb + I.nHb;
+    for (int idx = tid; idx < R * NW; idx += T) {
+        const int r = idx / NW, k = idx - r * NW;
         if (!I.prop[r]) continue;
-        const int w = S.wos[r];
-        const int c = I.cursor[r];
-        const uint32_t* entry = I.pool + (size_t)c * I.pstride + (size_t)r * NW;
-        for (int k = lane; k < NW; k += 32)
-            buf[k] = (__ldg(entry + k) & ~I.cbits[k]) | I.cbits[NW + k];  // clamps applied
-        __syncwarp();
-        int e = 0;
-        for (int k = lane; k < I.NE; k += 32) {
-            const int a = __ldg(I.ei + k), b = __ldg(I.ej + k);
-            const uint32_t ba = (buf[a >> 5] >> (a & 31)) & 1u, bb = (buf[b >> 5] >> (b & 31)) & 1u;
-            e -= (ba == bb) ? __ldg(I.eJ + k) : -__ldg(I.eJ + k);
-        }
-        for (int i = lane; i < N; i += 32)
-            e -= ((buf[i >> 5] >> (i & 31)) & 1u) ? S.h[i] : -S.h[i];
-        const int ET = __reduce_add_sync(kFull, e);
+        const uint32_t* entry = I.pool + (size_t)I.cursor[r] * I.pstride + (size_t)r * NW;
+        S.pbuf[idx] = (__ldg(entry + k) & ~I.cbits[k]) | I.cbits[NW + k];
+    }
+    __syncthreads();
+    for (int gk = warp; gk < G * NW; gk += nwarps) {
+        const int g = gk / NW, k = gk - g * NW;
+        const int r = 32 * g + lane;
+        const uint32_t x = (r < R && I.prop[r]) ? S.pbuf[r * NW + k] : 0u;
+        const uint32_t y = warp_transpose32(x, lane);
+        const int i = 32 * k + lane;
+        if (i < N) S.pM[g * N1 + i] = y;
+    }
+    if (tid < G) S.pM[tid * N1 + N] = 0u;
+    __syncthreads();
+    for (int g = 0; g < G; ++g) {
+        const uint32_t* M = S.pM + g * N1;
         int acc = 0;
-        if (lane == 0) {
+        for (int bk = warp; bk < nB; bk += nwarps) {
+            uint32_t x;
+            int wgt;
+            if (bk < nEb) {
+                const uint32_t ab = S.pe_ab[bk * 32 + lane];
+                x = M[ab & 0xFFFFu] ^ M[ab >> 16];
+                wgt = S.pe_J[bk];
+            } else {
+                x = M[S.ph_i[(bk - nEb) * 32 + lane]];
+                wgt = -S.ph_h[bk - nEb];
+            }
+            acc += wgt * __popc(warp_transpose32(x, lane));
+        }
+        const int r = 32 * g + lane;
+        if (r < R && acc != 0) atomicAdd(&S.Eacc[r], acc);
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += T) {
+        int acc = 0;
+        if (I.prop[r]) {
+            const int ET = I.Kprop + 2 * S.Eacc[r];
+            const int w = S.wos[r];
             const int dE = S.E[w] - ET;
             acc = rule == 1 || dE >= 0 || I.beta[r] == 0.0;
             if (!acc) {
@@ -281,20 +326,23 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
                                        k0, k1);
                 acc = accept_ratio(I.beta[r], (float)I.beta[r], dE, q.x);
             }
-        }
-        acc = __shfl_sync(kFull, acc, 0);
-        if (acc) {
-            for (int i = lane; i < N; i += 32)
-                S.spins[i * I.R4 + w] = ((buf[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
-        }
-        if (lane == 0) {
             if (acc) S.E[w] = ET;
-            I.cursor[r] = (c + 1) % I.P;
-            S.st[3 * I.R + r] += 1u;
-            if (acc) S.st[2 * I.R + r] += 1u;
+            I.cursor[r] = (I.cursor[r] + 1) % I.P;
+            S.st[3 * R + r] += 1u;
+            if (acc) S.st[2 * R + r] += 1u;
         }
-        __syncwarp();
+        S.Eacc[r] = acc;
     }
+    __syncthreads();
+    for (int r = warp; r < R; r += nwarps) {
+        if (!S.Eacc[r]) continue;
+        const int w = S.wos[r];
+        const uint32_t* buf = S.pbuf + r * NW;
+        for (int i = lane; i < N; i += 32)
+            S.spins[i * I.R4 + w] = ((buf[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += T) S.Eacc[r] = 0;
 }
 
 __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict__ insts,
@@ -302,8 +350,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     extern __shared__ __align__(16) uint8_t smem[];
     const GraphInst& I = insts[blockIdx.x];
     if (!*I.active) return;
-    const int nwarps = blockDim.x >> 5;
-    GraphSmem S = carve_graph(smem, I, nwarps, with_pool != 0);
+    GraphSmem S = carve_graph(smem, I, with_pool != 0);
     const int tid = threadIdx.x, T = blockDim.x;
     const int N = I.N, R = I.R, R4 = I.R4;
     {
@@ -324,6 +371,12 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
         }
     }
     for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
+    if (with_pool) {
+        for (int k = tid; k < 32 * I.nEb; k += T) S.pe_ab[k] = I.pe_ab[k];
+        for (int k = tid; k < I.nEb; k += T) S.pe_J[k] = I.pe_J[k];
+        for (int k = tid; k < 32 * I.nHb; k += T) S.ph_i[k] = I.ph_i[k];
+        for (int k = tid; k < I.nHb; k += T) S.ph_h[k] = I.ph_h[k];
+    }
     for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
     for (int i = tid; i < R4; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
     for (int i = tid; i < R; i += T) S.wos[i] = I.wos[i];

@@ -24,9 +24,14 @@ struct GraphInst {
     int32_t packed;
     const int32_t* h;        // [N]
     const int32_t* csites;   // [nfree] free sites in colour order
-    const int32_t* ei;       // [NE]
-    const int32_t* ej;       // [NE]
-    const int32_t* eJ;       // [NE]
+    // proposal energies: E = Kprop + 2 (sum_e J_e [m_a != m_b] - sum_i h_i [m_i = +1]), with
+    // the edges and the sites of nonzero field in blocks of 32 of one coupling (field) value,
+    // padded with the index N (a zero word)
+    int32_t nEb, nHb, Kprop;     // edge blocks, field blocks, sum_i h_i - sum_e J_e
+    const uint32_t* pe_ab;   // [32 nEb] a | b << 16
+    const int32_t* pe_J;     // [nEb]
+    const int32_t* ph_i;     // [32 nHb] site
+    const int32_t* ph_h;     // [nHb]
     const uint32_t* cbits;   // [2][NW]: clamped mask, clamp value (+1) bits
     int32_t* E;              // [R4] per walker
     int16_t* sow;            // [R4]
@@ -43,12 +48,16 @@ struct GraphInst {
 };
 
 struct GraphLayout {
-    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, csites, E, Eacc, st, sow, wos, pbuf, total;
+    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, csites, E, Eacc, st, sow, wos, pbuf, pM,
+        pe_ab, pe_J, ph_i, ph_h, total;
 };
 
-// Packed instances keep only the packed rows (adjp); the others only adj and adjJ.
+// Packed instances keep only the packed rows (adjp); the others only adj and adjJ. With a
+// pool: every slot's staged proposal (bit-packed, [R][NW]), the same transposed to one word
+// per site and group of 32 slots ([ceil(R/32)][N+1], word N zero), and the proposal-energy
+// blocks.
 PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
-                                      int nwarps, bool with_pool, bool packed) {
+                                      bool with_pool, bool packed, int nEb, int nHb) {
     GraphLayout l;
     size_t o = 0;
     l.spins = o;  o = align16(o + (size_t)N * R4);
@@ -65,7 +74,13 @@ PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, in
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
     l.sow = o;    o = align16(o + (size_t)R4 * 2);
     l.wos = o;    o = align16(o + (size_t)R * 2);
-    l.pbuf = o;   o = align16(o + (with_pool ? (size_t)nwarps * NW * 4 : 0));
+    const size_t wp = with_pool ? 1 : 0;
+    l.pbuf = o;   o = align16(o + wp * R * NW * 4);
+    l.pM = o;     o = align16(o + wp * ((R + 31) / 32) * (N + 1) * 4);
+    l.pe_ab = o;  o = align16(o + wp * 32 * nEb * 4);
+    l.pe_J = o;   o = align16(o + wp * nEb * 4);
+    l.ph_i = o;   o = align16(o + wp * 32 * nHb * 4);
+    l.ph_h = o;   o = align16(o + wp * nHb * 4);
     l.total = o;
     return l;
 }
