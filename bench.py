@@ -429,47 +429,82 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
     return out
 
 
-def factorization_tts(stream, n_products=32, runs=32, R=32, P=1024, t_max=50000, check=1000):
-    """Time to solution of Supplementary S5 on the 8x8 multiplier (16-bit products): every
-    product is run `runs` times independently by plain PT and by TAPT, which proposes once per
-    sweep on the 23 hottest of 32 slots from a pre-generated bank (untimed). Every run has its
-    own bank, captured from its own long PT run of this library: of the universal (unclamped)
-    circuit, or of the run's clamped instance. s(t_a) per product from its runs; TTS*_MCS =
-    min over t_a of t_a * ceil(log 0.01 / log(1 - s(t_a))), converted to seconds with the
-    measured device time per run and sweep. Reported: medians over the products."""
+def _chain_bank(stream, src, betas, chains, captures, burn, gap, seed, id0):
+    """A proposal bank from independent PT chains of this library: `chains` chains per source
+    instance, each burned in for `burn` sweeps, then captured `captures` times `gap` sweeps
+    apart. uint32 [captures * chains][len(src)][R * ceil(N/32)]; entry c * chains + j is
+    capture c of chain j, so consecutive entries come from different chains."""
+    import paper_2509_23043_gb300 as pt
+    m, R = len(src), len(betas)
+    nw = (src[0].n_spins + 31) // 32
+    gi = [inst for inst in src for _ in range(chains)]
+    ids = [id0 + i for i in range(len(gi))]
+    gen = pt.create_instances(gi, [betas] * len(gi), pt.Config(update=pt.GIBBS, seed=seed),
+                              instance_ids=ids, stream=stream.cuda_stream)
+    dst = pt.create_instances(gi, [betas] * len(gi),
+                              pt.Config(update=pt.GIBBS, seed=1, pool_size=captures),
+                              instance_ids=ids, stream=stream.cuda_stream)
+    left = burn
+    while left > 0:
+        pt.run_cycles(gen, min(left, 10_000))
+        left -= 10_000
+    for c in range(captures):
+        pt.run_cycles(gen, gap)
+        pt.capture_proposals(dst, gen, c)
+    words = np.zeros((captures, len(gi) * R * nw), dtype=np.uint32)
+    pt.read_proposals_packed(dst, words, 0, captures)
+    pt.destroy(gen)
+    pt.destroy(dst)
+    return (words.reshape(captures, m, chains, R * nw).transpose(0, 2, 1, 3)
+            .reshape(captures * chains, m, R * nw))
+
+
+def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, check=1000,
+                      chains=64, captures=16, burn=100_000, gap=250, n_prop=23):
+    """Time to solution of Supplementary S5 on the w x w multiplier (2w-bit products of two
+    primes below 2^w): every product is run `runs` times independently by plain PT and by
+    TAPT, which proposes once per sweep on the n_prop hottest of R slots from a pre-generated
+    bank (untimed). A bank holds captures of `chains` independent PT chains of this library:
+    of each product's clamped instance (one bank per product), or of the universal
+    (unclamped) circuit (one bank for all). The runs of a product share its bank, each
+    starting at its own random entry. s(t_a) per product from its runs; TTS*_MCS = min over
+    t_a of t_a * ceil(log 0.01 / log(1 - s(t_a))), converted to seconds with the measured
+    device time per run and sweep. Reported: medians over the products."""
     import instances as I
     import paper_2509_23043_gb300 as pt
     from paper_2509_23043_gb300 import tts as TT
-    mult = I.multiplier(8)
-    prods = I.draw_prime_products(n_products, seed=0x7755)
+    mult = I.multiplier(w)
+    prods = I.draw_prime_products(n_products, max_factor=(1 << w) - 1, seed=0x7755)
     betas = I.geometric_betas(0.05, 5.0, R)
-    prop = [1] * 23 + [0] * (R - 23)
-    burn, gap = 100_000, 25
+    prop = [1] * n_prop + [0] * (R - n_prop)
+    P = chains * captures
     insts = [mult.instance(C) for C, _, _ in prods for _ in range(runs)]
     ids = [1000 * k + j for k in range(n_products) for j in range(runs)]
     n = len(insts)
     wA = 1 << np.arange(mult.w)
     checks = list(range(check // 10, check, check // 10)) + list(range(check, t_max + 1, check))
+    t0 = time.perf_counter()
+    banks = {"tapt_universal_bank": _chain_bank(stream, [mult.instance(None)], betas, chains,
+                                                captures, burn, gap, 0x9004, 6_000_000),
+             "tapt_instance_bank": _chain_bank(stream, [mult.instance(C) for C, _, _ in prods],
+                                               betas, chains, captures, burn, gap, 0x9005,
+                                               6_100_000)}
+    prep = time.perf_counter() - t0
+    start = np.random.default_rng(0x57A7).integers(0, P, size=n)      # each run's first entry
+    entry = (np.arange(P)[:, None] + start[None, :]) % P
     out = {}
-    prep = 0.0
     for name in ("plain_pt", "tapt_universal_bank", "tapt_instance_bank"):
         kw = {} if name == "plain_pt" else dict(propose_every=1, propose_start=0, pool_size=P)
         cfg = pt.Config(update=pt.GIBBS, seed=0x7A97, **kw)
         ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
                                   instance_ids=ids, stream=stream.cuda_stream)
         if kw:
-            t0 = time.perf_counter()
-            src = [mult.instance(None)] * n if name == "tapt_universal_bank" else insts
-            gen = pt.create_instances(src, [betas] * n, pt.Config(update=pt.GIBBS, seed=0x9003),
-                                      instance_ids=[5_000_000 + i for i in ids],
-                                      stream=stream.cuda_stream)
-            pt.run_cycles(gen, burn)
-            for e in range(P):
-                pt.run_cycles(gen, gap)
-                pt.capture_proposals(ctx, gen, e)
-            pt.destroy(gen)
+            bank = banks[name]
+            owner = np.arange(n) // runs if bank.shape[1] > 1 else np.zeros(n, dtype=np.int64)
+            words = np.ascontiguousarray(bank[entry, owner[None, :], :]).reshape(P, -1)
+            pt.load_proposals_packed(ctx, words, 0, P)
             stream.synchronize()
-            prep += time.perf_counter() - t0
+            del words
         solved_at = np.full(n, -1)
         t_ms, done = 0.0, 0
         for t in checks:
@@ -501,12 +536,41 @@ def factorization_tts(stream, n_products=32, runs=32, R=32, P=1024, t_max=50000,
                      "runs_solved": int((solved_at >= 0).sum()),
                      "us_per_run_sweep": round(per_sweep_s * 1e6, 4),
                      "device_ms": round(t_ms, 1)}
-    return {"workload": f"{n_products} products of two primes <= 255 on the 8x8 multiplier, "
-                        f"{runs} independent runs each, R={R} on 0.05->5.0, Gibbs, {t_max} sweeps "
-                        f"checked every {check // 10} up to {check}, then every {check}; TAPT proposes every sweep on 23 slots, each run "
-                        f"from its own bank of {P} (a PT run of {burn} + {P}x{gap} sweeps, "
-                        f"untimed, {prep:.1f} s for both banks)",
+    return {"workload": f"{n_products} products of two primes < 2^{w} on the {w}x{w} multiplier "
+                        f"(N={mult.n_spins}), {runs} independent runs each, R={R} on 0.05->5.0, "
+                        f"Gibbs, {t_max} sweeps checked every {check // 10} up to {check}, then "
+                        f"every {check}; TAPT proposes every sweep on {n_prop} slots from banks of {P}: "
+                        f"{chains} independent PT chains x {captures} captures {gap} sweeps apart "
+                        f"after {burn} (untimed, {prep:.1f} s for both kinds)",
             "target_success": TT.P_TARGET, "modes": out}
+
+
+def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23):
+    """The scaling fit of Fig. 5 (S5): median TTS* at product sizes n = 2w, then
+    TTS(n) = A exp(k n) by least squares on log TTS, for plain PT and both TAPT banks, in
+    sweeps and in seconds. Run lengths grow with n (5e4 * 2^(w-8) sweeps). 32 x 23 runs keep
+    every size in one wave of CTAs (760 fit at w = 10, limited by shared memory)."""
+    from paper_2509_23043_gb300 import tts as TT
+    per = {}
+    for w in ws:
+        f = 1 << (w - 8)
+        per[2 * w] = factorization_tts(stream, w=w, n_products=n_products, runs=runs,
+                                       t_max=50_000 * f, check=1000 * f)
+    modes = list(next(iter(per.values()))["modes"])
+    fits = {}
+    for m in modes:
+        fits[m] = {}
+        for unit in ("sweeps", "s"):
+            med = [per[n]["modes"][m][f"median_tts_{unit}"] for n in per]
+            fit = TT.fit_exponent(list(per), [np.inf if v is None else v for v in med])
+            fits[m][f"k_{unit}"] = None if fit is None else fit[1]
+            fits[m][f"median_tts_{unit}"] = dict(zip(per, med))
+    return {"workload": f"product bits n in {sorted(per)}, {n_products} products x {runs} runs "
+                        f"each, as the time-to-solution workload",
+            "fit": "log TTS = log A + k n, least squares over the per-size medians",
+            "modes": fits,
+            "per_size": {n: {m: {k: v for k, v in d.items() if k != "device_ms"}
+                             for m, d in per[n]["modes"].items()} for n in per}}
 
 
 def ladder_workload(stream, n=64, R=32, iterations=6, sweeps=2000):
@@ -819,6 +883,8 @@ def main():
             others["ladder"] = ladder_workload(stream)
         if "tts" in wl:
             others["factorization_tts"] = factorization_tts(stream)
+        if "tts_scaling" in wl:
+            others["tts_scaling"] = tts_scaling(stream)
         if "context" in wl:
             others["context_ablation"] = context_ablation(stream)
 

@@ -40,3 +40,15 @@ def success_curve(solved_at: np.ndarray, run_lengths) -> list[float]:
     """s(t_a) from the sweep at which each independent run first succeeded (-1: never)."""
     solved_at = np.asarray(solved_at)
     return [float(np.mean((solved_at >= 0) & (solved_at <= t))) for t in run_lengths]
+
+
+def fit_exponent(sizes, tts) -> tuple[float, float] | None:
+    """(A, k) of TTS(n) = A exp(k n), least squares on log TTS against n (Fig. 5, S5). None
+    when fewer than two sizes have a finite, positive TTS."""
+    n = np.asarray(sizes, dtype=np.float64)
+    t = np.asarray(tts, dtype=np.float64)
+    ok = np.isfinite(t) & (t > 0)
+    if ok.sum() < 2:
+        return None
+    k, log_a = np.polyfit(n[ok], np.log(t[ok]), 1)
+    return float(np.exp(log_a)), float(k)

@@ -34,3 +34,18 @@ def test_optimal_tts_takes_the_minimum_over_run_lengths():
 def test_success_curve_from_first_success_sweeps():
     solved = np.array([-1, 50, 100, 250, 400, -1])
     assert tts.success_curve(solved, [50, 100, 300, 500]) == pytest.approx([1 / 6, 2 / 6, 3 / 6, 4 / 6])
+
+
+def test_fit_exponent_recovers_an_exact_exponential_and_the_two_point_slope():
+    n = [16, 18, 20, 22, 24]
+    A, k = 3.5, 0.846
+    fit = tts.fit_exponent(n, [A * math.exp(k * x) for x in n])
+    assert fit[0] == pytest.approx(A, rel=1e-9) and fit[1] == pytest.approx(k, rel=1e-12)
+    # two sizes: the slope of the line through both points
+    a, b = tts.fit_exponent([16, 20], [1000.0, 9000.0])
+    assert b == pytest.approx(math.log(9.0) / 4) and a * math.exp(16 * b) == pytest.approx(1000.0)
+    # infinite or missing sizes are left out; fewer than two finite sizes give no fit
+    assert tts.fit_exponent([16, 18, 20], [100.0, math.inf, 100.0 * math.exp(4 * 0.5)])[1] == \
+        pytest.approx(0.5)
+    assert tts.fit_exponent([16, 18], [100.0, math.inf]) is None
+
