@@ -117,16 +117,19 @@ def test_config3_ragged_persistent_sampled():
         assert np.array_equal(_energy_all(insts[k], s), E.astype(np.int64))
 
 
-def test_config4_factorization_sampled():
+@pytest.mark.parametrize("update,every", [(pt.GIBBS, 10), (pt.METROPOLIS, 10), (pt.GIBBS, 1)])
+def test_config4_factorization_sampled(update, every):
     # 1000 products of two primes <= 255 on the 8x8-bit multiplier (N=200), product bits and
-    # carry-ins clamped, R=32, beta 0.05 -> 5.0, Gibbs, pool proposals every 10 sweeps
+    # carry-ins clamped, R=32, beta 0.05 -> 5.0, Gibbs or Metropolis, pool proposals every 10
+    # sweeps (the factorization workload) or every sweep (the time-to-solution workload)
     mult = I.multiplier(8)
     prods = I.draw_prime_products(1000)
     insts = [mult.instance(C) for C, _, _ in prods]
     R, P = 32, 16
     betas = [I.geometric_betas(0.05, 5.0, R)] * len(insts)
     prop = [[1] * 23 + [0] * 9] * len(insts)
-    cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+    cfg = pt.Config(update=update, seed=0x7A972509, propose_every=every, propose_start=0,
+                    pool_size=P)
     ids = list(range(len(insts)))
     ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids)
     assert pt.info(ctx)["engine"] == "graph"
@@ -138,8 +141,8 @@ def test_config4_factorization_sampled():
             pt.load_proposals(ctx, k, r, pools[k][r])
     pt.run_cycles(ctx, 40)
     for k in samples:
-        o = O.Oracle(insts[k], betas[k], instance_id=k, prop_enabled=prop[k], update=1,
-                     propose_every=10, seed=0x7A972509, pool_size=P)
+        o = O.Oracle(insts[k], betas[k], instance_id=k, prop_enabled=prop[k], update=update,
+                     propose_every=every, seed=0x7A972509, pool_size=P)
         for r in range(R):
             o.load_pool(r, pools[k][r])
         o.run_cycles(40)
