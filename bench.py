@@ -206,6 +206,14 @@ def alu_ops_per_word(e_blocks: float) -> float:
     return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 20)
 
 
+def smem_bytes_per_word(e_blocks: float) -> float:
+    """Algorithmic shared-memory bytes of one bit-sliced word update (32 attempts): the 16 B
+    table entry, the own word and six neighbour words (4 B each), the 4 planes x 3 threshold
+    words of every plane block drawn (48 B per block), and the 8 B word-and-complement store
+    (counted for every word, an upper bound)."""
+    return 16 + 4 + 24 + 8 + e_blocks * 48
+
+
 PROFILE = ROOT / "profiles" / "lattice_kernel_batched_tapt_L10_R32_B256.md"
 
 
@@ -862,6 +870,13 @@ def main():
                 "peak_basis": "measured in this run by pt_calibrate_int (independent lop3.b32 "
                               "on every SM); nominal 152 SMs x 64 ALU lanes x 2070 MHz = "
                               f"{nominal:.2f} TOP/s"}
+    smem_peak, _ = pt.calibrate_smem()
+    smem_achieved = smem_bytes_per_word(e_blocks) * words_per_step / (ms_step * 1e-3)
+    roofline["smem"] = {"achieved_gbs": smem_achieved / 1e9, "peak_gbs": smem_peak / 1e9,
+                        "frac": smem_achieved / smem_peak,
+                        "bytes_per_attempt": smem_bytes_per_word(e_blocks) / 32,
+                        "peak_basis": "measured in this run by pt_calibrate_smem (conflict-free "
+                                      "16-byte shared loads on every SM)"}
 
     serving = None
     if not args.no_serve and rank == 0:

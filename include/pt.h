@@ -46,7 +46,9 @@ typedef struct pt_ctx pt_ctx;   /* opaque; owns all device memory of a batch */
  * temperature ladder {beta_r} and proposal-enabled set R_prop.
  *  instance_id   caller's identifier; it keys every random stream of the instance, so an
  *                instance evolves identically whatever batch or position it runs in.
- *  n_spins       N >= 1.
+ *  n_spins       N >= 1 (lattice engine: N <= 8192; graph engine: N <= 65535; both: the
+ *                instance's state and tables must fit in one SM's shared memory, else
+ *                PT_ENOTSUP).
  *  lattice_L     > 0: a periodic L^3 lattice (N = L^3, L >= 2); the edges must then be the
  *                3N bonds in canonical order: for site n = x + L(y + L z), its +x, +y, +z
  *                bonds, in that order (Methods, benchmark instances: 3D spin glass). The
@@ -266,6 +268,14 @@ pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
  * *ms (may be NULL) receives the best launch time. It allocates and frees a small device
  * buffer and synchronises. PT_EINVAL for another kind or a NULL ops_per_s. */
 pt_status pt_calibrate_int(int32_t kind, double *ops_per_s, double *ms);
+
+/* Measured shared-memory load bandwidth of the current device, the peak of the lattice
+ * kernel's second roofline (its working set lives in shared memory): every warp of 4 blocks
+ * of 512 threads per SM reads 32 consecutive 16-byte words per load, without bank conflicts,
+ * from a 16 KB buffer. *bytes_per_s receives the bytes loaded per second of the best of three
+ * timed launches, *ms (may be NULL) that launch's time. It allocates and frees a small device
+ * buffer and synchronises. PT_EINVAL for a NULL bytes_per_s. */
+pt_status pt_calibrate_smem(double *bytes_per_s, double *ms);
 
 /* Release all device memory (stream ordered) and the context. NULL is allowed. */
 pt_status pt_destroy(pt_ctx *ctx);

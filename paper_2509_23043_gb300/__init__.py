@@ -54,7 +54,8 @@ EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed
            "pt_read_state_noalloc",
            "pt_read_walkers", "pt_write_state", "pt_read_counters", "pt_read_stats", "pt_info",
            "pt_group_info", "pt_autotune", "pt_run_cycles_graph", "pt_set_instance",
-           "pt_set_active", "pt_set_stream", "pt_calibrate_int", "pt_destroy", "pt_last_error"]
+           "pt_set_active", "pt_set_stream", "pt_calibrate_int", "pt_calibrate_smem", "pt_destroy",
+           "pt_last_error"]
 
 _lib = None
 
@@ -87,6 +88,7 @@ def lib():
         "pt_set_active": [vp, i32, i32],
         "pt_set_stream": [vp, vp], "pt_destroy": [vp],
         "pt_calibrate_int": [i32, vp, vp],
+        "pt_calibrate_smem": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -371,6 +373,14 @@ def calibrate_int(kind: int = 0) -> tuple[float, float]:
     or multiply-add (kind 1) operations on the current device."""
     v, ms = C.c_double(0.0), C.c_double(0.0)
     _check(lib().pt_calibrate_int(kind, C.byref(v), C.byref(ms)))
+    return v.value, ms.value
+
+
+def calibrate_smem() -> tuple[float, float]:
+    """pt_calibrate_smem: (shared-memory bytes loaded per second, best launch ms) on the
+    current device."""
+    v, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().pt_calibrate_smem(C.byref(v), C.byref(ms)))
     return v.value, ms.value
 
 
