@@ -468,7 +468,7 @@ def _chain_bank(stream, src, betas, chains, captures, burn, gap, seed, id0):
 
 
 def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, check=1000,
-                      chains=64, captures=16, burn=100_000, gap=250, n_prop=23):
+                      chains=256, captures=4, burn=100_000, gap=250, n_prop=23):
     """Time to solution of Supplementary S5 on the w x w multiplier (2w-bit products of two
     primes below 2^w): every product is run `runs` times independently by plain PT and by
     TAPT, which proposes once per sweep on the n_prop hottest of R slots from a pre-generated
