@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,ragged,factor,ladder,context,tts",
+    p.add_argument("--workloads", default="plain,engines,ragged,factor,ladder,context,tts",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--factor-pool-size", type=int, default=512)
@@ -328,6 +328,44 @@ def plain_pt_single(stream):
     pt.destroy(ctx)
     return {"workload": "plain PT, 1 EA instance L=6, R=16, 10^4 sweeps in one launch",
             "ms": ms, "attempts_per_ns": att / (ms * 1e6)}
+
+
+def engine_comparison(stream, B=256, L=10, R=32, P=64, cycles=100, reps=5):
+    """The batched-TAPT workload (256 EA L=10, R=32 on 0.1 -> 3.0, Metropolis, proposals every
+    10 sweeps on 30 slots) on both engines under one protocol: the bit-packed lattice engine
+    (32 walkers per word), and the int8 graph engine, given the same lattices as general graphs
+    (DSATUR finds their two colours). Pools of P from short PT runs of each engine (untimed);
+    block sizes autotuned per engine; no L2 flush (the state lives in shared memory)."""
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    lat = [I.ea_instance(L, index=k) for k in range(B)]
+    gra = [I.Instance(i.n_spins, i.edge_i, i.edge_j, i.edge_J, None, None, 0) for i in lat]
+    betas = [I.geometric_betas(0.1, 3.0, R)] * B
+    prop = [[1] * (R - 2) + [0, 0]] * B
+    ids = list(range(B))
+    out = {}
+    for name, insts in (("bit_packed_lattice_engine", lat), ("int8_graph_engine", gra)):
+        cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+        ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids,
+                                  stream=stream.cuda_stream)
+        gen = pt.create_instances(insts, betas, pt.Config(seed=0x9001),
+                                  instance_ids=[2_000_000 + i for i in ids],
+                                  stream=stream.cuda_stream)
+        pt.run_cycles(gen, 2000)
+        for e in range(P):
+            pt.run_cycles(gen, 2)
+            pt.capture_proposals(ctx, gen, e)
+        pt.destroy(gen)
+        pt.autotune(ctx, probe_cycles=20)
+        engine = pt.info(ctx)["engine"]
+        ms = _time_ms(lambda: pt.run_cycles(ctx, cycles), reps, stream)
+        out[name] = {"engine": engine, "threads_per_block": pt.info(ctx)["threads"],
+                     "ms_per_100_cycles": ms * 100 / cycles,
+                     "attempts_per_ns": B * R * L ** 3 * cycles / (ms * 1e6)}
+        pt.destroy(ctx)
+    return {"workload": f"{B} EA L={L}, R={R}, Metropolis, proposals every 10 from pools of {P}, "
+                        f"{cycles} cycles per launch, autotuned block sizes, no L2 flush",
+            "engines": out}
 
 
 def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
@@ -887,6 +925,8 @@ def main():
         others = {}
         if "plain" in wl:
             others["plain_pt_single"] = plain_pt_single(stream)
+        if "engines" in wl:
+            others["engine_comparison"] = engine_comparison(stream)
         if "ragged" in wl:
             others["ragged_batch"] = ragged_batch(stream)
         if "factor" in wl:
