@@ -542,7 +542,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, cs, pe_ab, pe_J, ph_i, ph_h, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
+    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, hk, cs, pe_ab, pe_J, ph_i, ph_h, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
@@ -671,6 +671,17 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].adjJ = A.add(adjJ.data(), adjJ.size() * 4);
         o[k].adjp = A.add(adjp.data(), adjp.size() * 4);
         o[k].h = A.add(h.data(), h.size() * 4);
+        {
+            std::vector<int32_t> hk(2 * (size_t)N, 0);
+            for (int i = 0; i < N; ++i) {
+                long long sc = 0, sr = 0;
+                for (int a = rowp[i]; a < rowl[i]; ++a) sc += adjJ[a];
+                for (int a = rowl[i]; a < rowp[i + 1]; ++a) sr += adjJ[a];
+                hk[2 * (size_t)i] = (int32_t)(h[i] + sc + 256);
+                hk[2 * (size_t)i + 1] = (int32_t)(h[i] + sc + sr + 512);
+            }
+            o[k].hk = A.add(hk.data(), hk.size() * 4);
+        }
         o[k].cs = A.add(cs.data(), std::max<size_t>(cs.size(), 1) * 4);
         // proposal-energy blocks: edges grouped by coupling, sites of nonzero field by field,
         // each group padded to a multiple of 32 with the index N
@@ -750,6 +761,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.adjJ = (const int32_t*)(b + o[k].adjJ);
         I.adjp = (const int32_t*)(b + o[k].adjp);
         I.h = (const int32_t*)(b + o[k].h);
+        I.hk = (const int2*)(b + o[k].hk);
         I.csites = (const int32_t*)(b + o[k].cs);
         I.pe_ab = (const uint32_t*)(b + o[k].pe_ab);
         I.pe_J = (const int32_t*)(b + o[k].pe_J);

@@ -22,6 +22,7 @@ struct GraphSmem {
     int32_t* adjJ;
     int32_t* adjp;
     int32_t* h;
+    int2* hk;
     int32_t* csites;
     int32_t* E;
     int32_t* Eacc;
@@ -49,6 +50,7 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     S.adjJ = reinterpret_cast<int32_t*>(base + l.adjJ);
     S.adjp = reinterpret_cast<int32_t*>(base + l.adjp);
     S.h = reinterpret_cast<int32_t*>(base + l.h);
+    S.hk = reinterpret_cast<int2*>(base + l.hk);
     S.csites = reinterpret_cast<int32_t*>(base + l.csites);
     S.E = reinterpret_cast<int32_t*>(base + l.E);
     S.Eacc = reinterpret_cast<int32_t*>(base + l.Eacc);
@@ -105,44 +107,45 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
         const int nc = cbeg - base;
         for (int si = s0; si < nc && tid < Ts; si += sstep) {
             const int site = S.csites[base + si];
-            const int hs = S.h[site];
-            int g[4], f[4];                            // counted-neighbour sums, local fields
+            int hg[4], f[4];            // h + counted-neighbour sums, local fields
             const int split = S.rowl[site], end = S.rowp[site + 1];
             if (packed) {
-                // bytes of ac / ar: 128 + sum of J over the neighbours whose spin is -1
+                // bytes of ac / ar: 128 + sum of J over the neighbours whose spin is -1. With
+                // sum J m = sum J - 2 sum_{m=-1} J, h + the counted sum is hk.x - 2 byte(ac),
+                // and the local field hk.y - 2 (byte(ac) + byte(ar)).
                 uint32_t ac = 0x80808080u, ar = 0x80808080u;
-                int sjc = 0, sjr = 0;
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
                     const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
                     ac += (uint32_t)J * neg;
-                    sjc += J;
                 }
                 for (int a2 = split; a2 < end; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
                     const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
                     ar += (uint32_t)J * neg;
-                    sjr += J;
                 }
-                // sum J m = sum J - 2 sum_{m=-1} J
+                const int2 kk = S.hk[site];
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
-                    g[k4] = sjc - 2 * ((int)((ac >> (8 * k4)) & 0xFFu) - 128);
-                    f[k4] = hs + g[k4] + sjr - 2 * ((int)((ar >> (8 * k4)) & 0xFFu) - 128);
+                    const int bc = (int)((ac >> (8 * k4)) & 0xFFu);
+                    const int br = (int)((ar >> (8 * k4)) & 0xFFu);
+                    hg[k4] = kk.x - 2 * bc;
+                    f[k4] = kk.y - 2 * (bc + br);
                 }
             } else {
+                const int hs = S.h[site];
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) g[k4] = 0;
+                for (int k4 = 0; k4 < 4; ++k4) hg[k4] = hs;
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
                     const uint32_t wd = sp[S.adj[a2] * Q + quad];
                     const int J = S.adjJ[a2];
 #pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) g[k4] += J * sbyte(wd, k4);
+                    for (int k4 = 0; k4 < 4; ++k4) hg[k4] += J * sbyte(wd, k4);
                 }
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) f[k4] = hs + g[k4];
+                for (int k4 = 0; k4 < 4; ++k4) f[k4] = hg[k4];
                 for (int a2 = split; a2 < end; ++a2) {
                     const uint32_t wd = sp[S.adj[a2] * Q + quad];
                     const int J = S.adjJ[a2];
@@ -173,10 +176,10 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
             }
             if (out != own) sp[site * Q + quad] = out;
             if (energy_on) {
-                e0 -= nmv[0] * (hs + g[0]);
-                e1 -= nmv[1] * (hs + g[1]);
-                e2 -= nmv[2] * (hs + g[2]);
-                e3 -= nmv[3] * (hs + g[3]);
+                e0 -= nmv[0] * hg[0];
+                e1 -= nmv[1] * hg[1];
+                e2 -= nmv[2] * hg[2];
+                e3 -= nmv[3] * hg[3];
             }
         }
         if (energy_on && c == ncol - 1 && tid < Ts) {
@@ -208,7 +211,7 @@ __device__ void graph_energy(const GraphInst& I, GraphSmem& S) {
         int acc = 0;
         if (w < I.R) {
             for (int site = warp; site < I.N; site += nwarps) {
-                const int hs = S.h[site];
+                const int hs = I.h[site];
                 int f = hs;
                 if (I.packed) {
                     for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
@@ -370,7 +373,11 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
             S.adjJ[i] = I.adjJ[i];
         }
     }
-    for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
+    if (I.packed) {
+        for (int i = tid; i < N; i += T) S.hk[i] = I.hk[i];
+    } else {
+        for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
+    }
     if (with_pool) {
         for (int k = tid; k < 32 * I.nEb; k += T) S.pe_ab[k] = I.pe_ab[k];
         for (int k = tid; k < I.nEb; k += T) S.pe_J[k] = I.pe_J[k];

@@ -23,6 +23,9 @@ struct GraphInst {
                              // when `packed` (every |coupling| and every site's sum of them <= 127)
     int32_t packed;
     const int32_t* h;        // [N]
+    const int2* hk;          // [N] packed rows only: {h + sum of J over the counted neighbours
+                             // + 256, that + sum of J over the others + 256}, the constants of
+                             // the biased byte sums (graph_sweep)
     const int32_t* csites;   // [nfree] free sites in colour order
     // proposal energies: E = Kprop + 2 (sum_e J_e [m_a != m_b] - sum_i h_i [m_i = +1]), with
     // the edges and the sites of nonzero field in blocks of 32 of one coupling (field) value,
@@ -48,14 +51,14 @@ struct GraphInst {
 };
 
 struct GraphLayout {
-    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, csites, E, Eacc, st, sow, wos, pbuf, pM,
+    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, hk, csites, E, Eacc, st, sow, wos, pbuf, pM,
         pe_ab, pe_J, ph_i, ph_h, total;
 };
 
-// Packed instances keep only the packed rows (adjp); the others only adj and adjJ. With a
-// pool: every slot's staged proposal (bit-packed, [R][NW]), the same transposed to one word
-// per site and group of 32 slots ([ceil(R/32)][N+1], word N zero), and the proposal-energy
-// blocks.
+// Packed instances keep only the packed rows (adjp) and the per-site constants hk; the others
+// only adj, adjJ and the fields h. With a pool: every slot's staged proposal (bit-packed,
+// [R][NW]), the same transposed to one word per site and group of 32 slots ([ceil(R/32)][N+1],
+// word N zero), and the proposal-energy blocks.
 PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
                                       bool with_pool, bool packed, int nEb, int nHb) {
     GraphLayout l;
@@ -67,7 +70,8 @@ PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, in
     l.adj = o;    o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
     l.adjJ = o;   o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
     l.adjp = o;   o = align16(o + (packed ? (size_t)2 * NE * 4 : 0));
-    l.h = o;      o = align16(o + (size_t)N * 4);
+    l.h = o;      o = align16(o + (packed ? 0 : (size_t)N * 4));
+    l.hk = o;     o = align16(o + (packed ? (size_t)N * 8 : 0));
     l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
     l.E = o;      o = align16(o + (size_t)R4 * 4);
     l.Eacc = o;   o = align16(o + (size_t)R4 * 4);
