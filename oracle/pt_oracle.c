@@ -7,7 +7,7 @@
  * Random-number counters (Philox4x32-10, key = seed low/high 32 bits). ctr = {c0,c1,c2,c3}:
  *   init        c0 = site,  c1 = 0,      c2 = (0<<24) | (walker>>5),                 c3 = id
  *               spin = +1 iff bit (walker & 31) of output word 0 is set
- *   local move, bit-plane layout (lattice + Metropolis + J=+-1, no field, no clamp):
+ *   local move, bit-plane layout (lattice + J=+-1, no field, no clamp; either rule):
  *               c0 = site,  c1 = sweep, c2 = (1<<24) | (k>>2)<<16 | (walker>>5),     c3 = id
  *               u = sum_k bit(walker & 31) of output word (k & 3), times 2^(31-k), k=0..31
  *   local move, word layout (all other instances):
@@ -267,7 +267,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     memcpy(o->beta, beta, (size_t)n_replicas * sizeof(double));
     o->prop = (uint8_t *)xcalloc((size_t)n_replicas, 1);
     if (prop_enabled) memcpy(o->prop, prop_enabled, (size_t)n_replicas);
-    o->bitplane = (lattice_L > 0 && update == 0 && !has_h && !has_clamp && unit_J);
+    o->bitplane = (lattice_L > 0 && !has_h && !has_clamp && unit_J);
     if (proposal_source == 1) {
         int32_t n_en = 0;
         for (int32_t r = 0; r < n_replicas; ++r) n_en += o->prop[r] != 0;

@@ -273,11 +273,15 @@ def _assert_matches(p, q, n, E=None):
         assert _tv(pe, qe) < 0.02, (pe, qe)
 
 
-@pytest.mark.parametrize("update,bitplane", [(0, True), (1, False)])
+@pytest.mark.parametrize("update,bitplane", [(0, True), (1, True), (0, False), (1, False)])
 def test_single_replica_samples_boltzmann_2x2x2(update, bitplane):
     # On the 2x2x2 lattice (256 states) a long single-temperature run reproduces the exact
-    # Boltzmann law; a dropped term or a wrong sign in the update would not.
+    # Boltzmann law; a dropped term or a wrong sign in the update would not. Both rules, with
+    # the bit-plane uniforms (the lattice) and with one word per walker (the same couplings
+    # given as a general graph).
     inst = I.ea_instance(2, index=7)
+    if not bitplane:
+        inst = I.Instance(inst.n_spins, inst.edge_i, inst.edge_j, inst.edge_J, None, None, 0)
     beta = 0.45
     o = O.Oracle(inst, [beta], update=update, seed=11)
     assert o.bitplane == bitplane
