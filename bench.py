@@ -240,7 +240,7 @@ def source_hash():
     comment edit does not invalidate the profile's counters."""
     import re
     h = hashlib.sha256()
-    for name in ("pt_lattice.cu", "pt_device.cuh", "pt_layout.h"):
+    for name in ("pt_lattice.cuh", "pt_lattice.cu", "pt_device.cuh", "pt_layout.h"):
         text = (ROOT / "paper_2509_23043_gb300" / "csrc" / name).read_text()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         lines = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
@@ -331,11 +331,12 @@ def plain_pt_single(stream):
 
 
 def engine_comparison(stream, B=256, L=10, R=32, P=64, cycles=100, reps=5):
-    """The batched-TAPT workload (256 EA L=10, R=32 on 0.1 -> 3.0, Metropolis, proposals every
-    10 sweeps on 30 slots) on both engines under one protocol: the bit-packed lattice engine
-    (32 walkers per word), and the int8 graph engine, given the same lattices as general graphs
-    (DSATUR finds their two colours). Pools of P from short PT runs of each engine (untimed);
-    block sizes autotuned per engine; no L2 flush (the state lives in shared memory)."""
+    """The batched-TAPT workload (256 EA L=10, R=32 on 0.1 -> 3.0, proposals every 10 sweeps on
+    30 slots), with Metropolis (the benchmark's rule) and Gibbs (the paper's rule), on both
+    engines under one protocol: the bit-packed lattice engine (32 walkers per word), and the
+    int8 graph engine, given the same lattices as general graphs (DSATUR finds their two
+    colours). Pools of P from short PT runs of each engine (untimed); block sizes autotuned per
+    engine; no L2 flush (the state lives in shared memory)."""
     import instances as I
     import paper_2509_23043_gb300 as pt
     lat = [I.ea_instance(L, index=k) for k in range(B)]
@@ -344,26 +345,28 @@ def engine_comparison(stream, B=256, L=10, R=32, P=64, cycles=100, reps=5):
     prop = [[1] * (R - 2) + [0, 0]] * B
     ids = list(range(B))
     out = {}
-    for name, insts in (("bit_packed_lattice_engine", lat), ("int8_graph_engine", gra)):
-        cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
-        ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids,
-                                  stream=stream.cuda_stream)
-        gen = pt.create_instances(insts, betas, pt.Config(seed=0x9001),
-                                  instance_ids=[2_000_000 + i for i in ids],
-                                  stream=stream.cuda_stream)
-        pt.run_cycles(gen, 2000)
-        for e in range(P):
-            pt.run_cycles(gen, 2)
-            pt.capture_proposals(ctx, gen, e)
-        pt.destroy(gen)
-        pt.autotune(ctx, probe_cycles=20)
-        engine = pt.info(ctx)["engine"]
-        ms = _time_ms(lambda: pt.run_cycles(ctx, cycles), reps, stream)
-        out[name] = {"engine": engine, "threads_per_block": pt.info(ctx)["threads"],
-                     "ms_per_100_cycles": ms * 100 / cycles,
-                     "attempts_per_ns": B * R * L ** 3 * cycles / (ms * 1e6)}
-        pt.destroy(ctx)
-    return {"workload": f"{B} EA L={L}, R={R}, Metropolis, proposals every 10 from pools of {P}, "
+    for rule, update in (("metropolis", pt.METROPOLIS), ("gibbs", pt.GIBBS)):
+        for name, insts in (("bit_packed_lattice_engine", lat), ("int8_graph_engine", gra)):
+            cfg = pt.Config(update=update, seed=0x7A972509, propose_every=10, propose_start=0,
+                            pool_size=P)
+            ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids,
+                                      stream=stream.cuda_stream)
+            gen = pt.create_instances(insts, betas, pt.Config(update=update, seed=0x9001),
+                                      instance_ids=[2_000_000 + i for i in ids],
+                                      stream=stream.cuda_stream)
+            pt.run_cycles(gen, 2000)
+            for e in range(P):
+                pt.run_cycles(gen, 2)
+                pt.capture_proposals(ctx, gen, e)
+            pt.destroy(gen)
+            pt.autotune(ctx, probe_cycles=20)
+            ms = _time_ms(lambda: pt.run_cycles(ctx, cycles), reps, stream)
+            out[f"{rule}_{name}"] = {"engine": pt.info(ctx)["engine"],
+                                     "threads_per_block": pt.info(ctx)["threads"],
+                                     "ms_per_100_cycles": ms * 100 / cycles,
+                                     "attempts_per_ns": B * R * L ** 3 * cycles / (ms * 1e6)}
+            pt.destroy(ctx)
+    return {"workload": f"{B} EA L={L}, R={R}, proposals every 10 from pools of {P}, "
                         f"{cycles} cycles per launch, autotuned block sizes, no L2 flush",
             "engines": out}
 

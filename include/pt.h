@@ -101,13 +101,14 @@ typedef struct {
  *                    proposal-probability correction then cancels the Boltzmann ratio;
  *                    Supplementary S2). Other values: PT_EINVAL.
  *  proposal_source   0 = proposals from the pools (pt_load_proposals...); 1 = contextual
- *                    proposals (Supplementary S3), lattice engine only: at each event every
+ *                    proposals (Supplementary S3), lattice engine with Metropolis sweeps
+ *                    (update 0) only: at each event every
  *                    proposal-enabled slot (at most 32 per instance) copies its configuration,
  *                    keeps each site with probability 2^-context_log2 (1, 2 or 3: 50, 25 or
  *                    12.5 %), refills the other sites by context_sweeps (>= 1) Metropolis
  *                    sweeps at its beta, and the result is accepted by proposal_rule. Pools
- *                    are not used. Violations: PT_EINVAL, or PT_ENOTSUP for the graph engine
- *                    or more than 32 enabled slots.
+ *                    are not used. Violations: PT_EINVAL, or PT_ENOTSUP for the graph engine,
+ *                    Gibbs sweeps or more than 32 enabled slots.
  */
 typedef struct {
     int32_t update;
@@ -124,8 +125,9 @@ typedef struct {
     int32_t context_sweeps;
 } pt_config;
 
-/* Create a batch of n >= 1 instances (all lattice+Metropolis+J=+-1 without field or clamp,
- * or all otherwise: one engine per context), allocate its device memory (cudaMallocAsync
+/* Create a batch of n >= 1 instances (all lattices with J = +-1 and no field or clamp, which
+ * run on the bit-packed lattice engine under either rule, or all otherwise, which run on the
+ * int8 graph engine: one engine per context), allocate its device memory (cudaMallocAsync
  * on `cuda_stream`, a cudaStream_t or NULL for the legacy stream), draw the random initial
  * state of every replica (Algorithm 1, initialisation) and compute
  * its energies. On success *out owns everything; release it with pt_destroy. */

@@ -18,8 +18,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libpt.so"
-SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_graph.cu", "pt_calib.cu"]
-HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh"]
+SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_lattice_gibbs.cu", "pt_graph.cu", "pt_calib.cu"]
+HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh", "pt_lattice.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ffp-contract=off on the host: FP64 threshold tables are evaluated exactly as written.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

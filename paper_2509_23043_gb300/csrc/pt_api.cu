@@ -215,7 +215,8 @@ cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, i
         const int per_thread = (g.maxitems / std::max(g.maxW, 1) + g.T - 1) / g.T;
         const int counting = (c->L[g.members[0]] % 2 == 0) ? 1 : 2;
         const int kb4 = 6 * per_thread * counting < 16 ? 1 : 0;
-        const int flags = (c->with_pool ? kWithPool : 0) | (c->with_ctx ? kWithContext : 0);
+        const int flags = (c->with_pool ? kWithPool : 0) | (c->with_ctx ? kWithContext : 0) |
+                          (c->cfg.update == 1 ? kGibbs : 0);
         return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, kb4, g.T, g.smem, a,
                               flags, s);
     }
@@ -262,8 +263,9 @@ void drop_graph(pt_ctx* c) {
     c->gcycles = -1;
 }
 
-bool is_lattice_desc(const pt_instance_desc& d, const pt_config& cfg) {
-    if (d.lattice_L <= 0 || cfg.update != 0) return false;
+// The bit-packed lattice engine takes +-1 lattices without field or clamps (either rule).
+bool is_lattice_desc(const pt_instance_desc& d) {
+    if (d.lattice_L <= 0) return false;
     if (d.h)
         for (int i = 0; i < d.n_spins; ++i)
             if (d.h[i] != 0) return false;
@@ -328,7 +330,7 @@ struct LatHost {
     int maxitems = 0;
 };
 
-pt_status lattice_host(const pt_instance_desc& d, LatHost& h, int k) {
+pt_status lattice_host(const pt_instance_desc& d, LatHost& h, int k, bool gibbs) {
     const int L = d.lattice_L, N = d.n_spins, R = d.n_replicas, W = (R + 31) / 32, NW = (N + 31) / 32;
     if (N > 8192) return fail(PT_ENOTSUP, "instance %d: lattice engine supports N <= 8192 (L <= 20)", k);
     h.L = L; h.N = N; h.R = R; h.W = W; h.NW = NW;
@@ -389,11 +391,18 @@ pt_status lattice_host(const pt_instance_desc& d, LatHost& h, int k) {
             if (wrap[dd]) h.eb[(size_t)(3 + dd) * NW + (i >> 5)] |= 1u << (i & 31);
         }
     }
-    h.thr.assign(4 * (size_t)R, 0u);
-    for (int r = 0; r < R; ++r) {
-        h.thr[4 * r + 0] = metropolis_threshold(d.beta[r], 4);
-        h.thr[4 * r + 1] = metropolis_threshold(d.beta[r], 8);
-        h.thr[4 * r + 2] = metropolis_threshold(d.beta[r], 12);
+    if (gibbs) {
+        // class q = 0..6 has the local field I = 6 - 2q (Methods, Eq. 5)
+        h.thr.assign(8 * (size_t)R, 0u);
+        for (int r = 0; r < R; ++r)
+            for (int q = 0; q < 7; ++q) h.thr[8 * r + q] = gibbs_threshold(d.beta[r], 6 - 2 * q);
+    } else {
+        h.thr.assign(4 * (size_t)R, 0u);
+        for (int r = 0; r < R; ++r) {
+            h.thr[4 * r + 0] = metropolis_threshold(d.beta[r], 4);
+            h.thr[4 * r + 1] = metropolis_threshold(d.beta[r], 8);
+            h.thr[4 * r + 2] = metropolis_threshold(d.beta[r], 12);
+        }
     }
     h.sow.assign(W * 32, -1);
     h.wos.assign(R, 0);
@@ -424,7 +433,7 @@ pt_status lattice_group_shape(pt_ctx* c, Group& g, int T) {
     size_t smem = 0;
     for (int k : g.members) {
         const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0,
-                                           c->with_ctx != 0);
+                                           c->with_ctx != 0, c->cfg.update == 1);
         smem = std::max(smem, l.total);
     }
     if (smem > (size_t)c->optin)
@@ -445,7 +454,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
     for (int k = 0; k < n; ++k) {
         const pt_instance_desc& d = descs[k];
         LatHost h;
-        pt_status st = lattice_host(d, h, k);
+        pt_status st = lattice_host(d, h, k, c->cfg.update == 1);
         if (st != PT_OK) return st;
         c->N[k] = h.N; c->R[k] = h.R; c->W[k] = h.W; c->NW[k] = h.NW; c->R4[k] = h.W * 32; c->L[k] = h.L;
         maxitems[k] = h.maxitems;
@@ -861,10 +870,12 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
         if (cfg->context_log2 < 1 || cfg->context_log2 > 3)
             return fail(PT_EINVAL, "context_log2 must be 1, 2 or 3");
         if (cfg->context_sweeps < 1) return fail(PT_EINVAL, "context_sweeps must be >= 1");
+        if (cfg->update != 0)
+            return fail(PT_ENOTSUP, "contextual proposals are implemented with Metropolis sweeps");
         for (int k = 0; k < n; ++k) {
-            if (!is_lattice_desc(descs[k], *cfg))
+            if (!is_lattice_desc(descs[k]))
                 return fail(PT_ENOTSUP, "instance %d: contextual proposals are implemented for the "
-                                        "lattice engine (Metropolis, J = +-1, no field or clamp)", k);
+                                        "lattice engine (J = +-1, no field or clamp)", k);
             pt_status s = context_slots_ok(descs[k], k);
             if (s != PT_OK) return s;
         }
@@ -873,9 +884,9 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
         pt_status s = validate(descs[k], k);
         if (s != PT_OK) return s;
     }
-    const bool lat0 = is_lattice_desc(descs[0], *cfg);
+    const bool lat0 = is_lattice_desc(descs[0]);
     for (int k = 1; k < n; ++k)
-        if (is_lattice_desc(descs[k], *cfg) != lat0)
+        if (is_lattice_desc(descs[k]) != lat0)
             return fail(PT_EINVAL, "instance %d: a context holds only lattice-engine or only graph-engine instances", k);
     pt_ctx* c = new (std::nothrow) pt_ctx();
     if (!c) return fail(PT_ENOMEM, "host allocation failed");
@@ -1085,7 +1096,7 @@ pt_status pt_set_instance(pt_ctx* ctx, int32_t inst, const pt_instance_desc* des
     if (ctx->engine != 0) return fail(PT_ENOTSUP, "slot replacement is implemented for the lattice engine");
     s = validate(*desc, inst);
     if (s != PT_OK) return s;
-    if (!is_lattice_desc(*desc, ctx->cfg)) return fail(PT_EINVAL, "the new instance needs the lattice engine");
+    if (!is_lattice_desc(*desc)) return fail(PT_EINVAL, "the new instance needs the lattice engine");
     if (ctx->with_ctx) {
         s = context_slots_ok(*desc, inst);
         if (s != PT_OK) return s;
@@ -1094,7 +1105,7 @@ pt_status pt_set_instance(pt_ctx* ctx, int32_t inst, const pt_instance_desc* des
         return fail(PT_EINVAL, "slot %d holds L=%d, R=%d; the new instance must have the same shape",
                     inst, ctx->L[inst], ctx->R[inst]);
     LatHost h;
-    s = lattice_host(*desc, h, inst);
+    s = lattice_host(*desc, h, inst, ctx->cfg.update == 1);
     if (s != PT_OK) return s;
     LatInst& I = ctx->lat[inst];
     lattice_fill_inst(I, h, desc->instance_id, ctx->cfg.pool_size);

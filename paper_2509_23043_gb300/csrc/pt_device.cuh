@@ -139,7 +139,7 @@ struct LatInst {
 };
 
 // Lattice kernel flags: pool proposals, contextual proposals
-constexpr int kWithPool = 1, kWithContext = 2;
+constexpr int kWithPool = 1, kWithContext = 2, kGibbs = 4;
 
 // Kernel modes
 enum : int32_t {

@@ -84,3 +84,6 @@ def test_contextual_proposals_rejected_where_unsupported():
     with pytest.raises(pt.PTError):          # kept fraction 2^-4
         pt.create_instances([inst], [[0.5, 1.0]],
                             pt.Config(proposal_source=pt.CONTEXT, context_log2=4))
+    with pytest.raises(pt.PTError):          # Gibbs sweeps (the refill is Metropolis)
+        pt.create_instances([inst], [[0.5, 1.0]],
+                            pt.Config(update=pt.GIBBS, proposal_source=pt.CONTEXT))

@@ -55,14 +55,17 @@ def test_config1_plain_pt_full_run():
     assert list(c) == [10_000, 10_000, 0]
 
 
-def test_config2_batched_tapt_sampled():
+@pytest.mark.parametrize("update", [pt.METROPOLIS, pt.GIBBS])
+def test_config2_batched_tapt_sampled(update):
     # 256 EA L=10, R=32, pools of 1024 per slot, proposals every 10 sweeps from sweep 100 on
-    # the 30 hottest slots (the benchmark's layout and launch shape)
+    # the 30 hottest slots (the benchmark's layout and launch shape), Metropolis (the
+    # benchmark's rule) and Gibbs
     B, R, P = 256, 32, 1024
     insts = [I.ea_instance(10, index=k) for k in range(B)]
     betas = [I.geometric_betas(0.1, 3.0, R)] * B
     prop = [[1] * (R - 2) + [0, 0]] * B
-    cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=100, pool_size=P)
+    cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=100, pool_size=P,
+                    update=update)
     ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=list(range(B)))
     assert pt.info(ctx)["threads"] == 256
     samples = (0, 131, 255)
@@ -74,7 +77,7 @@ def test_config2_batched_tapt_sampled():
     pt.run_cycles(ctx, 130)
     for k in samples:
         o = O.Oracle(insts[k], betas[k], instance_id=k, prop_enabled=prop[k], propose_every=10,
-                     propose_start=100, seed=0x7A972509, pool_size=P)
+                     propose_start=100, seed=0x7A972509, pool_size=P, update=update)
         for r in range(R):
             o.load_pool(r, pools[k][r])
         o.run_cycles(130)

@@ -42,11 +42,12 @@ def _ea_pool(inst, R, P, seed):
     return [I.random_configs(inst.n_spins, P, seed=seed, index=r) for r in range(R)]
 
 
+@pytest.mark.parametrize("update", [0, 1])
 @pytest.mark.parametrize("L,R", [(6, 16), (4, 32), (2, 5), (3, 8), (5, 33), (4, 70)])
-def test_lattice_cycles_match_oracle(L, R):
+def test_lattice_cycles_match_oracle(L, R, update):
     inst = I.ea_instance(L, index=L * 7 + R)
     betas = I.geometric_betas(0.2, 3.0, R)
-    cfg = pt.Config(seed=0x5EED + L, sweeps_per_cycle=1)
+    cfg = pt.Config(seed=0x5EED + L, sweeps_per_cycle=1, update=update)
     ctx = pt.create_instances([inst], [betas], cfg, instance_ids=[17])
     assert pt.info(ctx)["engine"] == "lattice"
     o = _oracle(inst, betas, cfg, 17)
@@ -58,13 +59,15 @@ def test_lattice_cycles_match_oracle(L, R):
     _stats_same(ctx, 0, o)
 
 
+@pytest.mark.parametrize("update", [0, 1])
 @pytest.mark.parametrize("M", [1, 3])
-def test_lattice_tapt_with_pool_matches_oracle(M):
+def test_lattice_tapt_with_pool_matches_oracle(M, update):
     L, R, P = 4, 12, 37
     inst = I.ea_instance(L, index=3)
     betas = I.geometric_betas(0.1, 3.0, R)
     prop = [1] * (R - 2) + [0, 0]
-    cfg = pt.Config(seed=77, sweeps_per_cycle=M, propose_every=2, propose_start=4, pool_size=P)
+    cfg = pt.Config(seed=77, sweeps_per_cycle=M, propose_every=2, propose_start=4, pool_size=P,
+                    update=update)
     ctx = pt.create_instances([inst], [betas], cfg, prop_enabled=[prop], instance_ids=[5])
     o = _oracle(inst, betas, cfg, 5, prop)
     pools = _ea_pool(inst, R, P, 99)
@@ -154,15 +157,21 @@ def test_multiplier_graph_matches_oracle(update):
     _stats_same(ctx, 0, o)
 
 
+@pytest.mark.parametrize("engine", ["lattice", "graph"])
 @pytest.mark.parametrize("L", [3, 4])
-def test_lattice_gibbs_runs_on_graph_engine(L):
+def test_lattice_gibbs_on_both_engines(L, engine):
+    # a lattice runs on the bit-packed engine (bit-plane uniforms); the same couplings given
+    # as a general graph run on the int8 engine (one uniform word per walker)
     inst = I.ea_instance(L, index=50 + L)
+    if engine == "graph":
+        inst = I.Instance(inst.n_spins, inst.edge_i, inst.edge_j, inst.edge_J, None, None, 0)
     R = 6
     betas = I.geometric_betas(0.2, 2.0, R)
     cfg = pt.Config(update=1, seed=9)
     ctx = pt.create_instances([inst], [betas], cfg, instance_ids=[L])
-    assert pt.info(ctx)["engine"] == "graph"
+    assert pt.info(ctx)["engine"] == engine
     o = _oracle(inst, betas, cfg, L)
+    assert o.bitplane == (engine == "lattice")
     pt.run_cycles(ctx, 30)
     o.run_cycles(30)
     _assert_same(ctx, 0, o)
