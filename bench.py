@@ -49,7 +49,7 @@ ALU_LANES_PER_SM = 64
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--instances", type=int, default=256)
@@ -129,8 +129,9 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
+        self.rows = []          # (monotonic time of arrival, fields)
         self.proc = None
+        self.window = None      # (start, end) of the timed region
 
     def __enter__(self):
         try:
@@ -145,7 +146,16 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([t.strip() for t in line.split(",")])
+            self.rows.append((time.monotonic(), [t.strip() for t in line.split(",")]))
+
+    def wait_first(self, timeout=3.0):
+        """Block until the first sample has arrived, so that sampling covers the timed region."""
+        t0 = time.monotonic()
+        while self.proc and not self.rows and time.monotonic() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self, start, end):
+        self.window = (start, end)
 
     def __exit__(self, *a):
         if self.proc:
@@ -156,11 +166,19 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        rows = [r for _, r in self.rows]
+        if self.window:
+            # samples that arrived during the timed region (each reports the state at most one
+            # sampling period earlier), else the one just after it
+            a, b = self.window
+            inside = [r for t, r in self.rows if a <= t <= b + 0.2]
+            later = [r for t, r in self.rows if t > b]
+            rows = inside or later[:1] or rows
+        sm = [float(r[0]) for r in rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             if len(r) < 8:
                 continue
             for k, nm in enumerate(names):
@@ -753,6 +771,10 @@ def run_reference(args):
     pool = mp.get_context("spawn").Pool(cores)
     for _ in range(args.warmup):
         cpu_oracle(args, cores, 2, pool)
+    # each step's sample is sized so that the K timed steps take about two minutes in all
+    probe = cpu_oracle(args, n_inst, 2, pool)
+    per_cycle_s = max(probe["wall_s"] / 2, 1e-6)
+    sweeps = int(max(2, min(sweeps, 120.0 / (max(args.steps, 1) * per_cycle_s))))
     tot_att, tot_t = 0, 0.0
     for _ in range(args.steps):
         r = cpu_oracle(args, n_inst, sweeps, pool)
@@ -830,12 +852,15 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        t_start = time.monotonic()
         for k in range(args.steps):
             flush.zero_()                       # L2 flush between timed steps (untimed)
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+        clk.mark(t_start, time.monotonic())
     if dist:
         dist.barrier()
     ms = shard.job_ms(sum(a.elapsed_time(b) for a, b in ev), dist, device="cuda")
