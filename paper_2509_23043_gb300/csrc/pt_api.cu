@@ -149,6 +149,7 @@ struct pt_ctx {
     int NWmax = 0;
     int uniformN = -1;        // N when all instances share it, else -1
     int optin = 0;            // device limit on dynamic shared memory per block
+    int sms = 0;              // streaming multiprocessors of the device
     std::vector<int> N, R, W, NW, R4, L;
     std::vector<size_t> slab_off;  // words, instance offset inside one pool entry
     size_t slab = 0;               // words per pool entry (all instances, all slots)
@@ -418,10 +419,13 @@ void lattice_fill_inst(LatInst& I, const LatHost& h, uint32_t iid, int P) {
     for (int cc = 0; cc < 4; ++cc) I.col_off[cc] = h.col_off[cc];
 }
 
-// Block shape of a lattice group: about two words per thread per colour class (at most 42,
-// the width of the energy counters), unless threads_per_block fixes it.
-int lattice_auto_threads(int maxitems) {
-    int T = ((maxitems / 2 + 31) / 32) * 32;
+// Block shape of a lattice group, unless threads_per_block fixes it: about two words per
+// thread per colour class, so that two blocks share an SM; or, when the context holds at most
+// half as many instances as the device has SMs (the SMs are not all busy anyway), about one
+// word per thread, which shortens each cycle. Capped at 512 threads (and the words per thread
+// at 42, the width of the energy counters).
+int lattice_auto_threads(int maxitems, bool few) {
+    int T = ((maxitems / (few ? 1 : 2) + 31) / 32) * 32;
     return std::max(64, std::min(512, T));
 }
 
@@ -499,7 +503,8 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
             g.maxW = std::max(g.maxW, c->W[k]);
         }
         if (g.maxW > 2) g.maxW = 4;
-        const int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block : lattice_auto_threads(g.maxitems);
+        const int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block
+                                                    : lattice_auto_threads(g.maxitems, 2 * c->n <= c->sms);
         pt_status st = lattice_group_shape(c, g, T);
         if (st != PT_OK) return st;
     }
@@ -901,6 +906,8 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
         cudaError_t e0 = cudaGetDevice(&dev);
         if (e0 == cudaSuccess)
             e0 = cudaDeviceGetAttribute(&c->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e0 == cudaSuccess)
+            e0 = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (e0 != cudaSuccess) { release(c); return fail(PT_ECUDA, "device query: %s", cudaGetErrorString(e0)); }
     }
     for (int k = 0; k < n; ++k) c->L[k] = descs[k].lattice_L;
