@@ -104,8 +104,8 @@ struct Counters {
     long long pad;
 };
 
-// Lattice engine: periodic L^3, J = +-1, no field, no clamp, Metropolis. Spins bit-packed:
-// word [wb][site], bit b = walker 32*wb + b.
+// Lattice engine: periodic L^3, J = +-1, no field, no clamp, Metropolis or Gibbs. Spins
+// bit-packed: word [wb][site], bit b = walker 32*wb + b.
 struct LatInst {
     uint32_t iid;
     int32_t L, N, R, W, NW, ncol, P;
@@ -127,7 +127,8 @@ struct LatInst {
     int32_t* E;            // [W*32] per walker
     int16_t* sow;          // [W*32] slot of walker (-1: padding lane)
     int16_t* wos;          // [R] walker of slot
-    const uint32_t* thr;   // [R][4] Metropolis thresholds for dE = 4, 8, 12 (and 0 pad)
+    const uint32_t* thr;   // [R][4] Metropolis thresholds for dE = 4, 8, 12 (and 0 pad), or
+                           // [R][8] Gibbs thresholds for I = 6 - 2q, q = 0..6 (and 0 pad)
     const double* beta;    // [R]
     const uint8_t* prop;   // [R]
     int32_t* cursor;       // [R]
@@ -155,7 +156,7 @@ struct RunArgs {
     int32_t mode;
     int32_t n;
     int32_t M, every, start, stop;
-    int32_t update;      // graph engine: 0 Metropolis, 1 Gibbs
+    int32_t update;      // 0 Metropolis, 1 Gibbs (the lattice engine takes it from its template)
     int32_t prule;       // proposal rule: 0 Delta-E-only, 1 always accept
     int32_t ctx_log2;    // contextual proposals: a site is kept with probability 2^-ctx_log2
     int32_t ctx_sweeps;  // contextual proposals: refill sweeps

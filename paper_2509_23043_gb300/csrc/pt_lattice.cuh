@@ -1,5 +1,5 @@
 // Lattice engine: parallel tempering with global proposals (Algorithm 1 of arXiv 2509.23043)
-// on periodic L^3 Edwards-Anderson +-J instances with Metropolis local moves.
+// on periodic L^3 Edwards-Anderson +-J instances with Metropolis or Gibbs local moves.
 //
 // Layout. The R replicas of an instance are "walkers" packed 32 per uint32 word: word
 // [wb][site] holds spin `site` of walkers 32*wb .. 32*wb+31, bit b set iff spin = +1. A
