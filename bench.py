@@ -426,6 +426,19 @@ def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
             "threads_per_class": sorted({gr["threads"] for gr in groups}), "prep_s": round(prep, 1)}
 
 
+def _mark_factored(ctx, mult, products, solved_at, sweeps):
+    """Success of a factorization run (S4): some replica decodes to A * B = C with A, B > 1.
+    Marks every instance k not yet solved whose state succeeds now with `sweeps`."""
+    import paper_2509_23043_gb300 as pt
+    wA = 1 << np.arange(mult.w)
+    for k in np.nonzero(solved_at < 0)[0]:
+        sp, _ = pt.read_state(ctx, int(k))
+        A = (sp[:, mult.A] > 0) @ wA
+        B = (sp[:, mult.B] > 0) @ wA
+        if np.any((A * B == products[k]) & (A > 1) & (B > 1)):
+            solved_at[k] = sweeps
+
+
 def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=25, chunk=1000):
     """The 8x8-bit multiplier (N = 200) with the product bits clamped to n products of two
     primes <= 255; R = 32 on 0.05 -> 5.0, proposals every 10 sweeps on the 23 hottest slots,
@@ -461,7 +474,6 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
     pt.destroy(gen)
     stream.synchronize()
     prep = time.perf_counter() - t0
-    wA = 1 << np.arange(mult.w)
     att = n * R * int((insts[0].clamp == 0).sum())
     out = {"workload": f"{n} clamped 8x8-bit multipliers (N={mult.n_spins}), R={R} on "
                        f"0.05->5.0, proposals every 10 sweeps on 23 slots from per-product pools "
@@ -480,13 +492,7 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
             e.synchronize()
             t_gpu += s.elapsed_time(e)
             done += step
-            for k in np.nonzero(solved_at < 0)[0]:
-                sp, _ = pt.read_state(ctx, int(k))
-                A = (sp[:, mult.A] > 0) @ wA
-                B = (sp[:, mult.B] > 0) @ wA
-                C = prods[k][0]
-                if np.any((A * B == C) & (A > 1) & (B > 1)):
-                    solved_at[k] = done
+            _mark_factored(ctx, mult, [C for C, _, _ in prods], solved_at, done)
             checkpoints[done] = int((solved_at >= 0).sum())
         pt.destroy(ctx)
         out[name] = {"attempts_per_ns": att * done / (t_gpu * 1e6),
@@ -548,7 +554,6 @@ def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, ch
     insts = [mult.instance(C) for C, _, _ in prods for _ in range(runs)]
     ids = [1000 * k + j for k in range(n_products) for j in range(runs)]
     n = len(insts)
-    wA = 1 << np.arange(mult.w)
     checks = list(range(check // 10, check, check // 10)) + list(range(check, t_max + 1, check))
     t0 = time.perf_counter()
     banks = {"tapt_universal_bank": _chain_bank(stream, [mult.instance(None)], betas, chains,
@@ -582,13 +587,7 @@ def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, ch
             b_.synchronize()
             t_ms += a_.elapsed_time(b_)
             done = t
-            for k in np.nonzero(solved_at < 0)[0]:
-                sp, _ = pt.read_state(ctx, int(k))
-                A = (sp[:, mult.A] > 0) @ wA
-                B = (sp[:, mult.B] > 0) @ wA
-                C = prods[k // runs][0]
-                if np.any((A * B == C) & (A > 1) & (B > 1)):
-                    solved_at[k] = t
+            _mark_factored(ctx, mult, [prods[k // runs][0] for k in range(n)], solved_at, t)
         pt.destroy(ctx)
         per_sweep_s = t_ms * 1e-3 / (n * t_max)          # device time per run and sweep
         best = np.array([TT.optimal_tts(checks, TT.success_curve(
