@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12,13,14,15,16")
     p.add_argument("--serve-budget", type=int, default=100_000)
     p.add_argument("--serve-gap-ms", type=float, default=4.0)
+    p.add_argument("--serve-load", type=float, default=0.7,
+                   help="offered load as a fraction of the served TAPT capacity (the completion "
+                        "rate with every request submitted at once); 0 keeps --serve-gap-ms")
     p.add_argument("--serve-pool-burnin", type=int, default=100_000)
     p.add_argument("--serve-pool-gap", type=int, default=100)
     p.add_argument("--serve-hbm-frac", type=float, default=0.5,
@@ -290,12 +293,23 @@ def served_stream(args, stream):
                          gap=args.serve_pool_gap, stream=stream)
     eref = S.reference_energies(insts, [betas] * n, ids, sweeps=200_000, chunk=2000, stream=stream)
     prep_s = time.perf_counter() - t0
-    arrivals = np.cumsum(g.exponential(args.serve_gap_ms * 1e-3, size=n))
-    arrivals -= arrivals[0]
+    unit = np.cumsum(g.exponential(1.0, size=n))        # arrival pattern, scaled by the mean gap
+    unit -= unit[0]
     mk = lambda k, a: S.Request(ids[k], insts[k], betas, prop, pools[k], eref[k], arrival=float(a))
     cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
     slots = {L: 4 for L in Ls}
     budget = int(args.serve_hbm_frac * sum(4 * S.footprint_bytes(L, R, P) for L in Ls))
+    gap_s, capacity = args.serve_gap_ms * 1e-3, None
+    if args.serve_load > 0:
+        # capacity: the completion rate of the TAPT server with every request submitted at
+        # once (n / makespan, admission limited by slots and the device-memory budget); the
+        # measured stream then arrives at serve_load x capacity
+        cal = S.TaptServer(slots, betas, prop, cfg, hbm_budget=budget, tick_cycles=100,
+                           stream=stream)
+        done = cal.serve([mk(k, 0.0) for k in range(n)], budget_sweeps=args.serve_budget)
+        capacity = n / max(r.finished for r in done)
+        gap_s = 1.0 / (args.serve_load * capacity)
+    arrivals = unit * gap_s
     srv = S.TaptServer(slots, betas, prop, cfg, hbm_budget=budget, tick_cycles=100, stream=stream)
     served = srv.serve([mk(k, arrivals[k]) for k in range(n)], budget_sweeps=args.serve_budget)
     cfg_pt = pt.Config(seed=0x7A972509, propose_every=0, pool_size=0)
@@ -308,7 +322,7 @@ def served_stream(args, stream):
     alone = [S.run_alone(mk(k, 0.0), cfg_pt, budget_sweeps=args.serve_budget, tick_cycles=100,
                          stream=stream) for k in range(n)]
     return {"workload": f"{n} requests, L uniform in {{{args.serve_L}}}, R={R}, Poisson arrivals "
-                        f"(mean gap {args.serve_gap_ms} ms), target E_ref + 0.1%|E_ref| "
+                        f"(mean gap {gap_s * 1e3:.2f} ms), target E_ref + 0.1%|E_ref| "
                         f"(E_ref: best of a 2e5-sweep PT run), budget {args.serve_budget} sweeps, "
                         f"pools P={P} from PT runs of {args.serve_pool_burnin} + "
                         f"{args.serve_pool_gap * P} sweeps (untimed, {prep_s:.1f} s)",
@@ -316,7 +330,9 @@ def served_stream(args, stream):
             "served_plain_pt": S.summarize(served_pt),
             "plain_pt_one_instance_per_launch": S.summarize(alone),
             "slots_per_L": 4, "hbm_budget_bytes": budget, "peak_bytes_admitted": srv.peak_used,
-            "peak_requests_in_flight": srv.peak_active}
+            "peak_requests_in_flight": srv.peak_active,
+            "capacity_per_s": capacity, "offered_per_s": 1.0 / gap_s,
+            "load": (1.0 / gap_s) / capacity if capacity else None}
 
 
 # ------------------------------------------------------------------------------ other workloads

@@ -253,11 +253,15 @@ def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int
 
 
 def summarize(reqs: list[Request]) -> dict:
-    """p50/p99 time-to-solution (s and sweeps) over the solved requests, and the fitted TTS
-    exponent k of log TTS = a + k L (least squares over the per-L medians, as in Eq. for
-    TTS(n) = A exp(k n) of Supplementary S5)."""
+    """p50/p99 time-to-solution (s and sweeps) over the solved requests, the mean wait
+    (arrival to admission) and service (admission to retirement) over all requests, and the
+    fitted TTS exponent k of log TTS = a + k L (least squares over the per-L medians, as in
+    Eq. for TTS(n) = A exp(k n) of Supplementary S5)."""
     solved = [r for r in reqs if r.sweeps >= 0]
     out = {"requests": len(reqs), "solved": len(solved)}
+    if reqs:
+        out["mean_wait_s"] = float(np.nanmean([r.admitted - r.arrival for r in reqs]))
+        out["mean_service_s"] = float(np.nanmean([r.finished - r.admitted for r in reqs]))
     if not solved:
         return out
     t = np.array([r.tts for r in solved])
