@@ -255,8 +255,8 @@ def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int
 def summarize(reqs: list[Request]) -> dict:
     """p50/p99 time-to-solution (s and sweeps) over the solved requests, the mean wait
     (arrival to admission) and service (admission to retirement) over all requests, and the
-    fitted TTS exponent k of log TTS = a + k L (least squares over the per-L medians, as in
-    Eq. for TTS(n) = A exp(k n) of Supplementary S5)."""
+    fitted TTS exponent k of log TTS = a + k L, and of log TTS = a + k N with N = L^3 (least
+    squares over the per-L medians, as in TTS(n) = A exp(k n) of Supplementary S5)."""
     solved = [r for r in reqs if r.sweeps >= 0]
     out = {"requests": len(reqs), "solved": len(solved)}
     if reqs:
@@ -274,4 +274,7 @@ def summarize(reqs: list[Request]) -> dict:
         medsw = [float(np.median([r.sweeps for r in solved if r.L == L])) for L in Ls]
         out["k_seconds_per_L"] = float(np.polyfit(Ls, np.log(med), 1)[0])
         out["k_sweeps_per_L"] = float(np.polyfit(Ls, np.log(medsw), 1)[0])
+        Ns = [L ** 3 for L in Ls]                     # the same fit against the spin count
+        out["k_seconds_per_N"] = float(np.polyfit(Ns, np.log(med), 1)[0])
+        out["k_sweeps_per_N"] = float(np.polyfit(Ns, np.log(medsw), 1)[0])
     return out
