@@ -7,7 +7,9 @@ context of pre-sized slots (one size class per L); a request is admitted into a 
 its class when the device-memory budget allows. Its replica state and pool then stay on the
 device and it runs, cycle after cycle, together with every other admitted request in the
 same launches. When its best replica energy reaches the target, or the sweep budget is spent,
-it retires and frees its slot.
+it retires and frees its slot. A request that can never be admitted (no slot class for its L,
+or a footprint above the device-memory budget) is rejected at arrival; a request can be
+cancelled, and one past its deadline retires unsolved, whether waiting or running.
 
 Every request's random streams are keyed by its request id, and its counters start at zero
 on admission, so its trajectory (and its sweeps-to-target) is the same alone or in the mix.
@@ -37,10 +39,12 @@ class Request:
     pool: np.ndarray | None     # uint32 [P][R][ceil(N/32)]
     e_ref: int                  # reference lowest energy
     arrival: float = 0.0        # seconds after the start of the stream
+    deadline: float = math.inf  # seconds after arrival; past it the request retires unsolved
     admitted: float = math.nan
     finished: float = math.nan
-    sweeps: int = -1            # sweeps from admission to the target (-1: budget spent)
+    sweeps: int = -1            # sweeps from admission to the target (-1: not reached)
     best: int = 0
+    status: str = "pending"     # then "solved", "budget", "rejected", "cancelled", "timeout"
 
     @property
     def L(self) -> int:
@@ -160,6 +164,16 @@ class TaptServer:
         self.used = 0
         self.peak_used = 0        # largest footprint admitted at once (bytes)
         self.peak_active = 0      # most requests in flight at once
+        self.cancelled: set[int] = set()
+
+    def cancel(self, rid: int) -> None:
+        """Withdraw request `rid`: dropped if still waiting, retired at the next tick if running."""
+        self.cancelled.add(rid)
+
+    def fits(self, req: Request) -> bool:
+        """Whether the request can ever be admitted: a slot class for its L, and a footprint
+        within the device-memory budget."""
+        return req.L in self.free and (self.budget is None or self._fp(req) <= self.budget)
 
     def _fp(self, req: Request) -> int:
         return footprint_bytes(req.L, self.R, self.cfg.pool_size)
@@ -181,6 +195,14 @@ class TaptServer:
         req.admitted = now
         return True
 
+    def _retire(self, k: int, req: Request, now: float, status: str) -> None:
+        req.status = status
+        req.finished = now
+        set_active(self.ctx, k, False)
+        self.free[req.L].append(k)
+        self.used -= self._fp(req)
+        del self.active[k]
+
     def tick(self, now_fn, budget_sweeps: int) -> list[Request]:
         if not self.active:
             return []
@@ -195,14 +217,18 @@ class TaptServer:
             self.ticks_of[k] += 1
             sw = self.ticks_of[k] * self.tick_cycles * self.cfg.sweeps_per_cycle
             req.best = int(E[k].min())
-            if req.best <= req.target or sw >= budget_sweeps:
-                req.sweeps = sw if req.best <= req.target else -1
-                req.finished = now
-                set_active(self.ctx, k, False)
-                self.free[req.L].append(k)
-                self.used -= self._fp(req)
-                del self.active[k]
-                done.append(req)
+            if req.best <= req.target:
+                req.sweeps = sw
+                self._retire(k, req, now, "solved")
+            elif sw >= budget_sweeps:
+                self._retire(k, req, now, "budget")
+            elif req.rid in self.cancelled:
+                self._retire(k, req, now, "cancelled")
+            elif now - req.arrival > req.deadline:
+                self._retire(k, req, now, "timeout")
+            else:
+                continue
+            done.append(req)
         return done
 
     def serve(self, requests: list[Request], budget_sweeps: int) -> list[Request]:
@@ -215,15 +241,25 @@ class TaptServer:
         while pending or waiting or self.active:
             t = now()
             while pending and pending[0].arrival <= t:
-                waiting.append(pending.pop(0))
+                req = pending.pop(0)
+                if not self.fits(req):                   # could never be admitted
+                    req.status, req.finished = "rejected", t
+                    finished.append(req)
+                else:
+                    waiting.append(req)
             still = []
             for req in waiting:
-                if not self.try_admit(req, now()):
+                if req.rid in self.cancelled or t - req.arrival > req.deadline:
+                    req.status = "cancelled" if req.rid in self.cancelled else "timeout"
+                    req.finished = t
+                    finished.append(req)
+                elif not self.try_admit(req, now()):
                     still.append(req)
             waiting = still
             if not self.active:
-                if pending:
-                    time.sleep(max(0.0, min(0.002, pending[0].arrival - now())))
+                if pending or waiting:
+                    nxt = pending[0].arrival - now() if pending else 0.002
+                    time.sleep(max(0.0, min(0.002, nxt)))
                 continue
             finished += self.tick(now, budget_sweeps)
         return finished
@@ -245,6 +281,7 @@ def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int
         req.best = int(energies(ctx)[0].min())
         if req.best <= req.target or sw >= budget_sweeps:
             req.sweeps = sw if req.best <= req.target else -1
+            req.status = "solved" if req.best <= req.target else "budget"
             break
     req.finished = time.perf_counter() - t0
     req.arrival = 0.0
@@ -259,6 +296,10 @@ def summarize(reqs: list[Request]) -> dict:
     squares over the per-L medians, as in TTS(n) = A exp(k n) of Supplementary S5)."""
     solved = [r for r in reqs if r.sweeps >= 0]
     out = {"requests": len(reqs), "solved": len(solved)}
+    for st in ("budget", "rejected", "cancelled", "timeout"):
+        n = sum(r.status == st for r in reqs)
+        if n:
+            out[st] = n
     if reqs:
         out["mean_wait_s"] = float(np.nanmean([r.admitted - r.arrival for r in reqs]))
         out["mean_service_s"] = float(np.nanmean([r.finished - r.admitted for r in reqs]))
