@@ -19,13 +19,14 @@ def _same(ctx, k, o):
     assert np.array_equal(s, so)
 
 
-def test_largest_lattice_L20_R32():
+@pytest.mark.parametrize("update", [0, 1])
+def test_largest_lattice_L20_R32(update):
     inst = I.ea_instance(20, index=2)                  # N = 8000, the engine's limit
     betas = I.geometric_betas(0.2, 2.5, 32)
-    ctx = pt.create_instances([inst], [betas], pt.Config(seed=9), instance_ids=[4])
+    ctx = pt.create_instances([inst], [betas], pt.Config(seed=9, update=update), instance_ids=[4])
     assert pt.info(ctx)["engine"] == "lattice"
     pt.run_cycles(ctx, 4)
-    o = O.Oracle(inst, betas, instance_id=4, seed=9)
+    o = O.Oracle(inst, betas, instance_id=4, seed=9, update=update)
     o.run_cycles(4)
     _same(ctx, 0, o)
 

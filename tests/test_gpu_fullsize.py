@@ -153,12 +153,14 @@ def test_config4_factorization_sampled(update, every):
     _check_properties(ctx, insts, range(0, len(insts), 50))
 
 
-def test_maximal_walker_blocks_and_single_replica():
+@pytest.mark.parametrize("update", [0, 1])
+def test_maximal_walker_blocks_and_single_replica(update):
     inst = I.ea_instance(16, index=4)
     for R in (128, 1):
         betas = I.geometric_betas(0.3, 2.0, R)
-        ctx = pt.create_instances([inst], [betas], pt.Config(seed=5), instance_ids=[3])
+        ctx = pt.create_instances([inst], [betas], pt.Config(seed=5, update=update),
+                                  instance_ids=[3])
         pt.run_cycles(ctx, 3)
-        o = O.Oracle(inst, betas, instance_id=3, seed=5)
+        o = O.Oracle(inst, betas, instance_id=3, seed=5, update=update)
         o.run_cycles(3)
         _compare(ctx, 0, o)
