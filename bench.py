@@ -549,7 +549,8 @@ def _chain_bank(stream, src, betas, chains, captures, burn, gap, seed, id0):
 
 
 def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, check=1000,
-                      chains=256, captures=4, burn=100_000, gap=250, n_prop=23):
+                      chains=256, captures=4, burn=100_000, gap=250, n_prop=23,
+                      modes=("plain_pt", "tapt_universal_bank", "tapt_instance_bank")):
     """Time to solution of Supplementary S5 on the w x w multiplier (2w-bit products of two
     primes below 2^w): every product is run `runs` times independently by plain PT and by
     TAPT, which proposes once per sweep on the n_prop hottest of R slots from a pre-generated
@@ -572,16 +573,19 @@ def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, ch
     n = len(insts)
     checks = list(range(check // 10, check, check // 10)) + list(range(check, t_max + 1, check))
     t0 = time.perf_counter()
-    banks = {"tapt_universal_bank": _chain_bank(stream, [mult.instance(None)], betas, chains,
-                                                captures, burn, gap, 0x9004, 6_000_000),
-             "tapt_instance_bank": _chain_bank(stream, [mult.instance(C) for C, _, _ in prods],
-                                               betas, chains, captures, burn, gap, 0x9005,
-                                               6_100_000)}
+    banks = {}
+    if "tapt_universal_bank" in modes:
+        banks["tapt_universal_bank"] = _chain_bank(stream, [mult.instance(None)], betas, chains,
+                                                   captures, burn, gap, 0x9004, 6_000_000)
+    if "tapt_instance_bank" in modes:
+        banks["tapt_instance_bank"] = _chain_bank(stream, [mult.instance(C) for C, _, _ in prods],
+                                                  betas, chains, captures, burn, gap, 0x9005,
+                                                  6_100_000)
     prep = time.perf_counter() - t0
     start = np.random.default_rng(0x57A7).integers(0, P, size=n)      # each run's first entry
     entry = (np.arange(P)[:, None] + start[None, :]) % P
     out = {}
-    for name in ("plain_pt", "tapt_universal_bank", "tapt_instance_bank"):
+    for name in modes:
         kw = {} if name == "plain_pt" else dict(propose_every=1, propose_start=0, pool_size=P)
         cfg = pt.Config(update=pt.GIBBS, seed=0x7A97, **kw)
         ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
@@ -627,7 +631,8 @@ def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, ch
             "target_success": TT.P_TARGET, "modes": out}
 
 
-def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23):
+def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23,
+                modes=("plain_pt", "tapt_universal_bank", "tapt_instance_bank")):
     """The scaling fit of Fig. 5 (S5): median TTS* at product sizes n = 2w, then
     TTS(n) = A exp(k n) by least squares on log TTS, for plain PT and both TAPT banks, in
     sweeps and in seconds. Run lengths grow with n (5e4 * 2^(w-8) sweeps). 32 x 23 runs keep
@@ -637,7 +642,7 @@ def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23):
     for w in ws:
         f = 1 << (w - 8)
         per[2 * w] = factorization_tts(stream, w=w, n_products=n_products, runs=runs,
-                                       t_max=50_000 * f, check=1000 * f)
+                                       t_max=50_000 * f, check=1000 * f, modes=modes)
     modes = list(next(iter(per.values()))["modes"])
     fits = {}
     for m in modes:
@@ -983,6 +988,10 @@ def main():
             others["factorization_tts"] = factorization_tts(stream)
         if "tts_scaling" in wl:
             others["tts_scaling"] = tts_scaling(stream)
+        if "tts_scaling_pt" in wl:
+            # plain PT alone over the paper's full range of product sizes, n = 16 .. 24
+            others["tts_scaling_pt"] = tts_scaling(stream, ws=(8, 9, 10, 11, 12), runs=19,
+                                                   modes=("plain_pt",))
         if "context" in wl:
             others["context_ablation"] = context_ablation(stream)
 
