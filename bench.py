@@ -632,15 +632,15 @@ def factorization_tts(stream, w=8, n_products=32, runs=32, R=32, t_max=50000, ch
 
 
 def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23,
-                modes=("plain_pt", "tapt_universal_bank", "tapt_instance_bank")):
+                modes=("plain_pt", "tapt_universal_bank", "tapt_instance_bank"), growth=2):
     """The scaling fit of Fig. 5 (S5): median TTS* at product sizes n = 2w, then
     TTS(n) = A exp(k n) by least squares on log TTS, for plain PT and both TAPT banks, in
-    sweeps and in seconds. Run lengths grow with n (5e4 * 2^(w-8) sweeps). 32 x 23 runs keep
-    every size in one wave of CTAs (760 fit at w = 10, limited by shared memory)."""
+    sweeps and in seconds. Run lengths grow with n (5e4 * growth^(w-8) sweeps). 32 x 23 runs
+    keep every size in one wave of CTAs (760 fit at w = 10, limited by shared memory)."""
     from paper_2509_23043_gb300 import tts as TT
     per = {}
     for w in ws:
-        f = 1 << (w - 8)
+        f = growth ** (w - 8)
         per[2 * w] = factorization_tts(stream, w=w, n_products=n_products, runs=runs,
                                        t_max=50_000 * f, check=1000 * f, modes=modes)
     modes = list(next(iter(per.values()))["modes"])
@@ -991,7 +991,7 @@ def main():
         if "tts_scaling_pt" in wl:
             # plain PT alone over the paper's full range of product sizes, n = 16 .. 24
             others["tts_scaling_pt"] = tts_scaling(stream, ws=(8, 9, 10, 11, 12), runs=19,
-                                                   modes=("plain_pt",))
+                                                   modes=("plain_pt",), growth=3)
         if "context" in wl:
             others["context_ablation"] = context_ablation(stream)
 
