@@ -50,6 +50,9 @@ def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--update", choices=("metropolis", "gibbs"), default="metropolis",
+                   help="local rule of the main workload (Metropolis, the benchmark's; Gibbs, "
+                        "the paper's)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--instances", type=int, default=256)
@@ -98,15 +101,20 @@ def workload(args, first: int, count: int):
 
 
 def workload_name(args) -> str:
+    rule = "" if args.update == "metropolis" else ", Gibbs moves"
     return (f"batched TAPT: {args.instances} EA +-J instances per GPU, L={args.L} "
             f"(N={args.L ** 3}), R={args.R} beta 0.1->3.0 geometric, proposals every 10 sweeps "
             f"on {args.R - 2} slots from pools of {args.pool_size}, {args.sweeps_per_step} "
-            f"cycles per step")
+            f"cycles per step{rule}")
+
+
+def update_rule(args) -> int:
+    return 1 if args.update == "gibbs" else 0
 
 
 def make_config(args, pool_size):
     import paper_2509_23043_gb300 as pt
-    return pt.Config(update=pt.METROPOLIS, sweeps_per_cycle=1, propose_every=10,
+    return pt.Config(update=update_rule(args), sweeps_per_cycle=1, propose_every=10,
                      propose_start=100, pool_size=pool_size, seed=0x7A972509,
                      threads_per_block=args.threads)
 
@@ -115,7 +123,8 @@ def build_pools(args, insts, betas, prop, ids, ctx):
     """Pools from PT runs of the method itself: a separate batch (other random streams)
     burns in, then its slot configurations are captured every `gap` sweeps."""
     import paper_2509_23043_gb300 as pt
-    cfg = pt.Config(seed=0x9001, sweeps_per_cycle=1, threads_per_block=args.threads)
+    cfg = pt.Config(seed=0x9001, sweeps_per_cycle=1, threads_per_block=args.threads,
+                    update=update_rule(args))
     gen = pt.create_instances(insts, betas, cfg, instance_ids=[1_000_000 + i for i in ids])
     pt.run_cycles(gen, args.pool_burnin)
     for e in range(args.pool_size):
@@ -210,7 +219,8 @@ def expected_plane_blocks(ctx, args, sample=4):
             J[a, 2 * d], nb[a, 2 * d] = j, b
             J[b, 2 * d + 1], nb[b, 2 * d + 1] = j, a
         unsat = (J[None, :, :] * s[:, :, None] * s[:, nb] < 0).sum(-1)   # [R][N]
-        n_und = (unsat <= 2).sum(0)                                       # walkers per word
+        # walkers per word that compare: those with dE > 0 (Metropolis), all (Gibbs)
+        n_und = (unsat <= 2).sum(0) if args.update == "metropolis" else np.full(unsat.shape[1], args.R)
         b = np.zeros_like(n_und, dtype=np.float64)
         for q in range(8):
             b += np.where(n_und > 0, 1.0 - (1.0 - 2.0 ** (-4 * q)) ** n_und, 0.0)
@@ -218,21 +228,24 @@ def expected_plane_blocks(ctx, args, sample=4):
     return float(np.mean(blocks))
 
 
-def alu_ops_per_word(e_blocks: float) -> float:
+def alu_ops_per_word(e_blocks: float, gibbs: bool = False) -> float:
     """Algorithmic integer-ALU operations of one bit-sliced word update (32 attempts):
     6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
     + 4.5 (energy count in the last colour, half the words) + per plane block: 20 (the
     three-input XORs of Philox4x32-10's 10 rounds; its 20 wide multiplies run on the FMA pipe)
-    + 4 planes x 5 (compare)."""
+    + 4 planes x 5 (compare). Gibbs: 4 for the class q and 1 for the flip instead of the class
+    masks and flip, and 4 planes x 8 per block (a six-mux tree picks each plane's threshold)."""
+    if gibbs:
+        return 6 + 8 + 4 + 1 + 4.5 + e_blocks * (20 + 32)
     return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 20)
 
 
-def smem_bytes_per_word(e_blocks: float) -> float:
+def smem_bytes_per_word(e_blocks: float, gibbs: bool = False) -> float:
     """Algorithmic shared-memory bytes of one bit-sliced word update (32 attempts): the 16 B
     table entry, the own word and six neighbour words (4 B each), the 4 planes x 3 threshold
-    words of every plane block drawn (48 B per block), and the 8 B word-and-complement store
-    (counted for every word, an upper bound)."""
-    return 16 + 4 + 24 + 8 + e_blocks * 48
+    words of every plane block drawn (48 B per block; Gibbs: 4 x 7 words, 112 B), and the 8 B
+    word-and-complement store (counted for every word, an upper bound)."""
+    return 16 + 4 + 24 + 8 + e_blocks * (112 if gibbs else 48)
 
 
 PROFILE = ROOT / "profiles" / "lattice_kernel_batched_tapt_L10_R32_B256.md"
@@ -744,7 +757,7 @@ def _ev_pair():
 
 # ------------------------------------------------------------------------------ CPU oracle
 def _oracle_worker(a):
-    L, R, index, sweeps, seed = a
+    L, R, index, sweeps, seed, update = a
     sys.path.insert(0, str(ROOT))
     import instances as I
     import oracle as O
@@ -752,7 +765,7 @@ def _oracle_worker(a):
     betas = I.geometric_betas(0.1, 3.0, R)
     P = 64
     o = O.Oracle(inst, betas, instance_id=index, prop_enabled=[1] * (R - 2) + [0, 0],
-                 propose_every=10, propose_start=0, seed=seed, pool_size=P)
+                 propose_every=10, propose_start=0, seed=seed, pool_size=P, update=update)
     for r in range(R):
         o.load_pool(r, I.random_configs(inst.n_spins, P, index=r))
     t0 = time.perf_counter()
@@ -763,7 +776,7 @@ def _oracle_worker(a):
 def cpu_oracle(args, n_inst, sweeps, pool=None):
     import multiprocessing as mp
     cores = min(os.cpu_count() or 1, n_inst)
-    jobs = [(args.L, args.R, k, sweeps, 0x7A972509) for k in range(n_inst)]
+    jobs = [(args.L, args.R, k, sweeps, 0x7A972509, update_rule(args)) for k in range(n_inst)]
     own = pool is None
     if own:
         pool = mp.get_context("spawn").Pool(cores)
@@ -942,25 +955,26 @@ def main():
 
     # ---------------- roofline of the dominant kernel (the fused cycle kernel = the whole step)
     words_per_step = B * args.L ** 3 * ((args.R + 31) // 32) * spc
-    ops = alu_ops_per_word(e_blocks) * words_per_step
+    ops = alu_ops_per_word(e_blocks, args.update == "gibbs") * words_per_step
     achieved = ops / (ms_step * 1e-3) / 1e12
     nominal = SM_COUNT * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     measured, _ = pt.calibrate_int(0)
     peak = measured / 1e12
-    tr = load_traffic(source_hash())
+    # the committed capture is of the Metropolis instantiation
+    tr = load_traffic(source_hash()) if args.update == "metropolis" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                "kernel": "lattice_kernel", "alu_ops_per_attempt": alu_ops_per_word(e_blocks) / 32,
+                "kernel": "lattice_kernel", "alu_ops_per_attempt": alu_ops_per_word(e_blocks, args.update == "gibbs") / 32,
                 "plane_blocks_per_word": e_blocks,
                 "peak_basis": "measured in this run by pt_calibrate_int (independent lop3.b32 "
                               "on every SM); nominal 152 SMs x 64 ALU lanes x 2070 MHz = "
                               f"{nominal:.2f} TOP/s"}
     smem_peak, _ = pt.calibrate_smem()
-    smem_achieved = smem_bytes_per_word(e_blocks) * words_per_step / (ms_step * 1e-3)
+    smem_achieved = smem_bytes_per_word(e_blocks, args.update == "gibbs") * words_per_step / (ms_step * 1e-3)
     roofline["smem"] = {"achieved_gbs": smem_achieved / 1e9, "peak_gbs": smem_peak / 1e9,
                         "frac": smem_achieved / smem_peak,
-                        "bytes_per_attempt": smem_bytes_per_word(e_blocks) / 32,
+                        "bytes_per_attempt": smem_bytes_per_word(e_blocks, args.update == "gibbs") / 32,
                         "peak_basis": "measured in this run by pt_calibrate_smem (conflict-free "
                                       "16-byte shared loads on every SM)"}
 
