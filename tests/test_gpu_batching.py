@@ -61,9 +61,10 @@ def test_groups_run_concurrently_and_match_oracle():
         assert np.array_equal(g[0], s) and np.array_equal(g[1], E) and np.array_equal(g[2], w)
 
 
-def test_autotune_leaves_the_run_unchanged():
+@pytest.mark.parametrize("update", [0, 1])
+def test_autotune_leaves_the_run_unchanged(update):
     data = _ragged()
-    cfg = pt.Config(seed=12, propose_every=2, pool_size=8)
+    cfg = pt.Config(seed=12, propose_every=2, pool_size=8, update=update)
     a, b = _make(cfg, data), _make(cfg, data)
     pt.run_cycles(a, 5)
     pt.run_cycles(b, 5)
@@ -75,9 +76,10 @@ def test_autotune_leaves_the_run_unchanged():
         _same(_state(a, k), _state(b, k))
 
 
-def test_graph_replay_equals_direct_launches():
+@pytest.mark.parametrize("update", [0, 1])
+def test_graph_replay_equals_direct_launches(update):
     data = _ragged()
-    cfg = pt.Config(seed=13, propose_every=2, pool_size=8)
+    cfg = pt.Config(seed=13, propose_every=2, pool_size=8, update=update)
     a, b = _make(cfg, data), _make(cfg, data)
     pt.run_cycles(a, 30)
     for _ in range(3):
@@ -86,11 +88,12 @@ def test_graph_replay_equals_direct_launches():
         _same(_state(a, k), _state(b, k))
 
 
-def test_slot_replacement_and_deactivation():
+@pytest.mark.parametrize("update", [0, 1])
+def test_slot_replacement_and_deactivation(update):
     R = 16
     betas = I.geometric_betas(0.2, 3.0, R)
     insts = [I.ea_instance(6, index=k) for k in range(3)]
-    cfg = pt.Config(seed=14)
+    cfg = pt.Config(seed=14, update=update)
     ctx = pt.create_instances(insts, [betas] * 3, cfg, instance_ids=[1, 2, 3])
     pt.run_cycles(ctx, 8)
     frozen = _state(ctx, 1)

@@ -103,14 +103,15 @@ def test_manual_api_sequence_matches_oracle():
         _assert_same(ctx, 0, o, f"step {step}")
 
 
-def test_ragged_lattice_batch_and_mix_invariance():
+@pytest.mark.parametrize("update", [0, 1])
+def test_ragged_lattice_batch_and_mix_invariance(update):
     Ls = [6, 4, 7, 2, 5, 8]
     Rs = [16, 24, 8, 3, 40, 32]
     insts = [I.ea_instance(L, index=100 + k) for k, L in enumerate(Ls)]
     betas = [I.geometric_betas(0.1, 3.0, R) for R in Rs]
     P = 8
     props = [[1] * (R - 1) + [0] for R in Rs]
-    cfg = pt.Config(seed=2025, propose_every=3, pool_size=P)
+    cfg = pt.Config(seed=2025, propose_every=3, pool_size=P, update=update)
     ids = [1000 + k for k in range(len(Ls))]
     ctx = pt.create_instances(insts, betas, cfg, prop_enabled=props, instance_ids=ids)
     pools = [_ea_pool(insts[k], Rs[k], P, 40 + k) for k in range(len(Ls))]
