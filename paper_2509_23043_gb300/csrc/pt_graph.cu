@@ -3,9 +3,10 @@
 // invertible multiplier of Supplementary S4), Gibbs (the paper's rule, Methods) or
 // Metropolis local moves, colour class by colour class (DSATUR colouring, Methods).
 //
-// Layout. Spins int8 [N][R4] (R4 = R rounded up to 4): one 32-bit word holds four walkers of
-// one site, so a thread updates four walkers of one site with one Philox call, whose four
-// output words are the four walkers' uniforms. A walker keeps its storage column; exchange
+// Layout. Spin bytes [N][R4] (R4 = R rounded up to 4), 1 where the spin is -1 and 0 where
+// it is +1: one 32-bit word holds four walkers of one site, so a thread updates four walkers
+// of one site with one Philox call, whose four output words are the four walkers' uniforms,
+// and a neighbour word is directly the four walkers' [m = -1] flags. A walker keeps its storage column; exchange
 // permutes slot <-> walker labels, thresholds are looked up by the walker's current slot.
 #include "pt_device.cuh"
 #include "pt_layout.h"
@@ -66,8 +67,9 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     return S;
 }
 
+// the spin (+1 or -1) of walker k of a stored word
 __device__ __forceinline__ int sbyte(uint32_t w, int k) {
-    return (int)(int8_t)((w >> (8 * k)) & 0xFFu);
+    return 1 - 2 * (int)((w >> (8 * k)) & 1u);
 }
 
 // One sweep: every free site of every colour class, four walkers per thread. Thread t takes
@@ -117,14 +119,12 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
-                    const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
-                    ac += (uint32_t)J * neg;
+                    ac += (uint32_t)J * sp[(pk >> 8) + quad];
                 }
                 for (int a2 = split; a2 < end; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
-                    const uint32_t neg = (sp[(pk >> 8) + quad] >> 1) & 0x01010101u;
-                    ar += (uint32_t)J * neg;
+                    ar += (uint32_t)J * sp[(pk >> 8) + quad];
                 }
                 const int2 kk = S.hk[site];
 #pragma unroll
@@ -172,7 +172,7 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                     nm = (mI <= 0 || u[k4] < S.thr[trow[k4] + mI]) ? -m : m;
                 }
                 nmv[k4] = nm;
-                out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(uint8_t)(int8_t)nm << (8 * k4));
+                out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(nm < 0) << (8 * k4));
             }
             if (out != own) sp[site * Q + quad] = out;
             if (energy_on) {
@@ -216,13 +216,13 @@ __device__ void graph_energy(const GraphInst& I, GraphSmem& S) {
                 if (I.packed) {
                     for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
                         const uint32_t pk = (uint32_t)S.adjp[a];
-                        f += (int)(int8_t)(pk & 0xFFu) * (int)S.spins[(pk >> 8) * 4 + w];
+                        f += (int)(int8_t)(pk & 0xFFu) * (1 - 2 * (int)S.spins[(pk >> 8) * 4 + w]);
                     }
                 } else {
                     for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a)
-                        f += S.adjJ[a] * (int)S.spins[S.adj[a] * I.R4 + w];
+                        f += S.adjJ[a] * (1 - 2 * (int)S.spins[S.adj[a] * I.R4 + w]);
                 }
-                acc += (int)S.spins[site * I.R4 + w] * (f + hs);
+                acc += (1 - 2 * (int)S.spins[site * I.R4 + w]) * (f + hs);
             }
             atomicAdd(&S.Eacc[w], acc);
         }
@@ -342,7 +342,7 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
         const int w = S.wos[r];
         const uint32_t* buf = S.pbuf + r * NW;
         for (int i = lane; i < N; i += 32)
-            S.spins[i * I.R4 + w] = ((buf[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
+            S.spins[i * I.R4 + w] = (int8_t)(((buf[i >> 5] >> (i & 31)) & 1u) ^ 1u);
     }
     __syncthreads();
     for (int r = tid; r < R; r += T) S.Eacc[r] = 0;
@@ -460,7 +460,7 @@ __global__ void graph_init_kernel(const GraphInst* __restrict__ insts, uint64_t 
                 s = ((r.x >> (w & 31)) & 1u) ? 1 : -1;
             }
         }
-        I.spins[idx] = s;
+        I.spins[idx] = (int8_t)(s < 0);
     }
 }
 
@@ -475,7 +475,7 @@ __global__ void graph_capture_kernel(const GraphInst* __restrict__ dst,
         uint32_t word = 0;
         for (int b = 0; b < 32; ++b) {
             const int i = k * 32 + b;
-            if (i < N && Sr.spins[i * Sr.R4 + w] > 0) word |= 1u << b;
+            if (i < N && Sr.spins[i * Sr.R4 + w] == 0) word |= 1u << b;
         }
         const_cast<uint32_t*>(D.pool)[(size_t)entry * D.pstride + (size_t)r * NW + k] = word;
     }
@@ -486,7 +486,7 @@ __global__ void graph_read_kernel(const GraphInst* __restrict__ insts, int inst,
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
          idx += gridDim.x * blockDim.x) {
         const int r = idx / I.N, i = idx - r * I.N;
-        out[idx] = I.spins[i * I.R4 + I.wos[r]];
+        out[idx] = (int8_t)(1 - 2 * I.spins[i * I.R4 + I.wos[r]]);
     }
 }
 
@@ -496,7 +496,7 @@ __global__ void graph_write_kernel(const GraphInst* __restrict__ insts, int inst
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
          idx += gridDim.x * blockDim.x) {
         const int r = idx / I.N, i = idx - r * I.N;
-        I.spins[i * I.R4 + walker[r]] = in[idx];
+        I.spins[i * I.R4 + walker[r]] = (int8_t)(in[idx] < 0);
     }
 }
 

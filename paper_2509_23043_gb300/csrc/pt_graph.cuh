@@ -6,13 +6,13 @@
 
 namespace pt {
 
-// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spins int8 [N][R4].
+// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spin bytes [N][R4].
 struct GraphInst {
     uint32_t iid;
     int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
     int32_t Eclamp;          // energy of the clamped spins: their fields and mutual bonds
     int32_t col_off[33];
-    int8_t* spins;           // [N][R4]
+    int8_t* spins;           // [N][R4]: 1 where the spin is -1, 0 where it is +1
     const int8_t* clamp;     // [N]: 0 free, +-1 clamped
     const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
     const int32_t* rowl;     // [N] a free site's row lists first its "counted" neighbours
