@@ -116,11 +116,14 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
                 // sum J m = sum J - 2 sum_{m=-1} J, h + the counted sum is hk.x - 2 byte(ac),
                 // and the local field hk.y - 2 (byte(ac) + byte(ar)).
                 uint32_t ac = 0x80808080u, ar = 0x80808080u;
+                // unrolled: the loads of several neighbours are in flight together
+#pragma unroll 4
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
                     ac += (uint32_t)J * sp[(pk >> 8) + quad];
                 }
+#pragma unroll 4
                 for (int a2 = split; a2 < end; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const int J = (int)(int8_t)(pk & 0xFFu);
