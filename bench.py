@@ -221,11 +221,20 @@ def expected_plane_blocks(ctx, args, sample=4):
         unsat = (J[None, :, :] * s[:, :, None] * s[:, nb] < 0).sum(-1)   # [R][N]
         # walkers per word that compare: those with dE > 0 (Metropolis), all (Gibbs)
         n_und = (unsat <= 2).sum(0) if args.update == "metropolis" else np.full(unsat.shape[1], args.R)
-        b = np.zeros_like(n_und, dtype=np.float64)
-        for q in range(8):
-            b += np.where(n_und > 0, 1.0 - (1.0 - 2.0 ** (-4 * q)) ** n_und, 0.0)
-        blocks.append(b.mean())
+        blocks.append(blocks_for(n_und).mean())
     return float(np.mean(blocks))
+
+
+def blocks_for(n_und) -> np.ndarray:
+    """Expected plane blocks of a word whose n_und walkers compare a uniform u with their
+    thresholds MSB first: block k (4 planes) is needed iff some walker is still undecided
+    after 4k planes, which for one walker has probability 2^-4k (u uniform); none for
+    n_und = 0."""
+    n = np.asarray(n_und, dtype=np.float64)
+    b = np.zeros_like(n)
+    for q in range(8):
+        b += np.where(n > 0, 1.0 - (1.0 - 2.0 ** (-4 * q)) ** n, 0.0)
+    return b
 
 
 def alu_ops_per_word(e_blocks: float, gibbs: bool = False) -> float:
