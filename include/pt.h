@@ -21,6 +21,8 @@
  *  - errors: every call returns a pt_status; pt_last_error() gives a message for the last
  *    failing call of the calling thread. Nothing is thrown across the ABI. A context is not
  *    thread safe.
+ *  - a context belongs to the device that was current when it was created: every call on it
+ *    returns PT_ESTATE, with a message naming both devices, when another device is current.
  */
 #ifndef PT_H
 #define PT_H
@@ -181,15 +183,18 @@ pt_status pt_exchange(pt_ctx *ctx);
  * when the schedule says so, an exchange event. */
 pt_status pt_run_cycles(pt_ctx *ctx, int32_t n_cycles);
 
-/* Energies of every replica: host int32 [sum over instances of R], instance by instance,
+/* Energies of every replica, the output {E_r} of Algorithm 1 (exact integer energies, the
+ * energy step of each cycle): host int32 [sum over instances of R], instance by instance,
  * slot order. Synchronises. */
 pt_status pt_energies(pt_ctx *ctx, int32_t *out);
 
-/* Same, into caller device memory (stream ordered, no synchronisation). */
+/* Same output {E_r} of Algorithm 1, into caller device memory (int32 [sum over instances of
+ * R], the same order; stream ordered, no synchronisation). */
 pt_status pt_energies_device(pt_ctx *ctx, int32_t *dev_out);
 
-/* State of one instance: spins int8 [R][N] and energies int32 [R] in slot order (either may
- * be NULL). Synchronises. */
+/* State of one instance, the outputs {S_r} and {E_r} of Algorithm 1: spins int8 [R][N]
+ * (+-1) and energies int32 [R] in slot order (either may be NULL). Allocates a temporary
+ * device buffer for the unpacked spins (stream ordered). Synchronises. */
 pt_status pt_read_state(pt_ctx *ctx, int32_t inst, int8_t *spins, int32_t *E);
 
 /* Same result as pt_read_state, for callers that must not allocate device memory while they
@@ -201,8 +206,10 @@ pt_status pt_read_state(pt_ctx *ctx, int32_t inst, int8_t *spins, int32_t *E);
  *    (a file-scope __device__ array; every GPU that loads the library holds it until exit),
  *    and the energies through the context's own buffer made at creation.
  *  - R * N above 262144 returns PT_ENOTSUP with a message.
- *  - The first call on a device looks up the buffer's device address (once per device, with
- *    the context's device current); make that first call before any stream capture.
+ *  - The first call on a device looks up the buffer's device address (once per device and
+ *    CUDA context, with the context's device current); make that first call before any
+ *    stream capture. After a device reset the runtime creates a new CUDA context, and the
+ *    next call looks the address up again.
  *  - All calls share the one buffer, which keeps the last call's contents. Calls are
  *    stream ordered and synchronise, so calls from one thread never overlap; calls from
  *    several host threads at once would race on the buffer and must be serialised by the

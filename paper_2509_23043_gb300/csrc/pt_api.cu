@@ -151,6 +151,7 @@ struct pt_ctx {
     int uniformN = -1;        // N when all instances share it, else -1
     int optin = 0;            // device limit on dynamic shared memory per block
     int sms = 0;              // streaming multiprocessors of the device
+    int device = -1;          // the device current at creation; every call must run with it
     std::vector<int> N, R, W, NW, R4, L;
     std::vector<size_t> slab_off;  // words, instance offset inside one pool entry
     size_t slab = 0;               // words per pool entry (all instances, all slots)
@@ -839,8 +840,22 @@ void release(pt_ctx* c) {
     delete c;
 }
 
-pt_status check_inst(const pt_ctx* c, int inst) {
+// A context's memory and kernels belong to the device that was current at creation; a call
+// made with another device current would launch on the wrong device.
+pt_status check_ctx(const pt_ctx* c) {
     if (!c) return fail(PT_EINVAL, "ctx is NULL");
+    int cur = -1;
+    const cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return fail(PT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (cur != c->device)
+        return fail(PT_ESTATE, "the context was created on device %d but device %d is current; "
+                    "call cudaSetDevice(%d) first", c->device, cur, c->device);
+    return PT_OK;
+}
+
+pt_status check_inst(const pt_ctx* c, int inst) {
+    const pt_status s = check_ctx(c);
+    if (s != PT_OK) return s;
     if (inst < 0 || inst >= c->n) return fail(PT_EINVAL, "instance %d out of range [0, %d)", inst, c->n);
     return PT_OK;
 }
@@ -915,6 +930,7 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     {
         int dev = 0;
         cudaError_t e0 = cudaGetDevice(&dev);
+        c->device = dev;
         if (e0 == cudaSuccess)
             e0 = cudaDeviceGetAttribute(&c->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e0 == cudaSuccess)
@@ -994,7 +1010,7 @@ pt_status pt_group_info(const pt_ctx* ctx, int32_t group, int32_t info[4]) {
 
 pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
     const Range range("pt_autotune");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     if (probe_cycles < 1) return fail(PT_EINVAL, "probe_cycles must be >= 1");
     drop_graph(ctx);
     uint8_t* snap = nullptr;
@@ -1068,7 +1084,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
 
 pt_status pt_run_cycles_graph(pt_ctx* ctx, int32_t n_cycles) {
     const Range range("pt_run_cycles_graph");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     if (n_cycles < 1) return fail(PT_EINVAL, "n_cycles must be >= 1");
     cudaError_t e = cudaSuccess;
     if (!ctx->gstream) {
@@ -1174,7 +1190,7 @@ pt_status pt_info(const pt_ctx* ctx, int32_t inst, int32_t info[6]) {
 
 pt_status pt_sweep(pt_ctx* ctx, int32_t n_sweeps) {
     const Range range("pt_sweep");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     if (n_sweeps < 0) return fail(PT_EINVAL, "n_sweeps must be >= 0");
     if (n_sweeps == 0) return PT_OK;
     return launch_run(ctx, kModeSweeps, n_sweeps);
@@ -1182,26 +1198,27 @@ pt_status pt_sweep(pt_ctx* ctx, int32_t n_sweeps) {
 
 pt_status pt_global_propose(pt_ctx* ctx) {
     const Range range("pt_global_propose");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     return launch_run(ctx, kModePropose, 0);
 }
 
 pt_status pt_exchange(pt_ctx* ctx) {
     const Range range("pt_exchange");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     return launch_run(ctx, kModeExchange, 0);
 }
 
 pt_status pt_run_cycles(pt_ctx* ctx, int32_t n_cycles) {
     const Range range("pt_run_cycles");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     if (n_cycles < 0) return fail(PT_EINVAL, "n_cycles must be >= 0");
     if (n_cycles == 0) return PT_OK;
     return launch_run(ctx, kModeCycles, n_cycles);
 }
 
 pt_status pt_energies_device(pt_ctx* ctx, int32_t* dev_out) {
-    if (!ctx || !dev_out) return fail(PT_EINVAL, "NULL argument");
+    if (!dev_out) return fail(PT_EINVAL, "NULL argument");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     cudaError_t e = launch_gather_energies(ctx->d_Eptr, ctx->d_wosptr, ctx->d_eoff, ctx->n, dev_out, ctx->stream);
     if (e != cudaSuccess) return fail(PT_ECUDA, "gather: %s", cudaGetErrorString(e));
     return PT_OK;
@@ -1209,7 +1226,8 @@ pt_status pt_energies_device(pt_ctx* ctx, int32_t* dev_out) {
 
 pt_status pt_energies(pt_ctx* ctx, int32_t* out) {
     const Range range("pt_energies");
-    if (!ctx || !out) return fail(PT_EINVAL, "NULL argument");
+    if (!out) return fail(PT_EINVAL, "NULL argument");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     pt_status s = pt_energies_device(ctx, ctx->d_eout);
     if (s != PT_OK) return s;
     CK(cudaMemcpyAsync(out, ctx->d_eout, (size_t)ctx->totalR * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1372,7 +1390,7 @@ pt_status pt_load_proposals(pt_ctx* ctx, int32_t inst, int32_t replica, const in
 
 pt_status pt_load_proposals_packed(pt_ctx* ctx, const uint32_t* words, int32_t first, int32_t count) {
     const Range range("pt_load_proposals_packed");
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     const int P = ctx->cfg.pool_size;
     if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
     if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
@@ -1400,7 +1418,7 @@ pt_status pt_load_proposals_inst_packed(pt_ctx* ctx, int32_t inst, const uint32_
 }
 
 pt_status pt_read_proposals_packed(pt_ctx* ctx, uint32_t* words, int32_t first, int32_t count) {
-    if (!ctx) return fail(PT_EINVAL, "ctx is NULL");
+    { const pt_status cs = check_ctx(ctx); if (cs != PT_OK) return cs; }
     const int P = ctx->cfg.pool_size;
     if (P <= 0) return fail(PT_ESTATE, "the context was created with pool_size = 0");
     if (count < 0 || first < 0 || first + count > P) return fail(PT_EINVAL, "pool range [%d, %d) exceeds pool_size %d", first, first + count, P);
@@ -1415,6 +1433,8 @@ pt_status pt_read_proposals_packed(pt_ctx* ctx, uint32_t* words, int32_t first, 
 pt_status pt_capture_proposals(pt_ctx* dst, const pt_ctx* src, int32_t entry) {
     const Range range("pt_capture_proposals");
     if (!dst || !src) return fail(PT_EINVAL, "NULL context");
+    { const pt_status cs = check_ctx(dst); if (cs != PT_OK) return cs; }
+    { const pt_status cs = check_ctx(src); if (cs != PT_OK) return cs; }
     if (dst->engine != src->engine || dst->n != src->n) return fail(PT_EINVAL, "batches differ in shape");
     for (int k = 0; k < dst->n; ++k)
         if (dst->N[k] != src->N[k] || dst->R[k] != src->R[k]) return fail(PT_EINVAL, "instance %d differs in shape", k);
@@ -1447,10 +1467,12 @@ cudaError_t launch_gather_energies(const int32_t* const* E, const int16_t* const
 // pt_read_state allocates a temporary device buffer for the unpacked spins on every call.
 // pt_read_state_noalloc serves callers that must not allocate device memory in their steady
 // state: it unpacks into a fixed file-scope device buffer instead. Host code cannot use the
-// array's name as a device address, so the address is looked up once per device with
-// cudaGetSymbolAddress and cached. The buffer is shared by every call and keeps the last
-// call's contents; the read kernel overwrites every byte that is copied out, so nothing has
-// to be cleared first.
+// array's name as a device address, so the address is looked up with cudaGetSymbolAddress
+// once per device and CUDA context, with that device current, and cached. The cache is keyed
+// on the current CUDA context as well as the device: after a device reset the runtime builds
+// a new context, which loads the library's module afresh, so the address is looked up again.
+// The buffer is shared by every call and keeps the last call's contents; the read kernel
+// overwrites every byte that is copied out, so nothing has to be cleared first.
 namespace {
 constexpr size_t kReadScratchBytes = 256 * 1024;
 constexpr int kMaxDevices = 64;
@@ -1460,22 +1482,50 @@ static __device__ __align__(256) int8_t g_read_scratch[kReadScratchBytes];
 
 namespace {
 std::mutex g_scratch_mutex;
-int8_t* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+    void* cu_ctx = nullptr;      // the CUDA context the address belongs to
+    int8_t* ptr = nullptr;
+};
+ScratchEntry g_scratch[kMaxDevices];
+
+// cuCtxGetCurrent through the runtime's driver entry-point table, so that the library does not
+// link the driver library itself (it must load where no driver is installed).
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
 
 pt_status scratch_for_current_device(int8_t** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(PT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(PT_ENOTSUP, "device %d beyond %d", dev, kMaxDevices);
+    const CtxGetCurrentFn get = ctx_get_current();
+    if (!get) return fail(PT_ECUDA, "cuCtxGetCurrent is not available");
+    void* cu_ctx = nullptr;
+    if (get(&cu_ctx) != 0) return fail(PT_ECUDA, "cuCtxGetCurrent failed");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchEntry& ent = g_scratch[dev];
+    if (!cu_ctx || !ent.ptr || ent.cu_ctx != cu_ctx) {
+        // the lookup also binds the device's primary context to this thread when none is
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_read_scratch);
         if (e != cudaSuccess || !p)
             return fail(PT_ECUDA, "cudaGetSymbolAddress(read scratch): %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = static_cast<int8_t*>(p);
+        if (!cu_ctx && (get(&cu_ctx) != 0 || !cu_ctx))
+            return fail(PT_ECUDA, "no CUDA context is current after the symbol lookup");
+        ent.ptr = static_cast<int8_t*>(p);
+        ent.cu_ctx = cu_ctx;
     }
-    *out = g_scratch_ptr[dev];
+    *out = ent.ptr;
     return PT_OK;
 }
 }  // namespace

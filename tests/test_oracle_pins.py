@@ -429,3 +429,95 @@ def test_always_accepted_contextual_proposals_keep_boltzmann():
         _assert_matches(p, hist[r] / hist[r].sum(), 40000, E)
     _, _, pa, pt_ = o.stats()
     assert np.array_equal(pa, pt_) and pt_[0] > 0
+
+
+# ------------------------------------------------------------------ proposal schedule
+def _proposal_sweeps(M, every, start, stop, n_cycles):
+    """Sweep counts s at the end of the cycles after which the oracle held a proposal event,
+    observed one cycle at a time through its event counter."""
+    inst = I.ea_instance(2, index=1)
+    o = O.Oracle(inst, [0.3, 0.9], prop_enabled=[1, 1], sweeps_per_cycle=M,
+                 propose_every=every, propose_start=start, propose_stop=stop, seed=3,
+                 pool_size=1)
+    for r in range(2):
+        o.load_pool(r, I.random_configs(inst.n_spins, 1, index=r))
+    seen, prev = [], 0
+    for _ in range(n_cycles):
+        o.run_cycles(1)
+        sweeps, _, n_prop = (int(v) for v in o.counters())
+        assert n_prop - prev in (0, 1)
+        if n_prop > prev:
+            seen.append(sweeps)
+        prev = n_prop
+    _, _, pa, pt_ = o.stats()
+    assert list(pt_) == [len(seen)] * 2           # every enabled slot attempts once per event
+    return seen
+
+
+@pytest.mark.parametrize("M,every,start,stop,n_cycles,expected", [
+    # Fig. 3: proposals from 100 MCS on, every sweep; the first event follows sweep 100
+    (1, 1, 100, 0, 104, [100, 101, 102, 103, 104]),
+    # the benchmark workloads: every 10 sweeps from sweep 100
+    (1, 10, 100, 0, 131, [100, 110, 120, 130]),
+    # Fig. S3: proposals only during the first 100 MCS; sweep 100 itself is the last
+    (1, 1, 0, 100, 103, list(range(1, 101))),
+    # three sweeps per cycle: the cycle ends at s = 3, 6, 9, ...; every 6 sweeps from 0
+    (3, 6, 0, 0, 7, [6, 12, 18]),
+    # two sweeps per cycle never end at an odd s, so start 3 with every 4 is never due
+    (2, 4, 3, 15, 10, []),
+    # a window of one sweep: start = stop = 5
+    (1, 5, 5, 5, 20, [5]),
+    # every = 0 disables proposals
+    (1, 0, 0, 0, 12, []),
+])
+def test_proposal_schedule_event_times(M, every, start, stop, n_cycles, expected):
+    # Algorithm 1 proposes every `every` sweeps once `start` sweeps are done, until `stop`
+    # (Fig. 3, Fig. S3); the expected event times are listed by hand, so an off-by-one at
+    # start or stop (s > start, s < stop) or a schedule counted in cycles rather than sweeps
+    # fails one of these cases.
+    assert _proposal_sweeps(M, every, start, stop, n_cycles) == expected
+
+
+# ------------------------------------------------------------------ initial draw
+def test_initial_replicas_are_uniform_and_independent():
+    # Algorithm 1 starts every replica from a uniformly random configuration: spins are
+    # independent fair +-1 draws. Over 64 instances x 64 walkers x 64 sites, the mean spin,
+    # the mean of every walker lane, and the pair products of neighbouring walkers, walkers
+    # one word apart, neighbouring sites and consecutive instance ids all sit within 5
+    # standard deviations of 0 (false-failure probability below 6e-7 per check). A constant,
+    # biased or shared draw fails.
+    L, R, n_inst = 4, 64, 64
+    inst = I.ea_instance(L, index=0)
+    S = np.zeros((n_inst, R, inst.n_spins), np.float64)
+    for k in range(n_inst):
+        o = O.Oracle(inst, I.geometric_betas(0.1, 3.0, R), instance_id=1000 + k, seed=0x51)
+        s, _, w = o.read()
+        assert list(w) == list(range(R))            # slot r starts with walker r
+        S[k] = s
+    n = S.size
+    assert abs(S.mean()) < 5 / np.sqrt(n)
+    lane = S.mean(axis=(0, 2))                      # per walker, over instances and sites
+    assert np.all(np.abs(lane) < 5 / np.sqrt(n_inst * inst.n_spins))
+    pairs = {
+        "walker w, w+1": S[:, :-1, :] * S[:, 1:, :],
+        "walker w, w+32": S[:, :-32, :] * S[:, 32:, :],
+        "site i, i+1": S[:, :, :-1] * S[:, :, 1:],
+        "instance k, k+1": S[:-1] * S[1:],
+    }
+    for name, prod in pairs.items():
+        assert abs(prod.mean()) < 5 / np.sqrt(prod.size), name
+
+
+def test_initial_state_respects_clamps():
+    # Algorithm 1 with clamped spins (Supplementary S4: product bits of the multiplier):
+    # clamped sites start at their clamp value in every replica, free sites are drawn.
+    mult = I.multiplier(4)
+    inst = mult.instance(143)
+    o = O.Oracle(inst, I.geometric_betas(0.05, 5.0, 40), seed=9)
+    s, E, _ = o.read()
+    cl = inst.clamp
+    assert np.all(s[:, cl != 0] == cl[cl != 0])
+    free = s[:, cl == 0].astype(np.float64)
+    assert abs(free.mean()) < 5 / np.sqrt(free.size)
+    for r in range(s.shape[0]):
+        assert E[r] == O.energy(inst, s[r])

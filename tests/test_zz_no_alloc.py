@@ -50,3 +50,52 @@ def test_noalloc_rejects_sizes_beyond_its_buffer():
     assert "exceeds" in str(e.value)
     s, E = pt.read_state(ctx, 0)                      # the allocating path still serves it
     assert s.shape == (48, 5832)
+
+
+def _cudart():
+    import ctypes
+    # the runtime libpt.so is linked against; dlopen by soname returns the loaded copy
+    for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("CUDA runtime library not found")
+
+
+def _pool_high_water(rt, pool, reset=False):
+    import ctypes
+    kUsedMemHigh = 0x8                                  # cudaMemPoolAttrUsedMemHigh
+    v = ctypes.c_uint64(0)
+    if reset:
+        assert rt.cudaMemPoolSetAttribute(pool, kUsedMemHigh, ctypes.byref(v)) == 0
+        return 0
+    assert rt.cudaMemPoolGetAttribute(pool, kUsedMemHigh, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_noalloc_read_allocates_nothing():
+    # The point of the entry point: no device allocation. pt_read_state takes its temporary
+    # buffer from the device's default memory pool (cudaMallocAsync), so the pool's
+    # high-water mark above the context's own memory rises during that call; during
+    # pt_read_state_noalloc it must not rise at all.
+    import ctypes
+    rt = _cudart()
+    inst = I.ea_instance(8, index=3)
+    ctx = pt.create_instances([inst], [I.geometric_betas(0.1, 3.0, 32)], pt.Config(seed=4),
+                              instance_ids=[11])
+    pt.run_cycles(ctx, 5)
+    pt.read_state_noalloc(ctx, 0)                       # the first call does its look-up
+    dev = ctypes.c_int(0)
+    assert rt.cudaGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p(0)
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev.value) == 0
+    cur = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, 0x7, ctypes.byref(cur)) == 0   # UsedMemCurrent
+    base = cur.value                                    # the context's own memory
+    _pool_high_water(rt, pool, reset=True)              # high-water := current use
+    for _ in range(3):
+        pt.read_state_noalloc(ctx, 0)
+    assert _pool_high_water(rt, pool) == base
+    pt.read_state(ctx, 0)
+    assert _pool_high_water(rt, pool) > base            # the allocating path does allocate
