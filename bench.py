@@ -76,7 +76,9 @@ def parse():
     p.add_argument("--factor-pool-gap", type=int, default=25)
     p.add_argument("--serve-requests", type=int, default=66)
     p.add_argument("--serve-L", default="6,7,8,9,10,11,12,13,14,15,16")
-    p.add_argument("--serve-budget", type=int, default=100_000)
+    p.add_argument("--serve-budget", type=int, default=1_000_000)
+    p.add_argument("--serve-ref-runs", type=int, default=4)
+    p.add_argument("--serve-ref-sweeps", type=int, default=1_000_000)
     p.add_argument("--serve-gap-ms", type=float, default=4.0)
     p.add_argument("--serve-load", type=float, default=0.7,
                    help="offered load as a fraction of the served TAPT capacity (the completion "
@@ -202,27 +204,36 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ roofline model
-def expected_plane_blocks(ctx, args, sample=4):
-    """Algorithmic random-number work of the bit-plane compare: a word of 32 walkers needs
-    plane blocks (4 planes = one Philox call) until each walker with dE > 0 is decided, each
-    plane deciding a walker with probability 1/2. Averaged over the words of a state sample."""
-    import instances as I
+def plane_blocks_of(ctx, k, inst, update):
+    """Expected plane blocks per word of instance k of a lattice context in its current state:
+    a word (site, walker block) of 32 walkers needs plane blocks (4 planes = one Philox call)
+    until each of its comparing walkers is decided, each plane deciding a walker with
+    probability 1/2. The comparing walkers are those with dE > 0 (Metropolis) or all (Gibbs)."""
     import paper_2509_23043_gb300 as pt
-    blocks = []
-    for k in range(min(sample, ctx.n)):
-        s, _ = pt.read_state(ctx, k)              # [R][N] slot order
-        inst = I.ea_instance(args.L, index=k)
-        J = np.zeros((args.L ** 3, 6), np.int64)
-        nb = np.zeros((args.L ** 3, 6), np.int64)
-        for e, (a, b, j) in enumerate(zip(inst.edge_i, inst.edge_j, inst.edge_J)):
-            d = e % 3
-            J[a, 2 * d], nb[a, 2 * d] = j, b
-            J[b, 2 * d + 1], nb[b, 2 * d + 1] = j, a
-        unsat = (J[None, :, :] * s[:, :, None] * s[:, nb] < 0).sum(-1)   # [R][N]
-        # walkers per word that compare: those with dE > 0 (Metropolis), all (Gibbs)
-        n_und = (unsat <= 2).sum(0) if args.update == "metropolis" else np.full(unsat.shape[1], args.R)
-        blocks.append(blocks_for(n_und).mean())
-    return float(np.mean(blocks))
+    s, _ = pt.read_state(ctx, k)                 # [R][N] slot order
+    walker = pt.read_walkers(ctx, k)             # walker of each slot
+    L = int(inst.lattice_L)
+    J = np.zeros((L ** 3, 6), np.int64)
+    nb = np.zeros((L ** 3, 6), np.int64)
+    for e, (a, b, j) in enumerate(zip(inst.edge_i, inst.edge_j, inst.edge_J)):
+        d = e % 3
+        J[a, 2 * d], nb[a, 2 * d] = j, b
+        J[b, 2 * d + 1], nb[b, 2 * d + 1] = j, a
+    unsat = (J[None, :, :] * s[:, :, None] * s[:, nb] < 0).sum(-1)   # [R][N]
+    cmp = (unsat <= 2) if update == "metropolis" else np.ones_like(unsat, dtype=bool)
+    per_word = []
+    for wb in range((s.shape[0] + 31) // 32):
+        in_block = (walker // 32) == wb
+        per_word.append(blocks_for(cmp[in_block].sum(0)))
+    return float(np.mean(np.concatenate(per_word)))
+
+
+def expected_plane_blocks(ctx, args, sample=4):
+    """Algorithmic random-number work of the bit-plane compare, averaged over the words of a
+    state sample of the benchmark workload's first instances."""
+    import instances as I
+    return float(np.mean([plane_blocks_of(ctx, k, I.ea_instance(args.L, index=k), args.update)
+                          for k in range(min(sample, ctx.n))]))
 
 
 def blocks_for(n_und) -> np.ndarray:
@@ -242,11 +253,14 @@ def alu_ops_per_word(e_blocks: float, gibbs: bool = False) -> float:
     6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
     + 4.5 (energy count in the last colour, half the words) + per plane block: 20 (the
     three-input XORs of Philox4x32-10's 10 rounds; its 20 wide multiplies run on the FMA pipe)
-    + 4 planes x 5 (compare). Gibbs: 4 for the class q and 1 for the flip instead of the class
-    masks and flip, and 4 planes x 8 per block (a six-mux tree picks each plane's threshold)."""
+    + 17 for comparing its four planes: 4 x 2 to pick each plane's class threshold, then the
+    chained compare (4 steps for the decided-below bit, 4 for the still-undecided mask, 1 to
+    merge). Gibbs: 4 for the class q and 1 for the flip instead of the class masks and flip,
+    and 4 x 6 per block to pick each plane's threshold by a six-mux tree, with the same 9 for
+    the chain."""
     if gibbs:
-        return 6 + 8 + 4 + 1 + 4.5 + e_blocks * (20 + 32)
-    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 20)
+        return 6 + 8 + 4 + 1 + 4.5 + e_blocks * (20 + 24 + 9)
+    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 8 + 9)
 
 
 def smem_bytes_per_word(e_blocks: float, gibbs: bool = False) -> float:
@@ -296,8 +310,12 @@ def served_stream(args, stream):
     """Poisson arrivals of EA +-J requests (L uniform over --serve-L), each run by TAPT in the
     continuous-batching server to within 0.1% of its reference lowest energy or the sweep
     budget; the same requests run one instance per launch with plain PT (no proposals).
-    Pools (PT runs of this library) and reference energies (long PT runs) are made first and
-    are not part of any time-to-solution."""
+    Reference energies: the best of --serve-ref-runs independent PT runs of
+    --serve-ref-sweeps sweeps, each best configuration's energy recomputed on the host. Pools
+    (PT runs of this library) and reference energies are made first and are not part of any
+    time-to-solution; the pools' sweeps per request are reported beside it, and a second
+    served run uses pools that cost about as many sweeps as plain PT's median time to the
+    target. A third served run has a device-memory budget small enough to bind."""
     import instances as I
     import paper_2509_23043_gb300 as pt
     from paper_2509_23043_gb300 import serve as S
@@ -313,14 +331,18 @@ def served_stream(args, stream):
     t0 = time.perf_counter()
     pools = S.make_pools(insts, [betas] * n, ids, P, burnin=args.serve_pool_burnin,
                          gap=args.serve_pool_gap, stream=stream)
-    eref = S.reference_energies(insts, [betas] * n, ids, sweeps=200_000, chunk=2000, stream=stream)
+    pool_sweeps = args.serve_pool_burnin + args.serve_pool_gap * P
+    eref = S.reference_energies(insts, [betas] * n, ids, sweeps=args.serve_ref_sweeps, chunk=2000,
+                                runs=args.serve_ref_runs, verify=True, stream=stream)
     prep_s = time.perf_counter() - t0
     unit = np.cumsum(g.exponential(1.0, size=n))        # arrival pattern, scaled by the mean gap
     unit -= unit[0]
-    mk = lambda k, a: S.Request(ids[k], insts[k], betas, prop, pools[k], eref[k], arrival=float(a))
+    mk = lambda k, a, pl=None: S.Request(ids[k], insts[k], betas, prop, pools[k] if pl is None else pl[k],
+                                         eref[k], arrival=float(a))
     cfg = pt.Config(seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
     slots = {L: 4 for L in Ls}
-    budget = int(args.serve_hbm_frac * sum(4 * S.footprint_bytes(L, R, P) for L in Ls))
+    footprint_all = sum(4 * S.footprint_bytes(L, R, P) for L in Ls)
+    budget = int(args.serve_hbm_frac * footprint_all)
     gap_s, capacity = args.serve_gap_ms * 1e-3, None
     if args.serve_load > 0:
         # capacity: the completion rate of the TAPT server with every request submitted at
@@ -343,16 +365,44 @@ def served_stream(args, stream):
                              budget_sweeps=args.serve_budget)
     alone = [S.run_alone(mk(k, 0.0), cfg_pt, budget_sweeps=args.serve_budget, tick_cycles=100,
                          stream=stream) for k in range(n)]
+    alone_sum = S.summarize(alone)
+    # pools that cost about as many sweeps per request as plain PT needs to reach the target
+    # (its median over the solved requests): half burn-in, half captures
+    med = max(2 * P, int(alone_sum.get("solved_p50_sweeps", 2 * P)))
+    cheap_burn, cheap_gap = med // 2, max(1, (med // 2) // P)
+    cheap = S.make_pools(insts, [betas] * n, ids, P, burnin=cheap_burn, gap=cheap_gap, seed=0x9002,
+                         stream=stream)
+    srv_c = S.TaptServer(slots, betas, prop, cfg, hbm_budget=budget, tick_cycles=100, stream=stream)
+    served_c = srv_c.serve([mk(k, arrivals[k], cheap) for k in range(n)], budget_sweeps=args.serve_budget)
+    # a device-memory budget that binds: every request submitted at once, a budget of the
+    # footprint of four of the largest slots, so requests wait for memory with slots free
+    tight = 4 * S.footprint_bytes(max(Ls), R, P)
+    srv_m = S.TaptServer(slots, betas, prop, cfg, hbm_budget=tight, tick_cycles=100, stream=stream)
+    served_m = srv_m.serve([mk(k, 0.0) for k in range(n)], budget_sweeps=args.serve_budget)
+    s_tapt, s_cheap = S.summarize(served), S.summarize(served_c)
+    for sm, ps in ((s_tapt, pool_sweeps), (s_cheap, cheap_burn + cheap_gap * P)):
+        sm["pool_sweeps_per_request"] = ps
+        if "p50_sweeps" in sm:
+            sm["amortised_p50_sweeps"] = sm["p50_sweeps"] + ps
+    s_mem = S.summarize(served_m)
+    s_mem.update({"hbm_budget_bytes": tight, "peak_bytes_admitted": srv_m.peak_used,
+                  "peak_requests_in_flight": srv_m.peak_active})
     return {"workload": f"{n} requests, L uniform in {{{args.serve_L}}}, R={R}, Poisson arrivals "
                         f"(mean gap {gap_s * 1e3:.2f} ms), target E_ref + 0.1%|E_ref| "
-                        f"(E_ref: best of a 2e5-sweep PT run), budget {args.serve_budget} sweeps, "
-                        f"pools P={P} from PT runs of {args.serve_pool_burnin} + "
-                        f"{args.serve_pool_gap * P} sweeps (untimed, {prep_s:.1f} s)",
-            "served_tapt": S.summarize(served),
+                        f"(E_ref: best of {args.serve_ref_runs} PT runs of {args.serve_ref_sweeps} "
+                        f"sweeps, energies recomputed on the host), budget {args.serve_budget} sweeps "
+                        f"(a request stopped by it counts as censored at the budget), pools P={P} from "
+                        f"PT runs of {args.serve_pool_burnin} + {args.serve_pool_gap * P} sweeps "
+                        f"(untimed; {prep_s:.1f} s with the reference runs)",
+            "served_tapt": s_tapt,
+            "served_tapt_pools_at_pt_cost": s_cheap,
+            "served_tapt_memory_bound": s_mem,
             "served_plain_pt": S.summarize(served_pt),
-            "plain_pt_one_instance_per_launch": S.summarize(alone),
+            "plain_pt_one_instance_per_launch": alone_sum,
             "slots_per_L": 4, "hbm_budget_bytes": budget, "peak_bytes_admitted": srv.peak_used,
             "peak_requests_in_flight": srv.peak_active,
+            "admission": "device memory modelled: every slot is allocated when the server is "
+                         "built; the budget caps the summed footprint of the admitted requests",
             "capacity_per_s": capacity, "offered_per_s": 1.0 / gap_s,
             "load": (1.0 / gap_s) / capacity if capacity else None}
 
@@ -427,10 +477,16 @@ def engine_comparison(stream, B=256, L=10, R=32, P=64, cycles=100, reps=5):
             "engines": out}
 
 
-def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
+def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5, cpu_pool=None, e2e_steps=5,
+                 flush=None):
     """4096 EA instances, L uniform in {6..16} (even), R uniform in 24..48 on 0.1 -> 3.0,
     proposals every 10 sweeps from pools of 512 (PT runs of this library, untimed), block
-    sizes autotuned per size class, cycles replayed from a CUDA graph."""
+    sizes autotuned per size class, cycles replayed from a CUDA graph: the largest configuration
+    on one GPU. Beside its throughput: its ALU roofline (the algorithmic count of each size
+    class, its plane blocks per word from a state sample of two members), an end-to-end rate
+    through the public API (each step's pool window copied in from pinned host memory, the
+    energies read back), and the oracle on the host cores on a sample of the same mix."""
+    import torch
     import instances as I
     import paper_2509_23043_gb300 as pt
     g = np.random.default_rng(3)
@@ -456,12 +512,92 @@ def ragged_batch(stream, n=4096, P=512, cycles=100, reps=5):
     ms = _time_ms(lambda: pt.run_cycles_graph(ctx, cycles), reps, stream)
     att = int(sum(int(R) * int(L) ** 3 for L, R in zip(Ls, Rs))) * cycles
     groups = pt.group_info(ctx)
+    value = att / (ms * 1e6)
+    # roofline: the algorithmic ALU count of every word, by size class (L, walker blocks),
+    # counted for the occupied lanes only (R/32 words per site), so padding lanes of a
+    # partly filled walker block add no work
+    cls = {}
+    for k, (L, R) in enumerate(zip(Ls, Rs)):
+        cls.setdefault((int(L), (int(R) + 31) // 32), []).append(k)
+    ops = words = 0.0
+    eb_w = 0.0
+    for key, members in cls.items():
+        eb = float(np.mean([plane_blocks_of(ctx, k, insts[k], "metropolis") for k in members[:2]]))
+        w = sum(int(Ls[k]) ** 3 * int(Rs[k]) / 32.0 for k in members) * cycles
+        ops += alu_ops_per_word(eb) * w
+        words += w
+        eb_w += eb * w
+    peak = pt.calibrate_int(0)[0] / 1e12
+    achieved = ops / (ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "lattice_kernel",
+                "alu_ops_per_attempt": ops / att,
+                "plane_blocks_per_word": eb_w / words,
+                "peak_basis": "measured in this run by pt_calibrate_int (independent lop3.b32 on "
+                              "every SM)",
+                "note": "algorithmic count per size class over the occupied lanes, plane blocks "
+                        "from two members each"}
+    # end to end: each step's window of pool entries copied in (pinned host memory), energies out
+    e2e = None
+    if e2e_steps > 0:
+        per_step = cycles // cfg.propose_every
+        c, _ = pt.read_counters(ctx, 0)
+        first = int(c[2]) % P
+        need = min(P, per_step * e2e_steps)
+        nws = [(int(L) ** 3 + 31) // 32 for L in Ls]
+        slab = int(sum(int(R) * nw for R, nw in zip(Rs, nws)))
+        host = torch.empty((need, slab), dtype=torch.int32, pin_memory=True)
+        for j in range(need):                     # the entries the timed steps will use
+            pt.read_proposals_packed(ctx, host[j].data_ptr(), (first + j) % P, 1)
+        eout = torch.empty(sum(int(R) for R in Rs), dtype=torch.int32, device="cuda")
+        ehost = torch.empty_like(eout, device="cpu").pin_memory()
+        t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t_a.record(stream)
+        for st in range(e2e_steps):
+            if flush is not None:
+                flush.zero_()
+            for j in range(per_step):
+                jj = (st * per_step + j) % need
+                pt.load_proposals_packed(ctx, host[jj].data_ptr(), (first + st * per_step + j) % P, 1)
+            pt.run_cycles_graph(ctx, cycles)
+            pt.energies_device(ctx, eout.data_ptr())
+            ehost.copy_(eout, non_blocking=True)
+        t_b.record(stream)
+        torch.cuda.synchronize()
+        ms2 = t_a.elapsed_time(t_b) / e2e_steps
+        e2e = {"value": att / (ms2 * 1e6), "unit": "attempts/ns",
+               "h2d_bytes_per_step": per_step * slab * 4, "d2h_bytes_per_step": int(eout.numel()) * 4,
+               "steps": e2e_steps,
+               "note": "each step's pool window copied in from pinned host memory on the "
+                       "launch stream before its cycles; L2 flushed between steps inside the "
+                       "timed region"}
+        del host
     pt.destroy(ctx)
+    cpu = None
+    if cpu_pool is not None:
+        cpu = ragged_cpu_oracle(Ls[:16], Rs[:16], 40, cpu_pool)
     return {"workload": f"{n} EA instances, L in {{6..16}}, R in 24..48, proposals every 10 "
                         f"from pools of {P} (2000 + {4 * P} PT sweeps per instance, untimed), "
                         f"autotuned, {cycles} graph-replayed cycles per step",
-            "ms_per_step": ms, "attempts_per_ns": att / (ms * 1e6), "size_classes": len(groups),
-            "threads_per_class": sorted({gr["threads"] for gr in groups}), "prep_s": round(prep, 1)}
+            "value": value, "unit": "attempts/ns", "ms_per_step": ms, "attempts_per_ns": value,
+            "size_classes": len(groups), "gpu_launches_per_step": len(groups),
+            "threads_per_class": sorted({gr["threads"] for gr in groups}), "prep_s": round(prep, 1),
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+
+
+def ragged_cpu_oracle(Ls, Rs, sweeps, pool):
+    """The oracle on the host cores on a sample of the ragged mix: the given (L, R) pairs, one
+    process per instance, random pools of 64 per slot."""
+    cores = min(os.cpu_count() or 1, len(Ls))
+    jobs = [(int(L), int(R), k, sweeps, 0x7A972509, 0) for k, (L, R) in enumerate(zip(Ls, Rs))]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    return {"value": sum(r[0] for r in res) / (wall * 1e9), "unit": "attempts/ns", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{len(Ls)} instances of the ragged mix (L, R as the batch's first 16) x "
+                      f"{sweeps} cycles each, one process per instance on {cores} host cores"}
 
 
 def _mark_factored(ctx, mult, products, solved_at, sweeps):
@@ -988,6 +1124,7 @@ def main():
                                       "16-byte shared loads on every SM)"}
 
     serving = None
+    ragged = None
     if not args.no_serve and rank == 0:
         serving = served_stream(args, stream.cuda_stream)
     others = None
@@ -999,7 +1136,7 @@ def main():
         if "engines" in wl:
             others["engine_comparison"] = engine_comparison(stream)
         if "ragged" in wl:
-            others["ragged_batch"] = ragged_batch(stream)
+            ragged = ragged_batch(stream, cpu_pool=cpu_pool, flush=flush)
         if "factor" in wl:
             others["factorization"] = factorization(stream, args.factor_sweeps,
                                                     P=args.factor_pool_size,
@@ -1038,8 +1175,9 @@ def main():
                        "pool": f"PT runs of this library: {args.pool_burnin} burn-in sweeps, "
                                f"then one capture every {args.pool_gap} sweeps (untimed)",
                        "threads_per_block": pt.info(ctx)["threads"]},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-            "other_workloads": others,
+            "other_workloads": others, "serving": serving,
+            "ragged_batch_4096": ragged,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk.summary(),
         }), flush=True)
     if dist:

@@ -180,23 +180,34 @@ __device__ __forceinline__ void compare4(const uint4& r, const uint4* tw, uint32
 }
 
 // Gibbs: compare four bit planes of u with the thresholds of the walkers' classes q (3 bits
-// q0 q1 q2, 0..6), picked from the seven threshold planes by a mux tree.
+// q0 q1 q2, 0..6), each plane's threshold picked from the seven threshold planes by a mux
+// tree. The four planes are compared as one chain: a walker undecided before the block is
+// decided "u < T" within it iff g0 | e0 (g1 | e1 (g2 | e2 g3)), with g = ~r & t (u's bit is 0
+// where T's is 1) and e = ~(r ^ t) (the bits agree), and stays undecided iff all four e are 1.
+// Each step of the chain is one three-input function of (r, t, h), so a block costs 4 + 4 + 1
+// logic operations against 3 per plane compared one at a time. Planes are taken from the least
+// significant up.
+__device__ __forceinline__ uint32_t gibbs_pick(const uint4* tw, int j, uint32_t q0, uint32_t q1,
+                                               uint32_t q2) {
+    const uint4 ta = tw[2 * j], tb = tw[2 * j + 1];
+    const uint32_t a01 = mux(q0, ta.y, ta.x), a23 = mux(q0, ta.w, ta.z);
+    const uint32_t a45 = mux(q0, tb.y, tb.x);
+    const uint32_t a03 = mux(q1, a23, a01), a46 = mux(q1, tb.z, a45);
+    return mux(q2, a46, a03);
+}
+__device__ __forceinline__ void chain_step(uint32_t r, uint32_t t, uint32_t& h, uint32_t& e) {
+    h = (~r & t) | (~(r ^ t) & h);
+    e = e & ~(r ^ t);
+}
 __device__ __forceinline__ void compare4g(const uint4& r, const uint4* tw, uint32_t q0,
                                           uint32_t q1, uint32_t q2, uint32_t& und, uint32_t& lt) {
-    // one plane at a time (not unrolled), so that only one plane's seven threshold words are
-    // live: the planes of u rotate through w0
-    uint32_t w0 = r.x, w1 = r.y, w2 = r.z, w3 = r.w;
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-        const uint4 ta = tw[2 * j], tb = tw[2 * j + 1];
-        const uint32_t a01 = mux(q0, ta.y, ta.x), a23 = mux(q0, ta.w, ta.z);
-        const uint32_t a45 = mux(q0, tb.y, tb.x);
-        const uint32_t a03 = mux(q1, a23, a01), a46 = mux(q1, tb.z, a45);
-        const uint32_t tk = mux(q2, a46, a03);
-        lt |= und & ~w0 & tk;
-        und &= ~(w0 ^ tk);
-        w0 = w1; w1 = w2; w2 = w3;
-    }
+    const uint32_t t3 = gibbs_pick(tw, 3, q0, q1, q2);
+    uint32_t h = ~r.w & t3, e = und & ~(r.w ^ t3);
+    chain_step(r.z, gibbs_pick(tw, 2, q0, q1, q2), h, e);
+    chain_step(r.y, gibbs_pick(tw, 1, q0, q1, q2), h, e);
+    chain_step(r.x, gibbs_pick(tw, 0, q0, q1, q2), h, e);
+    lt |= und & h;
+    und = e;
 }
 
 __device__ __forceinline__ uint32_t nb_word(const uint8_t* base, uint32_t off) {
@@ -254,6 +265,22 @@ __device__ __forceinline__ void count_lower_bonds(uint32_t (&cnt)[KB], uint32_t 
     vc_add3(cnt, n0, n1, n2);
 }
 
+// Plane blocks 3..7 of one word, drawn while some walker is undecided (rarely needed), then
+// the new word: Gibbs, the comparison bits themselves; Metropolis, the flips.
+template <bool GIBBS>
+__device__ __forceinline__ uint32_t finish_word(const RunArgs& a, const LP& P, const uint4* tw,
+                                                uint32_t site, uint32_t sweep_idx, uint32_t ctr2,
+                                                uint32_t s, uint32_t b0, uint32_t c1, uint32_t c2,
+                                                uint32_t always, uint32_t vmask, uint32_t und,
+                                                uint32_t lt) {
+    for (uint32_t qb = 3; qb < 8 && und; ++qb) {
+        const uint4 r = philox_rk(make_uint4(site, sweep_idx, ctr2 | (qb << 16), P.iid), a);
+        if constexpr (GIBBS) compare4g(r, tw + 8 * qb, b0, c1, c2, und, lt);
+        else compare4(r, tw + 4 * qb, b0, c1, und, lt);
+    }
+    return GIBBS ? (s ^ lt) & vmask : (always | lt) & vmask;
+}
+
 // One sweep: colour classes in order, all (site, walker-block) words of a class in parallel.
 template <int MAXW, int KB, bool GIBBS>
 __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const RunArgs& a,
@@ -281,43 +308,36 @@ __device__ __forceinline__ void lattice_sweep(const LP& P, LatSmem& S, const Run
                 uint32_t m[6], b0, b1, b2;
                 bond_count(sp, it, s, m, b0, b1, b2);
                 uint32_t flip = 0;
-                if (GIBBS && flip_on) {
-                    // class q: c where s = +1, 6 - c where s = -1 (q0 = c0 either way)
-                    const uint32_t q1 = mux(s, b1, ~(b1 ^ b0));
-                    const uint32_t q2 = mux(s, b2, ~(b2 | (b1 & b0)));
-                    uint32_t und = vmask, lt = 0;
-                    const uint32_t site = it.x & 0xFFFFu;
-                    const uint4 r0 = philox_rk(make_uint4(site, sweep_idx, ctr2, P.iid), a);
-                    const uint4 r1 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (1u << 16), P.iid), a);
-                    const uint4 r2 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (2u << 16), P.iid), a);
-                    compare4g(r0, tw, b0, q1, q2, und, lt);
-                    compare4g(r1, tw + 8, b0, q1, q2, und, lt);
-                    compare4g(r2, tw + 16, b0, q1, q2, und, lt);
-                    for (uint32_t qb = 3; qb < 8 && und; ++qb) {
-                        const uint4 r = philox_rk(make_uint4(site, sweep_idx, ctr2 | (qb << 16), P.iid), a);
-                        compare4g(r, tw + 8 * qb, b0, q1, q2, und, lt);
+                if (flip_on) {
+                    uint32_t c1, c2 = 0, always = 0, und;
+                    if (GIBBS) {
+                        // class q: c where s = +1, 6 - c where s = -1 (q0 = c0 either way)
+                        c1 = mux(s, b1, ~(b1 ^ b0));
+                        c2 = mux(s, b2, ~(b2 | (b1 & b0)));
+                        und = vmask;
+                    } else {
+                        always = b2 | (b1 & b0);              // count >= 3: dE <= 0
+                        c1 = b1;
+                        und = ~always & vmask;
                     }
-                    flip = (s ^ lt) & vmask;                  // new spin +1 iff u < T
-                    if (flip) own_p[k] = make_uint2(s ^ flip, ~(s ^ flip));
-                } else if (flip_on) {
-                    const uint32_t always = b2 | (b1 & b0);   // count >= 3: dE <= 0
-                    uint32_t und = ~always & vmask, lt = 0;
+                    uint32_t lt = 0;
+                    const uint32_t site = it.x & 0xFFFFu;
                     if (und) {
                         // plane blocks 0-2 are almost always needed by some walker of the
-                        // warp: draw them together (three independent Philox chains)
-                        const uint32_t site = it.x & 0xFFFFu;
-                        const uint4 r0 = philox_rk(make_uint4(site, sweep_idx, ctr2, P.iid), a);
-                        const uint4 r1 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (1u << 16), P.iid), a);
-                        const uint4 r2 = philox_rk(make_uint4(site, sweep_idx, ctr2 | (2u << 16), P.iid), a);
-                        compare4(r0, tw, b0, b1, und, lt);
-                        compare4(r1, tw + 4, b0, b1, und, lt);
-                        compare4(r2, tw + 8, b0, b1, und, lt);
-                        for (uint32_t qb = 3; qb < 8 && und; ++qb) {
-                            const uint4 r = philox_rk(make_uint4(site, sweep_idx, ctr2 | (qb << 16), P.iid), a);
-                            compare4(r, tw + 4 * qb, b0, b1, und, lt);
+                        // warp: drawn together (three independent Philox chains)
+                        uint4 r[3];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            r[b] = philox_rk(make_uint4(site, sweep_idx, ctr2 | ((uint32_t)b << 16), P.iid), a);
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            if constexpr (GIBBS) compare4g(r[b], tw + 8 * b, b0, c1, c2, und, lt);
+                            else compare4(r[b], tw + 4 * b, b0, c1, und, lt);
                         }
                     }
-                    flip = (always | lt) & vmask;
+                    flip = und ? finish_word<GIBBS>(a, P, tw, site, sweep_idx, ctr2, s, b0, c1, c2, always,
+                                                    vmask, und, lt)
+                               : (GIBBS ? (s ^ lt) & vmask : (always | lt) & vmask);
                     if (flip) own_p[k] = make_uint2(s ^ flip, ~(s ^ flip));
                 }
                 if (acc) count_lower_bonds(cnt[wb], it.x >> 16, m, s ^ flip, b0, b1, b2, flip);

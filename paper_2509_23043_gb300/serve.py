@@ -16,6 +16,10 @@ on admission, so its trajectory (and its sweeps-to-target) is the same alone or 
 
 Time-to-solution follows the paper's definition of success within a run (Eq. for TTS and
 Supplementary S5): here one run per request, success = reaching E_ref + 0.1% |E_ref|.
+
+Admission by device memory is modelled: every slot's state and pool are allocated when the
+server is built, and the budget caps the summed footprint (footprint_bytes) of the requests
+admitted at once, so a request can wait for memory while a slot of its class is free.
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ import numpy as np
 
 from . import (Config, create_instances, destroy, energies, load_proposals_inst_packed,
                read_counters, read_proposals_packed, run_cycles, run_cycles_graph,
-               capture_proposals, set_active, set_instance, read_state)
+               capture_proposals, set_active, set_instance, read_state, read_walkers)
 
 
 @dataclass
@@ -45,6 +49,8 @@ class Request:
     sweeps: int = -1            # sweeps from admission to the target (-1: not reached)
     best: int = 0
     status: str = "pending"     # then "solved", "budget", "rejected", "cancelled", "timeout"
+    mem_waits: int = 0          # admission attempts refused by the device-memory budget
+    final: tuple | None = None  # (spins [R][N], energies [R], walker of each slot) at retirement
 
     @property
     def L(self) -> int:
@@ -119,20 +125,43 @@ def make_pools(insts, betas, ids, P: int, burnin: int, gap: int, seed: int = 0x9
     return out
 
 
+def host_energy(inst, spins) -> int:
+    """E = -sum_edges J m_i m_j - sum_i h_i m_i of one +-1 configuration, recomputed on the
+    host with numpy from the instance's edge list (Supplementary S4): an independent check of
+    the energies the device reports."""
+    m = np.asarray(spins, dtype=np.int64)
+    E = -int(np.sum(np.asarray(inst.edge_J, np.int64) * m[inst.edge_i] * m[inst.edge_j]))
+    if inst.h is not None:
+        E -= int(np.dot(np.asarray(inst.h, np.int64), m))
+    return E
+
+
 def reference_energies(insts, betas, ids, sweeps: int, chunk: int = 1000, seed: int = 0x5EF,
-                       stream=None) -> list[int]:
-    """Lowest energy met by a long PT run of every instance (checked every `chunk` sweeps)."""
-    ctx = create_instances(insts, betas, Config(seed=seed), instance_ids=[2_000_000 + i for i in ids],
-                           stream=stream)
+                       runs: int = 1, stream=None, verify: bool = False) -> list[int]:
+    """Lowest energy met by `runs` independent long PT runs of every instance (own random
+    streams each, checked every `chunk` sweeps). With verify, the configuration that reached
+    each best energy is read back and its energy recomputed on the host (host_energy), and a
+    mismatch raises."""
     best = [10 ** 9] * len(insts)
-    done = 0
-    while done < sweeps:
-        n = min(chunk, sweeps - done)
-        run_cycles(ctx, n)
-        done += n
-        for k, e in enumerate(energies(ctx)):
-            best[k] = min(best[k], int(e.min()))
-    destroy(ctx)
+    for run in range(runs):
+        ctx = create_instances(insts, betas, Config(seed=seed + 0x1000 * run),
+                               instance_ids=[2_000_000 + 100_000 * run + i for i in ids], stream=stream)
+        done = 0
+        while done < sweeps:
+            n = min(chunk, sweeps - done)
+            run_cycles(ctx, n)
+            done += n
+            for k, e in enumerate(energies(ctx)):
+                lo = int(e.min())
+                if lo < best[k]:
+                    best[k] = lo
+                    if verify:
+                        spins, E = read_state(ctx, k)
+                        r = int(np.argmin(E))
+                        if host_energy(insts[k], spins[r]) != int(E[r]):
+                            raise RuntimeError(f"instance {k}: reported energy {int(E[r])} is not "
+                                               f"the configuration's ({host_energy(insts[k], spins[r])})")
+        destroy(ctx)
     return best
 
 
@@ -141,11 +170,12 @@ class TaptServer:
 
     def __init__(self, slots_per_L: dict[int, int], betas: np.ndarray, prop: list,
                  config: Config, hbm_budget: int | None = None, tick_cycles: int = 100,
-                 use_graph: bool = True, stream=None):
+                 use_graph: bool = True, keep_final: bool = False, stream=None):
         self.R = len(betas)
         self.cfg = config
         self.tick_cycles = tick_cycles
         self.use_graph = use_graph
+        self.keep_final = keep_final
         self.slot_L, placeholders, ids = [], [], []
         for L, n in sorted(slots_per_L.items()):
             for j in range(n):
@@ -182,6 +212,7 @@ class TaptServer:
         if not self.free.get(req.L):
             return False
         if self.budget is not None and self.used + self._fp(req) > self.budget:
+            req.mem_waits += 1
             return False
         k = self.free[req.L].pop()
         set_instance(self.ctx, k, req.instance, req.betas, req.prop, instance_id=req.rid)
@@ -198,6 +229,9 @@ class TaptServer:
     def _retire(self, k: int, req: Request, now: float, status: str) -> None:
         req.status = status
         req.finished = now
+        if self.keep_final:
+            spins, E = read_state(self.ctx, k)
+            req.final = (spins, E, read_walkers(self.ctx, k))
         set_active(self.ctx, k, False)
         self.free[req.L].append(k)
         self.used -= self._fp(req)
@@ -221,6 +255,7 @@ class TaptServer:
                 req.sweeps = sw
                 self._retire(k, req, now, "solved")
             elif sw >= budget_sweeps:
+                req.budget_sweeps = sw
                 self._retire(k, req, now, "budget")
             elif req.rid in self.cancelled:
                 self._retire(k, req, now, "cancelled")
@@ -266,7 +301,7 @@ class TaptServer:
 
 
 def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int = 100,
-              stream=None) -> Request:
+              keep_final: bool = False, stream=None) -> Request:
     """One request in its own context and launch (plain PT when config.propose_every == 0)."""
     ctx = create_instances([req.instance], [req.betas], config, prop_enabled=[req.prop],
                            instance_ids=[req.rid], stream=stream)
@@ -281,34 +316,54 @@ def run_alone(req: Request, config: Config, budget_sweeps: int, tick_cycles: int
         req.best = int(energies(ctx)[0].min())
         if req.best <= req.target or sw >= budget_sweeps:
             req.sweeps = sw if req.best <= req.target else -1
+            req.budget_sweeps = sw
             req.status = "solved" if req.best <= req.target else "budget"
             break
     req.finished = time.perf_counter() - t0
     req.arrival = 0.0
+    if keep_final:
+        spins, E = read_state(ctx, 0)
+        req.final = (spins, E, read_walkers(ctx, 0))
     destroy(ctx)
     return req
 
 
 def summarize(reqs: list[Request]) -> dict:
-    """p50/p99 time-to-solution (s and sweeps) over the solved requests, the mean wait
-    (arrival to admission) and service (admission to retirement) over all requests, and the
-    fitted TTS exponent k of log TTS = a + k L, and of log TTS = a + k N with N = L^3 (least
-    squares over the per-L medians, as in TTS(n) = A exp(k n) of Supplementary S5)."""
+    """Time to solution over the requests that ran (solved, or stopped by the sweep budget):
+    p50/p99 in seconds and sweeps over all of them, a budget-limited request counted as
+    censored at its budget (so a p99 that falls on a censored request is a lower bound, flagged
+    by p99_censored); the same over the solved requests alone; the mean wait (arrival to
+    admission), the mean service (admission to retirement) and the requests that waited for
+    device memory; and the fitted TTS exponent k of log TTS = a + k L, and of
+    log TTS = a + k N with N = L^3 (least squares over the per-L medians of the solved
+    requests, as in TTS(n) = A exp(k n) of Supplementary S5)."""
     solved = [r for r in reqs if r.sweeps >= 0]
+    ran = [r for r in reqs if r.status in ("solved", "budget")]
     out = {"requests": len(reqs), "solved": len(solved)}
     for st in ("budget", "rejected", "cancelled", "timeout"):
         n = sum(r.status == st for r in reqs)
         if n:
             out[st] = n
+    out["censored"] = sum(r.status == "budget" for r in reqs)
+    out["waited_for_memory"] = sum(r.mem_waits > 0 for r in reqs)
     if reqs:
         out["mean_wait_s"] = float(np.nanmean([r.admitted - r.arrival for r in reqs]))
         out["mean_service_s"] = float(np.nanmean([r.finished - r.admitted for r in reqs]))
+    if ran:
+        t = np.array([r.tts for r in ran])
+        sw = np.array([r.sweeps if r.sweeps >= 0 else _ran_sweeps(r) for r in ran], dtype=np.float64)
+        cens = np.array([r.status == "budget" for r in ran])
+        out.update({"p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+                    "p50_sweeps": float(np.percentile(sw, 50)),
+                    "p99_sweeps": float(np.percentile(sw, 99)),
+                    "p99_censored": bool(cens.any() and np.percentile(t, 99) >= t[cens].min())})
     if not solved:
         return out
     t = np.array([r.tts for r in solved])
     s = np.array([r.sweeps for r in solved], dtype=np.float64)
-    out.update({"p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
-                "p50_sweeps": float(np.percentile(s, 50)), "p99_sweeps": float(np.percentile(s, 99))})
+    out.update({"solved_p50_s": float(np.percentile(t, 50)), "solved_p99_s": float(np.percentile(t, 99)),
+                "solved_p50_sweeps": float(np.percentile(s, 50)),
+                "solved_p99_sweeps": float(np.percentile(s, 99))})
     Ls = sorted({r.L for r in solved})
     if len(Ls) >= 2:
         med = [float(np.median([r.tts for r in solved if r.L == L])) for L in Ls]
@@ -319,3 +374,8 @@ def summarize(reqs: list[Request]) -> dict:
         out["k_seconds_per_N"] = float(np.polyfit(Ns, np.log(med), 1)[0])
         out["k_sweeps_per_N"] = float(np.polyfit(Ns, np.log(medsw), 1)[0])
     return out
+
+
+def _ran_sweeps(r: Request) -> float:
+    """Sweeps a budget-limited request ran: its budget (recorded when it retired)."""
+    return float(getattr(r, "budget_sweeps", float("nan")))

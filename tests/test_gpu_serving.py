@@ -28,15 +28,22 @@ def _requests():
 
 
 def test_served_results_equal_alone_results():
+    # Requests that arrive while others run share launches with them, yet each one's whole
+    # trajectory is its own: the sweeps to the target, the best energy, and the final spins,
+    # energies and walker labels of every slot are the same in the mix as alone.
     reqs, betas, prop, P = _requests()
     cfg = pt.Config(seed=77, propose_every=10, pool_size=P)
-    srv = S.TaptServer({6: 2, 7: 1, 8: 1}, betas, prop, cfg, tick_cycles=20)
+    srv = S.TaptServer({6: 2, 7: 1, 8: 1}, betas, prop, cfg, tick_cycles=20, keep_final=True)
     done = srv.serve(reqs, budget_sweeps=4000)
     assert len(done) == len(reqs)
     for r in done:
         alone = S.Request(r.rid, r.instance, r.betas, r.prop, r.pool, r.e_ref)
-        S.run_alone(alone, cfg, budget_sweeps=4000, tick_cycles=20)
+        S.run_alone(alone, cfg, budget_sweeps=4000, tick_cycles=20, keep_final=True)
         assert alone.sweeps == r.sweeps and alone.best == r.best
+        for mixed, own in zip(r.final, alone.final):     # spins, energies, walker labels
+            assert np.array_equal(mixed, own)
+        for k in range(len(betas)):                      # the energies are the states'
+            assert r.final[1][k] == O.energy(r.instance, r.final[0][k])
     summary = S.summarize(done)
     assert summary["requests"] == len(reqs)
 

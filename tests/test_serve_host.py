@@ -97,3 +97,26 @@ def test_budget_and_deadline_and_cancellation(fake):
     assert done[8].status == "solved" and done[8].sweeps == 10
     s = S.summarize(list(done.values()))
     assert s["solved"] == 1 and s["budget"] == 1 and s["timeout"] == 1 and s["cancelled"] == 1
+
+
+def test_summary_counts_budget_limited_requests_as_censored():
+    # time to solution over every request that ran: one stopped by the sweep budget counts at
+    # the budget (censored), so the p99 that falls on it is flagged as a lower bound
+    from paper_2509_23043_gb300 import serve as S
+
+    class _I:
+        lattice_L = 6
+    reqs = []
+    for k in range(10):
+        r = S.Request(k, _I(), None, None, None, -100, arrival=0.0)
+        r.admitted, r.finished = 0.0, 1.0 + k
+        if k < 8:
+            r.status, r.sweeps = "solved", 100 * (k + 1)
+        else:
+            r.status, r.sweeps, r.budget_sweeps = "budget", -1, 5000
+        reqs.append(r)
+    out = S.summarize(reqs)
+    assert out["solved"] == 8 and out["censored"] == 2
+    assert out["p99_censored"] and out["p99_sweeps"] == 5000.0
+    assert out["solved_p50_sweeps"] == 450.0
+    assert out["p50_sweeps"] == float(np.percentile([100 * (k + 1) for k in range(8)] + [5000, 5000], 50))
