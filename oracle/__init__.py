@@ -56,6 +56,8 @@ def lib():
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_load_pool.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]
         L.or_load_pool.restype = C.c_int
+        L.or_load_law.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.or_load_law.restype = C.c_int
         for f in ("or_sweeps", "or_run_cycles"):
             getattr(L, f).argtypes = [C.c_void_p, C.c_int32]
         for f in ("or_propose", "or_exchange"):
@@ -145,6 +147,12 @@ class Oracle:
         s = np.ascontiguousarray(spins, dtype=np.int8)
         if lib().or_load_pool(self.h, r, _ptr(s), s.shape[0], first):
             raise ValueError("bad pool load")
+
+    def load_law(self, r: int, p_plus):
+        """Proposal law of slot r (proposal_rule 2): P(spin i = +1) per site."""
+        p = np.ascontiguousarray(p_plus, dtype=np.float64)
+        if lib().or_load_law(self.h, r, _ptr(p)):
+            raise ValueError("bad proposal law")
 
     def sweeps(self, n: int):
         lib().or_sweeps(self.h, n)

@@ -114,8 +114,9 @@ struct or_inst {
     double *beta;
     uint8_t *prop;
     int32_t update, M, every, start, stop;
-    int32_t rule;             /* proposal rule: 0 Delta-E-only, 1 always accept */
+    int32_t rule;             /* proposal rule: 0 Delta-E-only, 1 always accept, 2 independent MH */
     int32_t source;           /* proposal source: 0 pool, 1 contextual */
+    int64_t *lw;              /* [R][N] log-odds of each slot's proposal law, units of 2^-32 */
     int32_t ctx_log2, ctx_sweeps;
     uint64_t seed;
     int32_t P;
@@ -205,6 +206,7 @@ void or_destroy(or_inst *o) {
     free(o->prop); free(o->adj_off); free(o->adj_j); free(o->adj_J); free(o->colour);
     free(o->spins); free(o->E); free(o->walker); free(o->pool); free(o->cursor);
     free(o->swap_acc); free(o->swap_att); free(o->prop_acc); free(o->prop_att);
+    free(o->lw);
     free(o);
 }
 
@@ -226,7 +228,8 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t context_log2, int32_t context_sweeps) {
     if (n_spins <= 0 || n_edges < 0 || n_replicas <= 0 || sweeps_per_cycle <= 0) return NULL;
     if (update != 0 && update != 1) return NULL;
-    if (proposal_rule != 0 && proposal_rule != 1) return NULL;
+    if (proposal_rule < 0 || proposal_rule > 2) return NULL;
+    if (proposal_rule == 2 && proposal_source != 0) return NULL;
     if (proposal_source != 0 && proposal_source != 1) return NULL;
     if (proposal_source == 1 && (context_log2 < 1 || context_log2 > 3 || context_sweeps < 1))
         return NULL;
@@ -243,6 +246,7 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
     o->rule = proposal_rule;
     o->source = proposal_source; o->ctx_log2 = context_log2; o->ctx_sweeps = context_sweeps;
     o->P = pool_size > 0 ? pool_size : 0;
+    o->lw = (int64_t *)xcalloc((size_t)n_replicas * n_spins, 8);
     o->ei = (int32_t *)xcalloc((size_t)n_edges, 4);
     o->ej = (int32_t *)xcalloc((size_t)n_edges, 4);
     o->eJ = (int32_t *)xcalloc((size_t)n_edges, 4);
@@ -331,6 +335,30 @@ int or_load_pool(or_inst *o, int32_t r, const int8_t *spins, int32_t count, int3
     if (r < 0 || r >= o->R || first < 0 || count < 0 || first + count > o->P) return 1;
     memcpy(o->pool + ((size_t)r * o->P + first) * o->N, spins, (size_t)count * o->N);
     return 0;
+}
+
+/* The proposal law of slot r's pool (proposal rule 2): the pool entries are independent
+ * draws from the product-Bernoulli law q(x) = prod_i p_i^[x_i=+1] (1-p_i)^[x_i=-1]. Its
+ * per-site log-odds log(p_i/(1-p_i)) are stored rounded to multiples of 2^-32, so that
+ * log q(x) - log q(x') = sum_i ([x_i=+1] - [x'_i=+1]) log-odds_i is an exact integer sum.
+ * Clamped sites carry no weight: the current state and the candidate agree on them. */
+int or_load_law(or_inst *o, int32_t r, const double *p_plus) {
+    if (r < 0 || r >= o->R) return 1;
+    for (int32_t i = 0; i < o->N; ++i)
+        if (!(p_plus[i] > 0.0 && p_plus[i] < 1.0)) return 1;
+    for (int32_t i = 0; i < o->N; ++i) {
+        double lo = log(p_plus[i]) - log1p(-p_plus[i]);
+        o->lw[(size_t)r * o->N + i] = o->clamp[i] != 0 ? 0 : llround(ldexp(lo, 32));
+    }
+    return 0;
+}
+
+/* sum of slot r's log-odds over the +1 spins of a configuration (units of 2^-32) */
+static int64_t law_weight(const or_inst *o, int32_t r, const int8_t *x) {
+    int64_t L = 0;
+    for (int32_t i = 0; i < o->N; ++i)
+        if (x[i] > 0) L += o->lw[(size_t)r * o->N + i];
+    return L;
 }
 
 /* the 32-bit uniform of one local move */
@@ -461,7 +489,13 @@ void or_propose(or_inst *o) {
         const int8_t *src = o->pool + ((size_t)r * o->P + o->cursor[r]) * o->N;
         for (int32_t i = 0; i < o->N; ++i) cand[i] = o->clamp[i] != 0 ? o->clamp[i] : src[i];
         int32_t ET = energy_of(o, cand);
+        /* Eq. 2: x = beta_r (E_r - E^T); rule 2 adds the Hastings correction of the
+         * independent proposal, log q(x_r) - log q(x^T) (Supplementary S2, the MH rule) */
         double x = o->beta[r] * (double)(o->E[r] - ET);
+        if (o->rule == 2) {
+            int64_t dl = law_weight(o, r, o->spins + (size_t)r * o->N) - law_weight(o, r, cand);
+            x = x + ldexp((double)dl, -32);
+        }
         uint32_t u = philox_word(o->seed, (uint32_t)r, (uint32_t)o->n_prop, 4u << 24, o->id, 0);
         o->prop_att[r]++;
         if (o->rule == 1 || or_accept(x, u)) {

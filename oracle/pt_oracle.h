@@ -50,7 +50,9 @@ int64_t or_energy(int32_t n, int32_t n_edges, const int32_t *ei, const int32_t *
  * propose_every = 0 disables proposals in or_run_cycles; propose_stop <= 0 means never stop.
  * proposal_rule: 0 = the Delta-E-only rule of Eq. 2; 1 = always accept (the independent
  * Metropolis-Hastings move for proposals drawn exactly from the slot's Boltzmann law, whose
- * correction cancels the Boltzmann ratio; Supplementary S2).
+ * correction cancels the Boltzmann ratio; Supplementary S2); 2 = the independent
+ * Metropolis-Hastings move min[1, pi(x')q(x) / (pi(x)q(x'))] for pools drawn from a
+ * product-Bernoulli law q given per slot by or_load_law (pool proposals only).
  * proposal_source: 0 = the pool; 1 = contextual proposals (Supplementary S3): a copy of the
  * slot's configuration with every spin kept (clamped) with probability 2^-context_log2
  * (1..3) and the others refilled by context_sweeps (>= 1) Metropolis sweeps at the slot's
@@ -65,6 +67,10 @@ or_inst *or_create(uint32_t instance_id, int32_t n_spins, int32_t lattice_L,
                    int32_t pool_size, int32_t proposal_rule, int32_t proposal_source,
                    int32_t context_log2, int32_t context_sweeps);
 void or_destroy(or_inst *o);
+
+/* Proposal law of slot r for proposal_rule 2: p_plus[i] = P(spin i = +1), in (0, 1). Its
+ * log-odds are kept rounded to multiples of 2^-32. Returns nonzero on invalid input. */
+int or_load_law(or_inst *o, int32_t r, const double *p_plus);
 
 /* Store `count` configurations (+-1) for replica slot r at pool positions first.. */
 int or_load_pool(or_inst *o, int32_t r, const int8_t *spins, int32_t count, int32_t first);

@@ -71,6 +71,29 @@ def _w_delta_e(E, beta, always=False):
     return W
 
 
+def _q_product(p):
+    """Product-Bernoulli proposal law over the 32 states: P(spin i = +1) = p[i]."""
+    S = _states()
+    return np.prod(np.where(S > 0, p[None, :], 1.0 - p[None, :]), axis=1)
+
+
+def _w_independent(E, beta, q, rule):
+    """An independent proposal x' ~ q, accepted by the DeltaE-only rule (Eq. 2) or by the
+    Metropolis-Hastings rule min[1, pi(x') q(x) / (pi(x) q(x'))] (Supplementary S2):
+    W(x' <- x) = q(x') A(x -> x'), rejected mass on the diagonal."""
+    ratio = np.exp(-beta * (E[:, None] - E[None, :]))       # pi(x') / pi(x), rows x'
+    if rule == "mh":
+        ratio = ratio * (q[None, :] / q[:, None])           # q(x) / q(x')
+    W = q[:, None] * np.minimum(1.0, ratio)
+    np.fill_diagonal(W, 0.0)
+    W += np.diag(1.0 - W.sum(0))
+    return W
+
+
+# proposal laws of the two proposal-receiving replicas, far from their Boltzmann laws
+LAWS = [np.array([0.3, 0.65, 0.5, 0.8, 0.25]), np.array([0.6, 0.35, 0.7, 0.2, 0.55])]
+
+
 def _w_swap(E, b_lo, b_hi):
     """W_swap on a pair of replica axes: 1024 x 1024, state index (s_lo, s_hi)."""
     W = np.zeros((32, 32, 32, 32))   # [s_lo', s_hi', s_lo, s_hi]
@@ -101,7 +124,11 @@ def _stationary(mode):
     S = _states()
     E = _energy(inst, S)
     Ws = [_w_sweep(inst, S, b) for b in BETAS]
-    Wp = [_w_delta_e(E, b, always=(mode == "always")) for b in BETAS[:2]]
+    if mode in ("mh", "delta_e_law"):
+        Wp = [_w_independent(E, b, _q_product(LAWS[r]), "mh" if mode == "mh" else "delta_e")
+              for r, b in enumerate(BETAS[:2])]
+    else:
+        Wp = [_w_delta_e(E, b, always=(mode == "always")) for b in BETAS[:2]]
     Wx = [_w_swap(E, BETAS[0], BETAS[1]), _w_swap(E, BETAS[1], BETAS[2])]
     p = np.full((32, 32, 32), 1.0 / 32 ** 3)
     marg = []
@@ -210,3 +237,52 @@ def test_swap_matrix_is_stochastic_and_keeps_the_product_law():
         p = np.outer(_pi(E, b_lo), _pi(E, b_hi))
         q = np.tensordot(W, p, axes=([2, 3], [0, 1]))
         assert np.allclose(q, p, atol=1e-14)
+
+
+def test_exact_chain_mh_with_a_product_law_keeps_boltzmann():
+    # Supplementary S2: an independent proposal from any law q, accepted by
+    # min[1, pi(x') q(x) / (pi(x) q(x'))], satisfies detailed balance, so PT with such moves
+    # keeps every replica at its Boltzmann law; the DeltaE-only rule with the same q does not.
+    m, pis, _ = _stationary("mh")
+    for r in range(3):
+        assert _kl(m[r], pis[r]) < 1e-10
+    m2, _, _ = _stationary("delta_e_law")
+    assert _kl(m2[0], pis[0]) > 1e-3 and _kl(m2[1], pis[1]) > 1e-3
+
+
+@pytest.mark.slow
+def test_mh_rule_oracle_keeps_boltzmann_with_a_product_law():
+    """proposal_rule = 2 on the oracle: pools drawn from the product laws above, the laws
+    loaded beside them; the slot marginals are the Boltzmann laws (the exact chain's), while
+    the DeltaE-only rule on the same pools is biased."""
+    inst = _fa()
+    S = _states()
+    E = _energy(inst, S)
+    pis = [_pi(E, b) for b in BETAS]
+    m_de, _, _ = _stationary("delta_e_law")
+    P, n = 40000, 60000
+    weights = 1 << np.arange(5)
+    hist = {}
+    for rule in (2, 0):
+        g = np.random.default_rng(2511)
+        o = O.Oracle(inst, BETAS, prop_enabled=[1, 1, 0], update=1, propose_every=1,
+                     seed=4444, pool_size=P, proposal_rule=rule)
+        for r in range(2):
+            draw = np.where(g.random((P, 5)) < LAWS[r][None, :], 1, -1).astype(np.int8)
+            o.load_pool(r, draw)
+            o.load_law(r, LAWS[r])
+        o.run_cycles(500)
+        h = np.zeros((3, 32))
+        for _ in range(n):
+            o.run_cycles(1)
+            s, _, _ = o.read()
+            for r in range(3):
+                h[r, int(((s[r] > 0) * weights).sum())] += 1
+        hist[rule] = h / n
+    for r in range(3):
+        noise = 0.5 * np.sum(np.sqrt(2 * pis[r] * (1 - pis[r]) / (np.pi * n / 3)))
+        assert 0.5 * np.abs(hist[2][r] - pis[r]).sum() < 4 * noise + 0.003, r
+    for r in range(2):
+        noise = 0.5 * np.sum(np.sqrt(2 * m_de[r] * (1 - m_de[r]) / (np.pi * n / 3)))
+        assert 0.5 * np.abs(hist[0][r] - m_de[r]).sum() < 4 * noise + 0.003, r
+        assert 0.5 * np.abs(hist[0][r] - pis[r]).sum() > 4 * noise + 0.003, r
