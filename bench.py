@@ -613,7 +613,36 @@ def _mark_factored(ctx, mult, products, solved_at, sweeps):
             solved_at[k] = sweeps
 
 
-def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=25, chunk=1000):
+def graph_alu_ops_per_attempt(mean_degree: float) -> float:
+    """Algorithmic integer-ALU operations of one attempt of the graph engine (int8 spins, four
+    walkers of one site per thread, Gibbs or Metropolis): 5 for the three-input XORs of one
+    Philox4x32-10 call shared by the four walkers (20 / 4; its wide multiplies run on the FMA
+    pipe), mean_degree / 4 to decode the packed row entries (one per neighbour, shared by the
+    four walkers; the byte-sum multiply-add runs on the FMA pipe), and 6 per walker: extract
+    its byte of the field sum, form the field (Gibbs) or the energy change (Metropolis), index
+    the threshold row, compare, insert the new spin byte, and its energy term."""
+    return 5.0 + mean_degree / 4.0 + 6.0
+
+
+def _oracle_worker_factor(a):
+    C, R, index, sweeps, seed = a
+    sys.path.insert(0, str(ROOT))
+    import instances as I
+    import oracle as O
+    inst = I.multiplier(8).instance(C)
+    betas = I.geometric_betas(0.05, 5.0, R)
+    P = 64
+    o = O.Oracle(inst, betas, instance_id=index, prop_enabled=[1] * 23 + [0] * (R - 23), update=1,
+                 propose_every=10, propose_start=0, seed=seed, pool_size=P)
+    for r in range(R):
+        o.load_pool(r, I.random_configs(inst.n_spins, P, index=r))
+    t0 = time.perf_counter()
+    o.run_cycles(sweeps)
+    return R * int((inst.clamp == 0).sum()) * sweeps, time.perf_counter() - t0
+
+
+def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=25, chunk=1000,
+                  cpu_pool=None):
     """The 8x8-bit multiplier (N = 200) with the product bits clamped to n products of two
     primes <= 255; R = 32 on 0.05 -> 5.0, proposals every 10 sweeps on the 23 hottest slots,
     Gibbs (the paper's rule) and Metropolis. Per-product pools: P configurations of each
@@ -649,6 +678,12 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
     stream.synchronize()
     prep = time.perf_counter() - t0
     att = n * R * int((insts[0].clamp == 0).sum())
+    free = insts[0].clamp == 0
+    deg = np.zeros(insts[0].n_spins)
+    np.add.at(deg, insts[0].edge_i, 1)
+    np.add.at(deg, insts[0].edge_j, 1)
+    ops_att = graph_alu_ops_per_attempt(float(deg[free].mean()))
+    peak = pt.calibrate_int(0)[0] / 1e12
     out = {"workload": f"{n} clamped 8x8-bit multipliers (N={mult.n_spins}), R={R} on "
                        f"0.05->5.0, proposals every 10 sweeps on 23 slots from per-product pools "
                        f"of {P} (a clamped PT run of {burn} + {P}x{gap} sweeps, untimed, "
@@ -669,10 +704,26 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
             _mark_factored(ctx, mult, [C for C, _, _ in prods], solved_at, done)
             checkpoints[done] = int((solved_at >= 0).sum())
         pt.destroy(ctx)
-        out[name] = {"attempts_per_ns": att * done / (t_gpu * 1e6),
+        rate = att * done / (t_gpu * 1e6)
+        out[name] = {"attempts_per_ns": rate,
                      "solved_of": n, "solved_after_sweeps": checkpoints,
                      "median_sweeps_to_solution": (float(np.median(solved_at[solved_at >= 0]))
-                                                   if (solved_at >= 0).any() else None)}
+                                                   if (solved_at >= 0).any() else None),
+                     "roofline": {"bound": "alu", "achieved": rate * ops_att * 1e9 / 1e12,
+                                  "peak": peak, "unit": "TOP/s",
+                                  "frac": rate * ops_att * 1e9 / 1e12 / peak, "traffic": None,
+                                  "kernel": "graph_kernel", "alu_ops_per_attempt": ops_att,
+                                  "peak_basis": "measured in this run by pt_calibrate_int"}}
+    if cpu_pool is not None:
+        jobs = [(int(C), R, k, 20, 0x7A972509) for k, (C, _, _) in enumerate(prods[:16])]
+        t0 = time.perf_counter()
+        res = cpu_pool.map(_oracle_worker_factor, jobs)
+        wall = time.perf_counter() - t0
+        cores = min(os.cpu_count() or 1, len(jobs))
+        out["cpu_baseline"] = {"value": sum(r[0] for r in res) / (wall * 1e9), "unit": "attempts/ns",
+                               "cores": cores, "kind": "oracle",
+                               "sample": f"{len(jobs)} of the clamped multipliers x 20 Gibbs cycles each "
+                                         f"(random pools of 64), one process per instance on {cores} host cores"}
     return out
 
 
@@ -1141,7 +1192,7 @@ def main():
             others["factorization"] = factorization(stream, args.factor_sweeps,
                                                     P=args.factor_pool_size,
                                                     burn=args.factor_pool_burnin,
-                                                    gap=args.factor_pool_gap)
+                                                    gap=args.factor_pool_gap, cpu_pool=cpu_pool)
         if "ladder" in wl:
             others["ladder"] = ladder_workload(stream)
         if "tts" in wl:

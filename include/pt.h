@@ -101,7 +101,12 @@ typedef struct {
  *                    1 = always accept, which is the independent Metropolis-Hastings move
  *                    when the pool entries are exact draws from the slot's Boltzmann law (the
  *                    proposal-probability correction then cancels the Boltzmann ratio;
- *                    Supplementary S2). Other values: PT_EINVAL.
+ *                    Supplementary S2); 2 = the independent Metropolis-Hastings move
+ *                    min[1, pi(x') q(x) / (pi(x) q(x'))] (Supplementary S2, the MH rule) for
+ *                    pools drawn from a product-Bernoulli law q given per slot by
+ *                    pt_load_proposal_law (pool proposals only; a slot whose law was never
+ *                    loaded has the uniform law, for which the rule is the Delta-E-only one).
+ *                    Other values: PT_EINVAL.
  *  proposal_source   0 = proposals from the pools (pt_load_proposals...); 1 = contextual
  *                    proposals (Supplementary S3), lattice engine with Metropolis sweeps
  *                    (update 0) only: at each event every
@@ -141,6 +146,17 @@ pt_status pt_create_instances(pt_ctx **out, const pt_instance_desc *descs, int32
  * These are the pre-generated proposals S^T_r at beta_r of Algorithm 1. */
 pt_status pt_load_proposals(pt_ctx *ctx, int32_t inst, int32_t replica, const int8_t *spins,
                             int32_t count, int32_t first);
+
+/* Proposal law of the pool of instance `inst`, slot `replica`, for proposal_rule 2 (no
+ * counterpart call in the paper; the law is the q of Supplementary S2's MH rule): the pool
+ * entries are independent draws from q(x) = prod_i p_i^[x_i=+1] (1 - p_i)^[x_i=-1], with
+ * p_plus[i] = p_i, N doubles in (0, 1) (host, copied during the call). The library keeps the
+ * log-odds log(p_i / (1 - p_i)) rounded to multiples of 2^-32, so log q(x) - log q(x') is an
+ * exact integer sum; clamped sites carry no weight. At a proposal event the acceptance
+ * exponent is x = beta_r (E_r - E^T) + log q(x_r) - log q(x^T), in FP64. PT_ESTATE unless
+ * the context was created with proposal_rule 2; PT_EINVAL for a value outside (0, 1).
+ * Synchronises. */
+pt_status pt_load_proposal_law(pt_ctx *ctx, int32_t inst, int32_t replica, const double *p_plus);
 
 /* Bulk load of bit-packed pool entries for every instance and slot: host words laid out
  * [count][instance][slot][ceil(N_instance/32)] uint32 (bit i%32 of word i/32 set iff spin i

@@ -21,7 +21,7 @@ PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT, PT_ESTATE, PT_ENOTSUP = rang
 _STATUS = {0: "PT_OK", 1: "PT_EINVAL", 2: "PT_ENOMEM", 3: "PT_ECUDA", 4: "PT_ETIMEOUT",
            5: "PT_ESTATE", 6: "PT_ENOTSUP"}
 METROPOLIS, GIBBS = 0, 1
-DELTA_E_ONLY, ALWAYS_ACCEPT = 0, 1     # proposal rules
+DELTA_E_ONLY, ALWAYS_ACCEPT, INDEPENDENT_MH = 0, 1, 2     # proposal rules
 POOL, CONTEXT = 0, 1                   # proposal sources
 
 
@@ -53,7 +53,7 @@ EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed
            "pt_run_cycles", "pt_energies", "pt_energies_device", "pt_read_state",
            "pt_read_state_noalloc",
            "pt_read_walkers", "pt_write_state", "pt_read_counters", "pt_read_stats", "pt_info",
-           "pt_group_info", "pt_autotune", "pt_run_cycles_graph", "pt_set_instance",
+           "pt_group_info", "pt_autotune", "pt_load_proposal_law", "pt_run_cycles_graph", "pt_set_instance",
            "pt_set_active", "pt_set_stream", "pt_calibrate_int", "pt_calibrate_smem", "pt_destroy",
            "pt_last_error"]
 
@@ -76,6 +76,7 @@ def lib():
         "pt_load_proposals_packed": [vp, vp, i32, i32],
         "pt_read_proposals_packed": [vp, vp, i32, i32],
         "pt_load_proposals_inst_packed": [vp, i32, vp, i32, i32],
+        "pt_load_proposal_law": [vp, i32, i32, vp],
         "pt_capture_proposals": [vp, vp, i32],
         "pt_sweep": [vp, i32], "pt_global_propose": [vp], "pt_exchange": [vp],
         "pt_run_cycles": [vp, i32], "pt_energies": [vp, vp], "pt_energies_device": [vp, vp],
@@ -215,6 +216,16 @@ def create_instances(instances: Sequence, betas: Sequence, config: Config,
 def load_proposals(ctx: Context, inst: int, replica: int, spins, first: int = 0):
     s = _arr(spins, np.int8)
     _check(lib().pt_load_proposals(ctx.handle, inst, replica, _ptr(s), s.shape[0], first))
+
+
+def load_proposal_law(ctx: Context, inst: int, replica: int, p_plus):
+    """pt_load_proposal_law: P(spin i = +1) per site of the law slot `replica`'s pool entries are
+    drawn from (proposal_rule 2, the independent Metropolis-Hastings move)."""
+    _inst(ctx, inst)
+    p = np.ascontiguousarray(p_plus, dtype=np.float64)
+    if p.shape != (ctx.N[inst],):
+        raise ValueError(f"p_plus must have shape ({ctx.N[inst]},)")
+    _check(lib().pt_load_proposal_law(ctx.handle, inst, replica, _ptr(p)))
 
 
 def load_proposals_packed(ctx: Context, words, first: int, count: int):

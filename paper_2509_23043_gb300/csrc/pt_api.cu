@@ -138,7 +138,7 @@ struct Group {
 };
 
 // Arena offsets of one lattice instance's arrays (for slot replacement).
-struct LatOff { size_t spins, itab, pos, E, sow, wos, thr, beta, prop, cur, eb, ctr, st, active; };
+struct LatOff { size_t spins, itab, pos, E, sow, wos, thr, beta, prop, cur, eb, ctr, st, active, lw; };
 
 struct pt_ctx {
     int engine = 0;           // 0 lattice, 1 graph
@@ -492,6 +492,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         o.ctr = A.zeros(sizeof(Counters));
         o.st = A.zeros((size_t)4 * h.R * 8);
         o.active = A.add(&one, 4);
+        o.lw = c->cfg.proposal_rule == 2 ? A.zeros((size_t)h.R * h.N * 8) : 0;
         c->slab_off[k] = c->slab;
         c->slab += (size_t)h.R * h.NW;
         c->NWmax = std::max(c->NWmax, h.NW);
@@ -546,6 +547,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         I.ctr = (Counters*)(b + o.ctr);
         I.stats = (unsigned long long*)(b + o.st);
         I.active = (const int32_t*)(b + o.active);
+        I.lw = c->cfg.proposal_rule == 2 ? (const long long*)(b + o.lw) : nullptr;
         I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
         I.pstride = (long long)c->slab;
     }
@@ -567,7 +569,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
 pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     Arena A;
     const int n = c->n;
-    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, hk, cs, pe_ab, pe_J, ph_i, ph_h, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active; };
+    struct Off { size_t spins, clamp, rowp, rowl, adj, adjJ, adjp, h, hk, cs, pe_ab, pe_J, ph_i, ph_h, cb, E, sow, wos, thr, beta, prop, cur, ctr, st, active, lw; };
     std::vector<Off> o(n);
     c->gr.resize(n);
     size_t maxsmem = 0;
@@ -752,6 +754,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].st = A.zeros((size_t)4 * R * 8);
         const int32_t one = 1;
         o[k].active = A.add(&one, 4);
+        o[k].lw = c->cfg.proposal_rule == 2 ? A.zeros((size_t)R * N * 8) : 0;
         c->slab_off[k] = c->slab;
         c->slab += (size_t)R * NW;
         c->NWmax = std::max(c->NWmax, NW);
@@ -803,6 +806,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         I.ctr = (Counters*)(b + o[k].ctr);
         I.stats = (unsigned long long*)(b + o[k].st);
         I.active = (const int32_t*)(b + o[k].active);
+        I.lw = c->cfg.proposal_rule == 2 ? (const long long*)(b + o[k].lw) : nullptr;
         I.pool = c->pool ? c->pool + c->slab_off[k] : nullptr;
         I.pstride = (long long)c->slab;
     }
@@ -893,8 +897,10 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     if (cfg->sweeps_per_cycle < 1) return fail(PT_EINVAL, "sweeps_per_cycle must be >= 1");
     if (cfg->pool_size < 0) return fail(PT_EINVAL, "pool_size must be >= 0");
     if (cfg->propose_every < 0) return fail(PT_EINVAL, "propose_every must be >= 0");
-    if (cfg->proposal_rule != 0 && cfg->proposal_rule != 1)
-        return fail(PT_EINVAL, "proposal_rule must be 0 or 1");
+    if (cfg->proposal_rule < 0 || cfg->proposal_rule > 2)
+        return fail(PT_EINVAL, "proposal_rule must be 0, 1 or 2");
+    if (cfg->proposal_rule == 2 && cfg->proposal_source != 0)
+        return fail(PT_EINVAL, "proposal_rule 2 needs pool proposals (proposal_source 0)");
     if (cfg->proposal_source != 0 && cfg->proposal_source != 1)
         return fail(PT_EINVAL, "proposal_source must be 0 or 1");
     if (cfg->proposal_source == 1) {
@@ -1160,6 +1166,7 @@ pt_status pt_set_instance(pt_ctx* ctx, int32_t inst, const pt_instance_desc* des
     CK(cudaMemsetAsync(b + o.cur, 0, (size_t)h.R * 4, st));
     CK(cudaMemsetAsync(b + o.ctr, 0, sizeof(Counters), st));
     CK(cudaMemsetAsync(b + o.st, 0, (size_t)4 * h.R * 8, st));
+    if (ctx->cfg.proposal_rule == 2) CK(cudaMemsetAsync(b + o.lw, 0, (size_t)h.R * h.N * 8, st));
     CK(cudaMemcpyAsync(b + o.active, &one, 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->d_lat + inst, &I, sizeof(LatInst), cudaMemcpyHostToDevice, st));
     {
@@ -1360,6 +1367,37 @@ pt_status pt_write_state(pt_ctx* ctx, int32_t inst, const int8_t* spins, const i
     // energies of the written state (all instances: the energy pass leaves others unchanged)
     s = launch_run(ctx, kModeEnergy, 0);
     if (s != PT_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PT_OK;
+}
+
+// Proposal law of one slot's pool for proposal rule 2: the log-odds log(p/(1-p)) of each site,
+// rounded to multiples of 2^-32 (the expression the oracle evaluates), clamped sites 0.
+pt_status pt_load_proposal_law(pt_ctx* ctx, int32_t inst, int32_t replica, const double* p_plus) {
+    const Range range("pt_load_proposal_law");
+    pt_status s = check_inst(ctx, inst);
+    if (s != PT_OK) return s;
+    if (!p_plus) return fail(PT_EINVAL, "p_plus is NULL");
+    if (ctx->cfg.proposal_rule != 2) return fail(PT_ESTATE, "the context's proposal_rule is not 2");
+    const int R = ctx->R[inst], N = ctx->N[inst];
+    if (replica < 0 || replica >= R) return fail(PT_EINVAL, "replica %d out of range [0, %d)", replica, R);
+    const int8_t* clamp = nullptr;
+    std::vector<int8_t> hclamp;
+    if (ctx->engine == 1) {
+        hclamp.resize(N);
+        CK(cudaMemcpyAsync(hclamp.data(), ctx->gr[inst].clamp, N, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        clamp = hclamp.data();
+    }
+    std::vector<long long> w(N);
+    for (int i = 0; i < N; ++i) {
+        const double p = p_plus[i];
+        if (!(p > 0.0 && p < 1.0)) return fail(PT_EINVAL, "p_plus[%d] = %g is not in (0, 1)", i, p);
+        const double lo = log(p) - log1p(-p);
+        w[i] = (clamp && clamp[i] != 0) ? 0 : llround(ldexp(lo, 32));
+    }
+    const long long* dst = (ctx->engine == 0 ? ctx->lat[inst].lw : ctx->gr[inst].lw) + (size_t)replica * N;
+    CK(cudaMemcpyAsync(const_cast<long long*>(dst), w.data(), (size_t)N * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return PT_OK;
 }

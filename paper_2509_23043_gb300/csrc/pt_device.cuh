@@ -137,7 +137,16 @@ struct LatInst {
     long long pstride;     // words between consecutive pool entries
     Counters* ctr;
     unsigned long long* stats;  // [4][R]: swap acc, swap att, prop acc, prop att
+    const long long* lw;   // [R][N] proposal rule 2: log-odds of each slot's proposal law in
+                           // units of 2^-32 (site order), or nullptr
 };
+
+// The FP64 acceptance exponent of proposal rule 2 (the independent Metropolis-Hastings move,
+// Supplementary S2): x = beta_r (E_r - E^T) + (log q(x_r) - log q(x^T)), the log-odds sum d
+// in units of 2^-32 (exact: |d| < 2^53). Rounded product, then rounded sum, never fused.
+__device__ __forceinline__ double mh_exponent(double beta, int dE, long long d) {
+    return __dadd_rn(__dmul_rn(beta, (double)dE), (double)d * 2.3283064365386963e-10);
+}
 
 // Lattice kernel flags: pool proposals, contextual proposals
 constexpr int kWithPool = 1, kWithContext = 2, kGibbs = 4;
@@ -157,7 +166,7 @@ struct RunArgs {
     int32_t n;
     int32_t M, every, start, stop;
     int32_t update;      // 0 Metropolis, 1 Gibbs (the lattice engine takes it from its template)
-    int32_t prule;       // proposal rule: 0 Delta-E-only, 1 always accept
+    int32_t prule;       // proposal rule: 0 Delta-E-only, 1 always accept, 2 independent MH
     int32_t ctx_log2;    // contextual proposals: a site is kept with probability 2^-ctx_log2
     int32_t ctx_sweeps;  // contextual proposals: refill sweeps
     uint32_t rk0[10];    // Philox round keys of the seed (kernel parameters, so the rounds

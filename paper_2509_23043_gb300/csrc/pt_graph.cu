@@ -320,6 +320,39 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
         if (r < R && acc != 0) atomicAdd(&S.Eacc[r], acc);
     }
     __syncthreads();
+    if (rule == 2) {
+        // the independent Metropolis-Hastings move (Supplementary S2): one warp per slot sums
+        // the Hastings correction log q(x_r) - log q(x^T) over the sites, lane 0 decides (the
+        // slot's accept flag replaces its energy count in Eacc; the other slots' counts are
+        // read by their own warps first)
+        for (int r = warp; r < R; r += nwarps) {
+            if (!I.prop[r]) continue;
+            const int w = S.wos[r];
+            const long long* lw = I.lw + (size_t)r * N;
+            const uint32_t* buf = S.pbuf + r * NW;
+            long long d = 0;
+            for (int i = lane; i < N; i += 32) {
+                const long long wi = __ldg(lw + i);
+                if (S.spins[i * I.R4 + w] == 0) d += wi;          // current spin +1
+                if ((buf[i >> 5] >> (i & 31)) & 1u) d -= wi;      // proposed spin +1
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+            if (lane == 0) {
+                const int ET = I.Kprop + 2 * S.Eacc[r];
+                const uint4 q = philox(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid),
+                                       k0, k1);
+                const int acc = accept_fp64(mh_exponent(I.beta[r], S.E[w] - ET, d), q.x);
+                if (acc) S.E[w] = ET;
+                I.cursor[r] = (I.cursor[r] + 1) % I.P;
+                S.st[3 * R + r] += 1u;
+                if (acc) S.st[2 * R + r] += 1u;
+                S.Eacc[r] = acc;
+            }
+        }
+        for (int r = tid; r < R; r += T)
+            if (!I.prop[r]) S.Eacc[r] = 0;
+    } else
     for (int r = tid; r < R; r += T) {
         int acc = 0;
         if (I.prop[r]) {

@@ -48,6 +48,8 @@ struct GraphInst {
     Counters* ctr;
     unsigned long long* stats;
     const int32_t* active;   // nonzero: the instance takes part in launches
+    const long long* lw;     // [R][N] proposal rule 2: log-odds of each slot's proposal law in
+                             // units of 2^-32 (clamped sites 0), or nullptr
 };
 
 struct GraphLayout {

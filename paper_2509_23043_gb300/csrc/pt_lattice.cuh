@@ -487,23 +487,55 @@ static __device__ void lattice_propose(const LatInst& I, LatSmem& S, const RunAr
         if (r >= 0 && lane == __ffs(m) - 1 && v) atomicAdd(&S.us[r], v);
     }
     __syncthreads();
-    for (int r = tid; r < R; r += T) {
-        if (!S.prop[r]) continue;
-        const int w = wos[r];
-        const int ET = 2 * S.us[r] - 3 * N;
-        const int dE = S.E[w] - ET;                   // x = beta_r (E_r - E^T)
-        bool acc = a.prule == 1 || dE >= 0 || S.beta[r] == 0.0;
-        if (!acc) {
-            const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid), a);
-            acc = accept_ratio(S.beta[r], S.fbeta[r], dE, u.x);
+    if (a.prule == 2) {
+        // the independent Metropolis-Hastings move (Supplementary S2): one warp per slot sums
+        // the Hastings correction log q(x_r) - log q(x^T) over the sites, lane 0 decides
+        for (int r = warp; r < R; r += nwarps) {
+            if (!S.prop[r]) continue;
+            const int w = wos[r];
+            const uint2* sw = S.spins + (w >> 5) * N;
+            const uint32_t bit = (uint32_t)(w & 31);
+            const long long* lw = I.lw + (size_t)r * N;
+            const uint32_t* sb = S.stage + r * NW;
+            long long d = 0;
+            for (int i = lane; i < N; i += 32) {
+                const long long wi = __ldg(lw + i);
+                if ((sw[I.pos[i]].x >> bit) & 1u) d += wi;
+                if ((sb[i >> 5] >> (i & 31)) & 1u) d -= wi;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+            if (lane == 0) {
+                const int ET = 2 * S.us[r] - 3 * N;
+                const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid), a);
+                if (accept_fp64(mh_exponent(S.beta[r], S.E[w] - ET, d), u.x)) {
+                    S.E[w] = ET;
+                    S.accr[w] = (int16_t)r;
+                    S.st[2 * R + r] += 1u;
+                }
+                S.cursor[r] = (S.cursor[r] + 1) % I.P;
+                S.st[3 * R + r] += 1u;
+            }
         }
-        if (acc) {
-            S.E[w] = ET;
-            S.accr[w] = (int16_t)r;
-            S.st[2 * R + r] += 1u;
+    } else {
+        for (int r = tid; r < R; r += T) {
+            if (!S.prop[r]) continue;
+            const int w = wos[r];
+            const int ET = 2 * S.us[r] - 3 * N;
+            const int dE = S.E[w] - ET;                   // x = beta_r (E_r - E^T)
+            bool acc = a.prule == 1 || dE >= 0 || S.beta[r] == 0.0;
+            if (!acc) {
+                const uint4 u = philox_rk(make_uint4((uint32_t)r, (uint32_t)n_prop, kDomProp << 24, I.iid), a);
+                acc = accept_ratio(S.beta[r], S.fbeta[r], dE, u.x);
+            }
+            if (acc) {
+                S.E[w] = ET;
+                S.accr[w] = (int16_t)r;
+                S.st[2 * R + r] += 1u;
+            }
+            S.cursor[r] = (S.cursor[r] + 1) % I.P;
+            S.st[3 * R + r] += 1u;
         }
-        S.cursor[r] = (S.cursor[r] + 1) % I.P;
-        S.st[3 * R + r] += 1u;
     }
     __syncthreads();
     for (int wb = 0; wb < I.W; ++wb) {

@@ -56,7 +56,59 @@ def test_always_accept_rule_matches_oracle(engine):
 
 def test_rule_out_of_range_rejected():
     with pytest.raises(pt.PTError):
-        pt.create_instances([I.ea_instance(4)], [[0.5, 1.0]], pt.Config(proposal_rule=2))
+        pt.create_instances([I.ea_instance(4)], [[0.5, 1.0]], pt.Config(proposal_rule=3))
+    with pytest.raises(pt.PTError):          # the MH rule needs pool proposals
+        pt.create_instances([I.ea_instance(4)], [[0.5, 1.0]],
+                            pt.Config(proposal_rule=2, proposal_source=1))
+
+
+@pytest.mark.parametrize("engine,R", [("lattice", 12), ("lattice", 40), ("graph", 10), ("graph", 36)])
+def test_independent_mh_rule_matches_oracle(engine, R):
+    # proposal_rule 2 (Supplementary S2, the MH rule) with product-Bernoulli laws loaded per
+    # slot (some slots left at the uniform law): spins, energies, walkers, decisions and
+    # statistics bit-exact against the oracle, after several chunk sizes
+    if engine == "lattice":
+        inst, update = I.ea_instance(6, index=13), 0
+    else:
+        inst, update = I.multiplier(3).instance(35), 1
+    P = 8
+    N = inst.n_spins
+    betas = I.geometric_betas(0.002, 0.5, R)     # hot: random entries are sometimes accepted
+    prop = [1] * (R - 2) + [0, 0]
+    cfg = pt.Config(update=update, seed=0x52, propose_every=2, propose_start=0, pool_size=P,
+                    proposal_rule=pt.INDEPENDENT_MH)
+    ctx = pt.create_instances([inst], [betas], cfg, prop_enabled=[prop], instance_ids=[22])
+    assert pt.info(ctx)["engine"] == engine
+    o = O.Oracle(inst, betas, instance_id=22, prop_enabled=prop, update=update,
+                 propose_every=2, seed=0x52, pool_size=P, proposal_rule=2)
+    g = np.random.default_rng(31)
+    for r in range(R):
+        law = g.uniform(0.45, 0.55, size=N)
+        pool = np.where(g.random((P, N)) < law[None, :], 1, -1).astype(np.int8)
+        pt.load_proposals(ctx, 0, r, pool)
+        o.load_pool(r, pool)
+        if r % 5 != 4:                        # every fifth slot keeps the uniform law
+            pt.load_proposal_law(ctx, 0, r, law)
+            o.load_law(r, law)
+    for chunk in (2, 7, 21):
+        pt.run_cycles(ctx, chunk)
+        o.run_cycles(chunk)
+        _same(ctx, 0, o)
+    sa, st, pa, ptot = pt.read_stats(ctx, 0)
+    osa, ost, opa, optot = o.stats()
+    assert np.array_equal(pa, opa) and np.array_equal(ptot, optot)
+    assert 0 < pa.sum() < ptot.sum()          # some proposals accepted, some rejected
+
+
+def test_proposal_law_needs_the_mh_rule():
+    ctx = pt.create_instances([I.ea_instance(4)], [[0.5, 1.0]], pt.Config(pool_size=2))
+    with pytest.raises(pt.PTError) as e:
+        pt.load_proposal_law(ctx, 0, 0, np.full(64, 0.5))
+    assert e.value.status == pt.PT_ESTATE
+    ctx2 = pt.create_instances([I.ea_instance(4)], [[0.5, 1.0]],
+                               pt.Config(pool_size=2, proposal_rule=pt.INDEPENDENT_MH))
+    with pytest.raises(pt.PTError):
+        pt.load_proposal_law(ctx2, 0, 0, np.full(64, 1.0))   # outside (0, 1)
 
 
 def _energy_marginals(p_states, E):
