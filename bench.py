@@ -253,14 +253,14 @@ def alu_ops_per_word(e_blocks: float, gibbs: bool = False) -> float:
     6 three-input XORs (bond test) + 8 (bit-sliced adder) + 2 (class masks) + 2 (flip)
     + 4.5 (energy count in the last colour, half the words) + per plane block: 20 (the
     three-input XORs of Philox4x32-10's 10 rounds; its 20 wide multiplies run on the FMA pipe)
-    + 17 for comparing its four planes: 4 x 2 to pick each plane's class threshold, then the
-    chained compare (4 steps for the decided-below bit, 4 for the still-undecided mask, 1 to
-    merge). Gibbs: 4 for the class q and 1 for the flip instead of the class masks and flip,
-    and 4 x 6 per block to pick each plane's threshold by a six-mux tree, with the same 9 for
-    the chain."""
+    + 4 planes x 5 for the compare the Metropolis kernel performs (2 to pick the class
+    threshold, 3 to compare one plane). Gibbs: 4 for the class q and 1 for the flip instead of
+    the class masks and flip, and per block 4 x 6 to pick each plane's threshold by a six-mux
+    tree plus 9 for the chained compare of the four planes (4 steps for the decided-below bit,
+    4 for the still-undecided mask, 1 to merge), the compare the Gibbs kernel performs."""
     if gibbs:
         return 6 + 8 + 4 + 1 + 4.5 + e_blocks * (20 + 24 + 9)
-    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 8 + 9)
+    return 6 + 8 + 2 + 2 + 4.5 + e_blocks * (20 + 20)
 
 
 def smem_bytes_per_word(e_blocks: float, gibbs: bool = False) -> float:
