@@ -271,3 +271,62 @@ def unpack_bits(words: np.ndarray, N: int) -> np.ndarray:
     bits = (w[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1
     bits = bits.reshape(w.shape[:-1] + (w.shape[-1] * 32,))[..., :N]
     return (2 * bits.astype(np.int8) - 1).astype(np.int8)
+
+
+# ---------------------------------------------------------------------------------- IsingFormer
+# Seeded parameters of the IsingFormer decoder (Methods, "IsingFormer architecture and
+# training"; Supplementary S6). No trained weights exist here, so the parameters are random;
+# they are rounded to bfloat16, the format the GPU library keeps them in, and both the library
+# and the oracle take exactly these values.
+
+@dataclass
+class FormerShape:
+    n_spins: int            # sequence length N
+    d_model: int = 256
+    n_heads: int = 4
+    n_layers: int = 5
+    d_ff: int = 1024
+
+
+def former_param_shapes(s: FormerShape) -> list[tuple[str, tuple[int, ...]]]:
+    """The parameters in their packing order (the order of the C ABI's weight array). Matrices
+    are row-major [in][out]: y = x W + b."""
+    d, F = s.d_model, s.d_ff
+    out = [("tok_emb", (3, d)), ("w_beta", (d,)), ("b_beta", (d,))]
+    for l in range(s.n_layers):
+        out += [(f"l{l}.ln1_g", (d,)), (f"l{l}.ln1_b", (d,)), (f"l{l}.w_qkv", (d, 3 * d)),
+                (f"l{l}.b_qkv", (3 * d,)), (f"l{l}.w_o", (d, d)), (f"l{l}.b_o", (d,)),
+                (f"l{l}.ln2_g", (d,)), (f"l{l}.ln2_b", (d,)), (f"l{l}.w_1", (d, F)),
+                (f"l{l}.b_1", (F,)), (f"l{l}.w_2", (F, d)), (f"l{l}.b_2", (d,))]
+    out += [("lnf_g", (d,)), ("lnf_b", (d,)), ("w_out", (d, 2)), ("b_out", (2,))]
+    return out
+
+
+def bf16_round(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Round to bfloat16 (nearest, ties to even): the 16-bit patterns and their values."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+    v = (r.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return r, v.reshape(x.shape)
+
+
+def former_weights(s: FormerShape, seed: int = MASTER_SEED, index: int = 0):
+    """Random IsingFormer parameters, bfloat16-rounded: (dict of float64 arrays, packed uint16
+    array in former_param_shapes order). Matrices ~ N(0, 1/fan_in), the token and beta
+    embeddings ~ N(0, 1), layer-norm gains 1 + N(0, 0.1^2), biases ~ N(0, 0.1^2)."""
+    g = _rng(seed, 0xF0, s.n_spins, index)
+    vals, packed = {}, []
+    for name, shape in former_param_shapes(s):
+        if name.endswith("_g"):
+            x = 1.0 + 0.1 * g.standard_normal(shape)
+        elif name in ("tok_emb", "w_beta"):
+            x = g.standard_normal(shape)
+        elif len(shape) == 2:
+            x = g.standard_normal(shape) / math.sqrt(shape[0])
+        else:
+            x = 0.1 * g.standard_normal(shape)
+        r, v = bf16_round(x)
+        vals[name] = v
+        packed.append(r.reshape(-1))
+    return vals, np.concatenate(packed)
