@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,engines,ragged,factor,ladder,context,tts",
+    p.add_argument("--workloads", default="plain,engines,ragged,factor,ladder,context,tts,former",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--factor-pool-size", type=int, default=512)
@@ -946,6 +946,83 @@ def context_ablation(stream, n=64, L=10, R=32, sweeps=3000, chunk=500):
                         f"sweeps", "modes": out}
 
 
+def isingformer_workload(stream, B=1024, reps=5):
+    """IsingFormer inference at the paper's spin-glass and factorization shape (d_model 256,
+    4 heads, 5 layers, FFN 1024; Methods and Supplementary S6) over the 8x8-bit multiplier's
+    N = 200 spins in the factorization order {C}{carry}{multiplier}{B}{A}, seeded bfloat16
+    weights. Scoring: log q(x | beta) of B configurations in one teacher-forced pass (the
+    Hastings factor of an MH move with a learned q). Sampling: B configurations drawn one
+    position after another, the product and carry-in bits given as the clamped prefix
+    (Supplementary S6), replayed from a CUDA graph. Tensor roofline of the matrix products
+    (bfloat16 inputs, FP32 accumulation) against the measured bfloat16 peak."""
+    import torch
+    import instances as I
+    from paper_2509_23043_gb300.former import Former
+    mult = I.multiplier(8)
+    N = mult.n_spins
+    shp = I.FormerShape(n_spins=N)
+    W, packed = I.former_weights(shp)
+    m = Former(shp, packed, stream=stream.cuda_stream)
+    g = np.random.default_rng(0xF0F0)
+    X = torch.from_numpy(np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)).cuda()
+    beta = torch.from_numpy(I.geometric_betas(0.05, 5.0, 32)[g.integers(0, 23, B)].astype(np.float32)).cuda()
+    ms = _time_ms(lambda: m.score(X, beta), reps, stream)
+    gemm = m.score_gemm_flops(B)
+    attn = shp.n_layers * shp.n_heads * B * (N * (N + 1) / 2) * 64 * 4.0
+    peak_tf = _measured_peak("bf16_tflops")
+    # sampling with the product and carry-in bits of a product as the prefix
+    inst = mult.instance(251 * 241)
+    npre = int((inst.clamp != 0).sum())
+    assert np.all(inst.clamp[:npre] != 0), "the clamped bits lead the factorization order"
+    pre = torch.from_numpy(np.tile(inst.clamp[:npre], (B, 1)).astype(np.int8)).cuda()
+    out = torch.empty((B, N), dtype=torch.int8, device="cuda")
+    lq = torch.empty(B, dtype=torch.float32, device="cuda")
+    m.sample(beta, 1, 0, prefix=pre, out=out, logq=lq)        # direct launches + capture
+    ms_s = _time_ms(lambda: m.sample(beta, 2, 0, prefix=pre, out=out, logq=lq), reps, stream)
+    # end to end: configurations in from pinned host memory, log q out, every call
+    hx = X.cpu().pin_memory()
+    hq = torch.empty(B, dtype=torch.float32).pin_memory()
+    dx = torch.empty_like(X)
+
+    def e2e_call():
+        dx.copy_(hx, non_blocking=True)
+        hq.copy_(m.score(dx, beta), non_blocking=True)
+    ms_e = _time_ms(e2e_call, reps, stream)
+    out_d = {"workload": f"IsingFormer d_model 256, 4 heads, 5 layers, FFN 1024, seeded bfloat16 "
+                         f"weights, N = {N} (8x8 multiplier), B = {B} configurations per call",
+             "score": {"configs_per_s": B / (ms * 1e-3), "ms_per_call": ms,
+                       "roofline": {"bound": "tensor", "achieved": gemm / (ms * 1e-3) / 1e12,
+                                    "peak": peak_tf, "unit": "TFLOP/s",
+                                    "frac": gemm / (ms * 1e-3) / 1e12 / peak_tf if peak_tf else None,
+                                    "traffic": None, "kernel": "the scoring pass (cuBLASLt projections "
+                                    "and this library's attention, norms and head)",
+                                    "flops_per_call": gemm, "attention_flops_per_call": attn,
+                                    "note": "matrix-product FLOPs over the whole pass's time; the "
+                                            "attention's FP32 FLOPs are reported beside it"}},
+             "sample": {"configs_per_s": B / (ms_s * 1e-3), "ms_per_call": ms_s, "prefix": npre,
+                        "gpu_launches_per_call": "one CUDA graph of N steps"},
+             "e2e": {"value": B / (ms_e * 1e-3), "unit": "configs/s", "h2d_bytes_per_step": B * N,
+                     "d2h_bytes_per_step": B * 4}}
+    # the oracle on the host cores (numpy float64, BLAS threads): a few configurations
+    from oracle import former as F
+    t0 = time.perf_counter()
+    F.score(W, shp, X[:8].cpu().numpy(), beta[:8].cpu().numpy().astype(np.float64))
+    dt = time.perf_counter() - t0
+    out_d["cpu_baseline"] = {"value": 8 / dt, "unit": "configs/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "8 configurations scored by the float64 "
+                             "numpy oracle (BLAS threads on the host cores)"}
+    del m
+    return out_d
+
+
+def _measured_peak(key):
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        return float(json.loads(p.read_text())[key])
+    except (OSError, KeyError, ValueError):
+        return 1900.0 if key == "bf16_tflops" else None
+
+
 def _ev_pair():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1205,6 +1282,8 @@ def main():
                                                    modes=("plain_pt",), growth=3)
         if "context" in wl:
             others["context_ablation"] = context_ablation(stream)
+        if "former" in wl:
+            others["isingformer"] = isingformer_workload(stream)
 
     cpu = None
     if cpu_pool is not None:

@@ -18,6 +18,10 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libpt.so"
+# IsingFormer inference: its own library, as it links cuBLASLt for the plain projections
+FORMER_LIB = OUT_DIR / "libptformer.so"
+FORMER_SOURCES = ["pt_former.cu"]
+CUDA_LIB_DIR = "/usr/local/cuda/lib64"
 SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_lattice_gibbs.cu", "pt_graph.cu", "pt_calib.cu"]
 HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh", "pt_lattice.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,10 +38,11 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not LIB.exists():
+    if not LIB.exists() or not FORMER_LIB.exists():
         return True
-    t = LIB.stat().st_mtime
-    deps = [CSRC / s for s in SOURCES + HEADERS] + [PKG.parent / "include" / "pt.h"]
+    t = min(LIB.stat().st_mtime, FORMER_LIB.stat().st_mtime)
+    deps = [CSRC / s for s in SOURCES + FORMER_SOURCES + HEADERS] + \
+        [PKG.parent / "include" / "pt.h", PKG.parent / "include" / "pt_former.h"]
     return any(p.stat().st_mtime > t for p in deps)
 
 
@@ -59,14 +64,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(r.stderr, file=sys.stderr)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = OUT_DIR / f"libpt.{os.getpid()}.so"
-    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(len(SOURCES) + len(FORMER_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + FORMER_SOURCES))
+    core, former = objs[:len(SOURCES)], objs[len(SOURCES):]
+    for out, parts, libs in ((LIB, core, ["-lcudart"]),
+                             (FORMER_LIB, former, ["-lcudart", f"-L{CUDA_LIB_DIR}", "-lcublasLt",
+                                                   "-Xlinker", f"-rpath,{CUDA_LIB_DIR}"])):
+        tmp = OUT_DIR / f"{out.stem}.{os.getpid()}.so"
+        cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, parts), *libs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed for {out.name}:\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

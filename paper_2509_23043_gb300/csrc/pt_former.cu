@@ -1,0 +1,748 @@
+// IsingFormer inference on GB300 (sm_103a): the decoder-only transformer of arXiv 2509.23043
+// (Methods, "IsingFormer architecture and training"; Supplementary S6) that gives the TAPT
+// proposals their law q(x | beta) and draws them. See include/pt_former.h for the model.
+//
+// Layout (row-major, one row per (configuration, position) for scoring, per configuration
+// for a sampling step): residual stream h FP32 [M][d]; layer-norm outputs, attention outputs
+// and GELU outputs bfloat16 (the inputs of the matrix products); query/key/value and the
+// first FFN map FP32. The matrix products run on the tensor cores through cuBLASLt (bfloat16
+// inputs, FP32 accumulation, bias and residual in the epilogue); the rest are the kernels
+// below. Sampling keeps an FP32 key/value cache [layer][B][N][2d].
+#include <cublasLt.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pt_former.h"
+#include "pt_device.cuh"
+
+namespace {
+
+thread_local std::string g_ferr;
+
+pt_status ffail(pt_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_ferr = buf;
+    return s;
+}
+
+#define FCK(x)                                                                           \
+    do {                                                                                 \
+        cudaError_t e_ = (x);                                                            \
+        if (e_ != cudaSuccess) return ffail(PT_ECUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+#define LCK(x)                                                                           \
+    do {                                                                                 \
+        cublasStatus_t s_ = (x);                                                         \
+        if (s_ != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "%s: cublas status %d", #x, (int)s_); \
+    } while (0)
+
+constexpr int kDH = 64;          // head dimension
+constexpr uint32_t kDomSample = 6u;
+
+// ------------------------------------------------------------------------------ kernels
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(pt::kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(pt::kFull, v, o));
+    return v;
+}
+
+// h[b N + t] = tok_emb[token] + (beta_b W_beta + b_beta) + PE[t]; token = start (2) at t = 0,
+// else the token of spin t - 1 (teacher forcing: the configurations scored).
+__global__ void embed_score_kernel(const int8_t* __restrict__ spins, const float* __restrict__ beta,
+                                   const float* __restrict__ tok, const float* __restrict__ wb,
+                                   const float* __restrict__ bb, const float* __restrict__ pe,
+                                   float* __restrict__ h, int N, int d) {
+    const size_t row = blockIdx.x;
+    const int b = (int)(row / N), t = (int)(row - (size_t)b * N);
+    const int k = t == 0 ? 2 : (spins[(size_t)b * N + t - 1] > 0 ? 1 : 0);
+    const float be = beta[b];
+    for (int c = threadIdx.x; c < d; c += blockDim.x)
+        h[row * d + c] = tok[k * d + c] + (be * wb[c] + bb[c]) + pe[(size_t)t * d + c];
+}
+
+// one sampling step: h[b] for position t, the token of the spin drawn at t - 1
+__global__ void embed_step_kernel(const int8_t* __restrict__ out, const float* __restrict__ beta,
+                                  const float* __restrict__ tok, const float* __restrict__ wb,
+                                  const float* __restrict__ bb, const float* __restrict__ pe,
+                                  float* __restrict__ h, int N, int d, int t) {
+    const int b = blockIdx.x;
+    const int k = t == 0 ? 2 : (out[(size_t)b * N + t - 1] > 0 ? 1 : 0);
+    const float be = beta[b];
+    for (int c = threadIdx.x; c < d; c += blockDim.x)
+        h[(size_t)b * d + c] = tok[k * d + c] + (be * wb[c] + bb[c]) + pe[(size_t)t * d + c];
+}
+
+// layer norm of each row (one warp per row), eps 1e-5, to bfloat16
+template <int D>
+__global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ g,
+                                 const float* __restrict__ bt, __nv_bfloat16* __restrict__ y,
+                                 size_t M) {
+    const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const float* xr = x + row * D;
+    float v[D / 32];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        v[i] = xr[lane + 32 * i];
+        s += v[i];
+    }
+    const float mu = warp_sum(s) / D;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        v[i] -= mu;
+        q += v[i] * v[i];
+    }
+    const float rstd = rsqrtf(warp_sum(q) / D + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        const int c = lane + 32 * i;
+        y[row * D + c] = __float2bfloat16_rn(v[i] * rstd * g[c] + bt[c]);
+    }
+}
+
+// y = GELU(x) = x (1 + erf(x / sqrt 2)) / 2, to bfloat16
+__global__ void gelu_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        y[i] = __float2bfloat16_rn(0.5f * v * (1.f + erff(v * 0.70710678118654752f)));
+    }
+}
+
+// Causal multi-head attention of the scoring pass: block (query block of 128, head, b); each
+// thread one query row, keys streamed through shared memory 64 at a time, softmax kept
+// online (running maximum and sum). qkv FP32 [B N][3d]; out bfloat16 [B N][d].
+constexpr int kAQ = 128, kAK = 64;
+__global__ void __launch_bounds__(kAQ) attention_kernel(const float* __restrict__ qkv,
+                                                        __nv_bfloat16* __restrict__ out, int N, int d) {
+    __shared__ float Ks[kAK][kDH];
+    __shared__ float Vs[kAK][kDH];
+    const int hd = blockIdx.y, b = blockIdx.z;
+    const int t0 = blockIdx.x * kAQ;
+    const int t = t0 + threadIdx.x;
+    const size_t ld = 3 * (size_t)d;
+    const float* base = qkv + (size_t)b * N * ld;
+    float q[kDH], acc[kDH];
+    if (t < N) {
+#pragma unroll
+        for (int c = 0; c < kDH; ++c) {
+            q[c] = base[(size_t)t * ld + hd * kDH + c] * 0.125f;      // 1 / sqrt(64)
+            acc[c] = 0.f;
+        }
+    }
+    float m = -INFINITY, l = 0.f;
+    const int tmax = min(N - 1, t0 + kAQ - 1);
+    for (int j0 = 0; j0 <= tmax; j0 += kAK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kAK * kDH; e += kAQ) {
+            const int r = e / kDH, c = e - r * kDH;
+            const int j = j0 + r;
+            Ks[r][c] = j < N ? base[(size_t)j * ld + d + hd * kDH + c] : 0.f;
+            Vs[r][c] = j < N ? base[(size_t)j * ld + 2 * d + hd * kDH + c] : 0.f;
+        }
+        __syncthreads();
+        if (t < N) {
+            const int jn = min(kAK, t - j0 + 1);
+            for (int r = 0; r < jn; ++r) {
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < kDH; ++c) s = fmaf(q[c], Ks[r][c], s);
+                const float mn = fmaxf(m, s);
+                const float corr = expf(m - mn), p = expf(s - mn);
+                l = l * corr + p;
+#pragma unroll
+                for (int c = 0; c < kDH; ++c) acc[c] = fmaf(p, Vs[r][c], acc[c] * corr);
+                m = mn;
+            }
+        }
+    }
+    if (t < N) {
+        const float inv = 1.f / l;
+        __nv_bfloat16* o = out + ((size_t)b * N + t) * d + hd * kDH;
+#pragma unroll
+        for (int c = 0; c < kDH; ++c) o[c] = __float2bfloat16_rn(acc[c] * inv);
+    }
+}
+
+// append the keys and values of step t to the cache [B][N][2d] of one layer
+__global__ void kv_append_kernel(const float* __restrict__ qkv, float* __restrict__ cache, int N, int d, int t) {
+    const int b = blockIdx.x;
+    for (int c = threadIdx.x; c < 2 * d; c += blockDim.x)
+        cache[((size_t)b * N + t) * 2 * d + c] = qkv[(size_t)b * 3 * d + d + c];
+}
+
+// Attention of the step-t query against the cached keys 0..t: block b, one warp per head;
+// lanes score keys lane, lane + 32, ..., then each lane sums two of the 64 output dimensions.
+__global__ void attention_step_kernel(const float* __restrict__ qkv, const float* __restrict__ cache,
+                                      __nv_bfloat16* __restrict__ out, int N, int d, int t) {
+    extern __shared__ float sm[];              // per warp: q [64], p [N]
+    const int hd = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.x;
+    float* qs = sm + hd * (kDH + N);
+    float* ps = qs + kDH;
+    const float* qr = qkv + (size_t)b * 3 * d + hd * kDH;
+    qs[lane] = qr[lane] * 0.125f;
+    qs[lane + 32] = qr[lane + 32] * 0.125f;
+    __syncwarp();
+    const float* kb = cache + (size_t)b * N * 2 * d + hd * kDH;
+    float mx = -INFINITY;
+    for (int j = lane; j <= t; j += 32) {
+        const float* kr = kb + (size_t)j * 2 * d;
+        float s = 0.f;
+#pragma unroll 16
+        for (int c = 0; c < kDH; ++c) s = fmaf(qs[c], kr[c], s);
+        ps[j] = s;
+        mx = fmaxf(mx, s);
+    }
+    mx = warp_max(mx);
+    float sum = 0.f;
+    for (int j = lane; j <= t; j += 32) {
+        const float p = expf(ps[j] - mx);
+        ps[j] = p;
+        sum += p;
+    }
+    sum = warp_sum(sum);
+    __syncwarp();
+    float a0 = 0.f, a1 = 0.f;
+    const float* vb = kb + d;
+    for (int j = 0; j <= t; ++j) {
+        const float p = ps[j];
+        const float* vr = vb + (size_t)j * 2 * d;
+        a0 = fmaf(p, vr[2 * lane], a0);
+        a1 = fmaf(p, vr[2 * lane + 1], a1);
+    }
+    const float inv = 1.f / sum;
+    __nv_bfloat16* o = out + (size_t)b * d + hd * kDH;
+    o[2 * lane] = __float2bfloat16_rn(a0 * inv);
+    o[2 * lane + 1] = __float2bfloat16_rn(a1 * inv);
+}
+
+// final layer norm and head of one row (one warp): the two logits and their log-softmax
+template <int D>
+__device__ __forceinline__ void head_row(const float* xr, const float* g, const float* bt,
+                                         const float* wout, const float* bout, int lane,
+                                         float& l0, float& l1) {
+    float v[D / 32];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        v[i] = xr[lane + 32 * i];
+        s += v[i];
+    }
+    const float mu = warp_sum(s) / D;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        v[i] -= mu;
+        q += v[i] * v[i];
+    }
+    const float rstd = rsqrtf(warp_sum(q) / D + 1e-5f);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        const int c = lane + 32 * i;
+        const float z = v[i] * rstd * g[c] + bt[c];
+        a0 = fmaf(z, wout[2 * c], a0);
+        a1 = fmaf(z, wout[2 * c + 1], a1);
+    }
+    l0 = warp_sum(a0) + bout[0];
+    l1 = warp_sum(a1) + bout[1];
+}
+
+__device__ __forceinline__ void log_softmax2(float l0, float l1, float& p0, float& p1) {
+    const float m = fmaxf(l0, l1);
+    const float lse = m + logf(expf(l0 - m) + expf(l1 - m));
+    p0 = l0 - lse;
+    p1 = l1 - lse;
+}
+
+// scoring head: per row the log-probability of the scored spin (and the logits)
+template <int D>
+__global__ void head_score_kernel(const float* __restrict__ h, const float* __restrict__ g,
+                                  const float* __restrict__ bt, const float* __restrict__ wout,
+                                  const float* __restrict__ bout, const int8_t* __restrict__ spins,
+                                  float* __restrict__ lp, float* __restrict__ logits, size_t M) {
+    const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    float l0, l1, p0, p1;
+    head_row<D>(h + row * D, g, bt, wout, bout, lane, l0, l1);
+    log_softmax2(l0, l1, p0, p1);
+    if (lane == 0) {
+        lp[row] = spins[row] > 0 ? p1 : p0;
+        if (logits) {
+            logits[2 * row] = l0;
+            logits[2 * row + 1] = l1;
+        }
+    }
+}
+
+// log q[b] = sum over positions, in position order (one warp per configuration)
+__global__ void sum_rows_kernel(const float* __restrict__ lp, float* __restrict__ logq, int B, int N) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float s = 0.f;
+    for (int t = lane; t < N; t += 32) s += lp[(size_t)b * N + t];
+    s = warp_sum(s);
+    if (lane == 0) logq[b] = s;
+}
+
+struct SampleArgs {
+    uint64_t seed;
+    uint32_t stream;
+};
+
+// sampling head of step t: spin t of each configuration (one warp each) drawn from its
+// logits (or copied from the prefix), its log-probability added to log q
+template <int D>
+__global__ void head_sample_kernel(const float* __restrict__ h, const float* __restrict__ g,
+                                   const float* __restrict__ bt, const float* __restrict__ wout,
+                                   const float* __restrict__ bout, const int8_t* __restrict__ prefix,
+                                   int npre, const SampleArgs* __restrict__ sa, int8_t* __restrict__ out,
+                                   float* __restrict__ logq, int B, int N, int t) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float l0, l1, p0, p1;
+    head_row<D>(h + (size_t)b * D, g, bt, wout, bout, lane, l0, l1);
+    log_softmax2(l0, l1, p0, p1);
+    if (lane == 0) {
+        int8_t s;
+        if (t < npre) {
+            s = prefix[(size_t)b * npre + t] > 0 ? 1 : -1;
+        } else {
+            const uint64_t seed = sa->seed;
+            const uint4 r = pt::philox(make_uint4((uint32_t)t, (uint32_t)b, kDomSample << 24, sa->stream),
+                                       (uint32_t)seed, (uint32_t)(seed >> 32));
+            const float u = (float)(r.x >> 8) * 5.9604644775390625e-08f;   // 2^-24
+            s = u < expf(p1) ? 1 : -1;
+        }
+        out[(size_t)b * N + t] = s;
+        const float add = s > 0 ? p1 : p0;
+        if (logq) logq[b] = (t == 0 ? 0.f : logq[b]) + add;
+    }
+}
+
+// ------------------------------------------------------------------------------ host side
+float bf16_bits_to_float(uint16_t v) {
+    uint32_t u = (uint32_t)v << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+struct Layer {
+    float *ln1_g, *ln1_b, *b_qkv, *b_o, *ln2_g, *ln2_b, *b_1, *b_2;
+    __nv_bfloat16 *w_qkv, *w_o, *w_1, *w_2;
+};
+
+struct Act {                       // activation buffers for `rows` rows
+    size_t rows = 0;
+    float *h = nullptr, *qkv = nullptr, *f1 = nullptr, *lp = nullptr;
+    __nv_bfloat16 *a = nullptr, *o = nullptr, *g = nullptr;
+};
+
+}  // namespace
+
+struct pt_former {
+    pt_former_config cfg{};
+    cudaStream_t stream = nullptr;     // the caller's stream: every call is ordered on it
+    cudaStream_t exec = nullptr;       // the stream the launches go to (stream, or cap in capture)
+    cudaStream_t cap = nullptr;        // private stream of the sampling graph (capture, replay)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cublasLtHandle_t lt = nullptr;
+    void* workspace = nullptr;
+    size_t ws_bytes = 32u << 20;
+    std::vector<void*> allocs;
+    float *tok = nullptr, *wb = nullptr, *bb = nullptr, *pe = nullptr;
+    float *lnf_g = nullptr, *lnf_b = nullptr, *wout = nullptr, *bout = nullptr;
+    std::vector<Layer> layers;
+    Act score, step;
+    float* cache = nullptr;        // sampling: [L][B][N][2d]
+    int cache_B = 0;
+    SampleArgs* d_sargs = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::tuple<int, int, const void*, const void*, const void*, const void*> gkey{};
+    std::map<std::tuple<size_t, int, int, int>, cublasLtMatmulAlgo_t> algos;
+};
+
+namespace {
+
+template <class T>
+pt_status dalloc(pt_former* m, T** p, size_t n) {
+    void* q = nullptr;
+    FCK(cudaMalloc(&q, n * sizeof(T) + 16));
+    m->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return PT_OK;
+}
+
+pt_status upload_f32(pt_former* m, float** dst, const uint16_t* src, size_t n) {
+    std::vector<float> h(n);
+    for (size_t i = 0; i < n; ++i) h[i] = bf16_bits_to_float(src[i]);
+    pt_status s = dalloc(m, dst, n);
+    if (s != PT_OK) return s;
+    FCK(cudaMemcpy(*dst, h.data(), n * 4, cudaMemcpyHostToDevice));
+    return PT_OK;
+}
+
+pt_status upload_bf16(pt_former* m, __nv_bfloat16** dst, const uint16_t* src, size_t n) {
+    pt_status s = dalloc(m, dst, n);
+    if (s != PT_OK) return s;
+    FCK(cudaMemcpy(*dst, src, n * 2, cudaMemcpyHostToDevice));
+    return PT_OK;
+}
+
+void free_act(Act& a) {
+    cudaFree(a.h); cudaFree(a.qkv); cudaFree(a.f1); cudaFree(a.lp);
+    cudaFree(a.a); cudaFree(a.o); cudaFree(a.g);
+    a = Act{};
+}
+
+pt_status ensure_act(pt_former* m, Act& a, size_t rows) {
+    if (a.rows >= rows) return PT_OK;
+    free_act(a);
+    const size_t d = m->cfg.d_model, F = m->cfg.d_ff;
+    FCK(cudaMalloc(&a.h, rows * d * 4));
+    FCK(cudaMalloc(&a.qkv, rows * 3 * d * 4));
+    FCK(cudaMalloc(&a.f1, rows * F * 4));
+    FCK(cudaMalloc(&a.lp, rows * 4));
+    FCK(cudaMalloc(&a.a, rows * d * 2));
+    FCK(cudaMalloc(&a.o, rows * d * 2));
+    FCK(cudaMalloc(&a.g, rows * F * 2));
+    a.rows = rows;
+    return PT_OK;
+}
+
+// Y [rows][n] (FP32) = X [rows][k] (bf16) W [k][n] (bf16) + bias [n] (+ Y when residual):
+// column-major Y^T = W^T X^T, with W^T as the [n x k] column-major view of row-major W.
+pt_status gemm(pt_former* m, float* Y, const __nv_bfloat16* X, const __nv_bfloat16* W,
+               const float* bias, size_t rows, int n, int k, bool residual) {
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
+    LCK(cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F));
+    const cublasOperation_t nt = CUBLAS_OP_N;
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &nt, sizeof nt));
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &nt, sizeof nt));
+    const cublasLtEpilogue_t ep = CUBLASLT_EPILOGUE_BIAS;
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_EPILOGUE, &ep, sizeof ep));
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof bias));
+    const cudaDataType_t bt = CUDA_R_32F;
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_BIAS_DATA_TYPE, &bt, sizeof bt));
+    LCK(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, n, k, n));
+    LCK(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, k, (uint64_t)rows, k));
+    LCK(cublasLtMatrixLayoutCreate(&lc, CUDA_R_32F, n, (uint64_t)rows, n));
+    const auto key = std::make_tuple(rows, n, k, residual ? 1 : 0);
+    auto it = m->algos.find(key);
+    if (it == m->algos.end()) {
+        cublasLtMatmulPreference_t pref = nullptr;
+        LCK(cublasLtMatmulPreferenceCreate(&pref));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES,
+                                                 &m->ws_bytes, sizeof m->ws_bytes));
+        cublasLtMatmulHeuristicResult_t res{};
+        int got = 0;
+        LCK(cublasLtMatmulAlgoGetHeuristic(m->lt, op, la, lb, lc, lc, pref, 1, &res, &got));
+        cublasLtMatmulPreferenceDestroy(pref);
+        if (got < 1) return ffail(PT_ENOTSUP, "no cuBLASLt algorithm for %zu x %d x %d", rows, n, k);
+        it = m->algos.emplace(key, res.algo).first;
+    }
+    const float one = 1.f, beta = residual ? 1.f : 0.f;
+    const cublasStatus_t st = cublasLtMatmul(m->lt, op, &one, W, la, X, lb, &beta, Y, lc, Y, lc,
+                                             &it->second, m->workspace, m->ws_bytes, m->exec);
+    cublasLtMatrixLayoutDestroy(la);
+    cublasLtMatrixLayoutDestroy(lb);
+    cublasLtMatrixLayoutDestroy(lc);
+    cublasLtMatmulDescDestroy(op);
+    if (st != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "cublasLtMatmul: status %d", (int)st);
+    return PT_OK;
+}
+
+template <int D>
+void launch_layernorm(const float* x, const float* g, const float* b, __nv_bfloat16* y, size_t M,
+                      cudaStream_t s) {
+    layernorm_kernel<D><<<(unsigned)((M + 7) / 8), 256, 0, s>>>(x, g, b, y, M);
+}
+
+pt_status layernorm(pt_former* m, const float* x, const float* g, const float* b, __nv_bfloat16* y,
+                    size_t M) {
+    switch (m->cfg.d_model) {
+        case 64: launch_layernorm<64>(x, g, b, y, M, m->exec); break;
+        case 128: launch_layernorm<128>(x, g, b, y, M, m->exec); break;
+        case 256: launch_layernorm<256>(x, g, b, y, M, m->exec); break;
+        case 512: launch_layernorm<512>(x, g, b, y, M, m->exec); break;
+        default: return ffail(PT_ENOTSUP, "d_model %d", m->cfg.d_model);
+    }
+    FCK(cudaGetLastError());
+    return PT_OK;
+}
+
+template <int D>
+void launch_head_score(pt_former* m, const float* h, const int8_t* spins, float* lp, float* logits, size_t M) {
+    head_score_kernel<D><<<(unsigned)((M + 7) / 8), 256, 0, m->exec>>>(h, m->lnf_g, m->lnf_b, m->wout,
+                                                                         m->bout, spins, lp, logits, M);
+}
+template <int D>
+void launch_head_sample(pt_former* m, const int8_t* prefix, int npre, int8_t* out, float* logq, int B, int t) {
+    head_sample_kernel<D><<<(B + 7) / 8, 256, 0, m->exec>>>(m->step.h, m->lnf_g, m->lnf_b, m->wout, m->bout,
+                                                              prefix, npre, m->d_sargs, out, logq, B,
+                                                              m->cfg.n_spins, t);
+}
+
+// one pre-layer-norm block on rows [0, M) of `a` (attention by `attn`)
+template <class AttnFn>
+pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, AttnFn attn) {
+    const int d = m->cfg.d_model, F = m->cfg.d_ff;
+    pt_status s = layernorm(m, x.h, Ly.ln1_g, Ly.ln1_b, x.a, M);
+    if (s == PT_OK) s = gemm(m, x.qkv, x.a, Ly.w_qkv, Ly.b_qkv, M, 3 * d, d, false);
+    if (s == PT_OK) s = attn();
+    if (s == PT_OK) s = gemm(m, x.h, x.o, Ly.w_o, Ly.b_o, M, d, d, true);
+    if (s == PT_OK) s = layernorm(m, x.h, Ly.ln2_g, Ly.ln2_b, x.a, M);
+    if (s == PT_OK) s = gemm(m, x.f1, x.a, Ly.w_1, Ly.b_1, M, F, d, false);
+    if (s == PT_OK) {
+        const size_t n = M * (size_t)F;
+        gelu_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 32), 256, 0, m->exec>>>(x.f1, x.g, n);
+        FCK(cudaGetLastError());
+    }
+    if (s == PT_OK) s = gemm(m, x.h, x.g, Ly.w_2, Ly.b_2, M, d, F, true);
+    return s;
+}
+
+pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* prefix, int npre,
+                          int8_t* out, float* logq) {
+    const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
+    const size_t smem = (size_t)H * (kDH + N) * 4;
+    for (int t = 0; t < N; ++t) {
+        embed_step_kernel<<<B, 256, 0, m->exec>>>(out, beta, m->tok, m->wb, m->bb, m->pe, m->step.h, N, d, t);
+        FCK(cudaGetLastError());
+        for (int l = 0; l < m->cfg.n_layers; ++l) {
+            float* cl = m->cache + (size_t)l * B * N * 2 * d;
+            pt_status s = block(m, m->step, (size_t)B, m->layers[l], [&]() -> pt_status {
+                kv_append_kernel<<<B, 256, 0, m->exec>>>(m->step.qkv, cl, N, d, t);
+                attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(m->step.qkv, cl, m->step.o, N, d, t);
+                FCK(cudaGetLastError());
+                return PT_OK;
+            });
+            if (s != PT_OK) return s;
+        }
+        switch (d) {
+            case 64: launch_head_sample<64>(m, prefix, npre, out, logq, B, t); break;
+            case 128: launch_head_sample<128>(m, prefix, npre, out, logq, B, t); break;
+            case 256: launch_head_sample<256>(m, prefix, npre, out, logq, B, t); break;
+            case 512: launch_head_sample<512>(m, prefix, npre, out, logq, B, t); break;
+        }
+        FCK(cudaGetLastError());
+    }
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_former_last_error(void) { return g_ferr.c_str(); }
+
+size_t pt_former_param_count(const pt_former_config* c) {
+    if (!c) return 0;
+    const size_t d = c->d_model, F = c->d_ff;
+    const size_t per = 2 * d + 3 * d * d + 3 * d + d * d + d + 2 * d + d * F + F + F * d + d;
+    return 3 * d + 2 * d + (size_t)c->n_layers * per + 2 * d + 2 * d + 2;
+}
+
+pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const uint16_t* params,
+                           size_t n_params, void* cuda_stream) {
+    if (!out || !cfg || !params) return ffail(PT_EINVAL, "NULL argument");
+    *out = nullptr;
+    const int d = cfg->d_model, F = cfg->d_ff;
+    if (cfg->n_spins < 1 || cfg->n_layers < 0 || cfg->n_heads < 1 || d != 64 * cfg->n_heads ||
+        (d != 64 && d != 128 && d != 256 && d != 512) || F < 8 || F % 8 != 0)
+        return ffail(PT_EINVAL, "unsupported shape (d_model must be 64 x n_heads, one of 64..512; d_ff a multiple of 8)");
+    if (n_params != pt_former_param_count(cfg))
+        return ffail(PT_EINVAL, "%zu parameters given, the shape has %zu", n_params, pt_former_param_count(cfg));
+    pt_former* m = new pt_former();
+    m->cfg = *cfg;
+    m->stream = (cudaStream_t)cuda_stream;
+    m->exec = m->stream;
+    pt_status s = PT_OK;
+    if (cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        s = ffail(PT_ECUDA, "stream or event creation");
+    const uint16_t* p = params;
+    auto take = [&](size_t n) { const uint16_t* q = p; p += n; return q; };
+    if (cublasLtCreate(&m->lt) != CUBLAS_STATUS_SUCCESS) s = ffail(PT_ECUDA, "cublasLtCreate");
+    if (s == PT_OK && cudaMalloc(&m->workspace, m->ws_bytes) != cudaSuccess) s = ffail(PT_ENOMEM, "workspace");
+    if (s == PT_OK) s = upload_f32(m, &m->tok, take(3 * (size_t)d), 3 * (size_t)d);
+    if (s == PT_OK) s = upload_f32(m, &m->wb, take(d), d);
+    if (s == PT_OK) s = upload_f32(m, &m->bb, take(d), d);
+    m->layers.resize(cfg->n_layers);
+    for (int l = 0; l < cfg->n_layers && s == PT_OK; ++l) {
+        Layer& L = m->layers[l];
+        s = upload_f32(m, &L.ln1_g, take(d), d);
+        if (s == PT_OK) s = upload_f32(m, &L.ln1_b, take(d), d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_qkv, take(3 * (size_t)d * d), 3 * (size_t)d * d);
+        if (s == PT_OK) s = upload_f32(m, &L.b_qkv, take(3 * (size_t)d), 3 * (size_t)d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_o, take((size_t)d * d), (size_t)d * d);
+        if (s == PT_OK) s = upload_f32(m, &L.b_o, take(d), d);
+        if (s == PT_OK) s = upload_f32(m, &L.ln2_g, take(d), d);
+        if (s == PT_OK) s = upload_f32(m, &L.ln2_b, take(d), d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_1, take((size_t)d * F), (size_t)d * F);
+        if (s == PT_OK) s = upload_f32(m, &L.b_1, take(F), F);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_2, take((size_t)F * d), (size_t)F * d);
+        if (s == PT_OK) s = upload_f32(m, &L.b_2, take(d), d);
+    }
+    if (s == PT_OK) s = upload_f32(m, &m->lnf_g, take(d), d);
+    if (s == PT_OK) s = upload_f32(m, &m->lnf_b, take(d), d);
+    if (s == PT_OK) s = upload_f32(m, &m->wout, take(2 * (size_t)d), 2 * (size_t)d);
+    if (s == PT_OK) s = upload_f32(m, &m->bout, take(2), 2);
+    if (s == PT_OK) {
+        // positional code PE[t, 2i] = sin(t / 10000^(2i/d)), PE[t, 2i+1] = cos(...), in FP64
+        const int N = cfg->n_spins;
+        std::vector<float> pe((size_t)N * d);
+        for (int t = 0; t < N; ++t)
+            for (int i = 0; i < d / 2; ++i) {
+                const double ang = t / std::pow(10000.0, 2.0 * i / d);
+                pe[(size_t)t * d + 2 * i] = (float)std::sin(ang);
+                pe[(size_t)t * d + 2 * i + 1] = (float)std::cos(ang);
+            }
+        s = dalloc(m, &m->pe, pe.size());
+        if (s == PT_OK && cudaMemcpy(m->pe, pe.data(), pe.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            s = ffail(PT_ECUDA, "positional code upload");
+    }
+    if (s == PT_OK) s = dalloc(m, &m->d_sargs, 1);
+    if (s != PT_OK) {
+        pt_former_destroy(m);
+        return s;
+    }
+    *out = m;
+    return PT_OK;
+}
+
+pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const float* beta,
+                          float* logq, float* logits) {
+    if (!m || !spins || !beta || !logq) return ffail(PT_EINVAL, "NULL argument");
+    if (B < 1) return ffail(PT_EINVAL, "B must be >= 1");
+    const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
+    const size_t M = (size_t)B * N;
+    pt_status s = ensure_act(m, m->score, M);
+    if (s != PT_OK) return s;
+    Act& x = m->score;
+    embed_score_kernel<<<(unsigned)M, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, x.h, N, d);
+    FCK(cudaGetLastError());
+    for (int l = 0; l < m->cfg.n_layers && s == PT_OK; ++l) {
+        s = block(m, x, M, m->layers[l], [&]() -> pt_status {
+            attention_kernel<<<dim3((N + kAQ - 1) / kAQ, H, B), kAQ, 0, m->exec>>>(x.qkv, x.o, N, d);
+            FCK(cudaGetLastError());
+            return PT_OK;
+        });
+    }
+    if (s != PT_OK) return s;
+    switch (d) {
+        case 64: launch_head_score<64>(m, x.h, spins, x.lp, logits, M); break;
+        case 128: launch_head_score<128>(m, x.h, spins, x.lp, logits, M); break;
+        case 256: launch_head_score<256>(m, x.h, spins, x.lp, logits, M); break;
+        case 512: launch_head_score<512>(m, x.h, spins, x.lp, logits, M); break;
+    }
+    FCK(cudaGetLastError());
+    sum_rows_kernel<<<(B + 7) / 8, 256, 0, m->exec>>>(x.lp, logq, B, N);
+    FCK(cudaGetLastError());
+    return PT_OK;
+}
+
+pt_status pt_former_sample(pt_former* m, int32_t B, const float* beta, const int8_t* prefix,
+                           int32_t n_prefix, uint64_t seed, uint32_t stream_id, int8_t* out,
+                           float* logq) {
+    if (!m || !beta || !out) return ffail(PT_EINVAL, "NULL argument");
+    const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
+    if (B < 1) return ffail(PT_EINVAL, "B must be >= 1");
+    if (n_prefix < 0 || n_prefix > N || (n_prefix > 0 && !prefix))
+        return ffail(PT_EINVAL, "n_prefix must be in [0, N], with a prefix array when > 0");
+    if ((size_t)H * (kDH + N) * 4 > 48 * 1024)
+        return ffail(PT_ENOTSUP, "sampling keeps per-head scores of N = %d positions in shared memory; N too large", N);
+    pt_status s = ensure_act(m, m->step, (size_t)B);
+    if (s != PT_OK) return s;
+    if (m->cache_B < B) {
+        if (m->cache) cudaFree(m->cache);
+        m->cache = nullptr;
+        m->cache_B = 0;
+        FCK(cudaMalloc(&m->cache, (size_t)std::max(m->cfg.n_layers, 1) * B * N * 2 * d * 4));
+        m->cache_B = B;
+        if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
+    }
+    const SampleArgs sa{seed, stream_id};
+    FCK(cudaMemcpyAsync(m->d_sargs, &sa, sizeof sa, cudaMemcpyHostToDevice, m->stream));
+    const auto key = std::make_tuple((int)B, (int)n_prefix, (const void*)beta, (const void*)prefix,
+                                     (const void*)out, (const void*)logq);
+    if (!m->gexec || m->gkey != key) {
+        if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
+        // the first call of each shape launches directly (which also finds the cuBLASLt
+        // algorithms), then captures the same launches on the private stream for later calls
+        s = sample_launches(m, B, beta, prefix, n_prefix, out, logq);
+        if (s != PT_OK) return s;
+        cudaGraph_t g = nullptr;
+        m->exec = m->cap;
+        cudaError_t e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = sample_launches(m, B, beta, prefix, n_prefix, out, logq);
+            e = cudaStreamEndCapture(m->cap, &g);
+        }
+        m->exec = m->stream;
+        if (s != PT_OK) { if (g) cudaGraphDestroy(g); return s; }
+        if (e != cudaSuccess) return ffail(PT_ECUDA, "capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&m->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return ffail(PT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        m->gkey = key;
+        return PT_OK;            // this call's sample came from the direct launches
+    }
+    // replay on the private stream, ordered after and before the caller's stream
+    FCK(cudaEventRecord(m->ev_in, m->stream));
+    FCK(cudaStreamWaitEvent(m->cap, m->ev_in, 0));
+    FCK(cudaGraphLaunch(m->gexec, m->cap));
+    FCK(cudaEventRecord(m->ev_out, m->cap));
+    FCK(cudaStreamWaitEvent(m->stream, m->ev_out, 0));
+    return PT_OK;
+}
+
+double pt_former_score_gemm_flops(const pt_former* m, int32_t B) {
+    if (!m) return 0.0;
+    const double M = (double)B * m->cfg.n_spins, d = m->cfg.d_model, F = m->cfg.d_ff;
+    return m->cfg.n_layers * 2.0 * M * (d * 3 * d + d * d + d * F + F * d);
+}
+
+pt_status pt_former_destroy(pt_former* m) {
+    if (!m) return PT_OK;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    else cudaDeviceSynchronize();
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    free_act(m->score);
+    free_act(m->step);
+    if (m->cache) cudaFree(m->cache);
+    for (void* p : m->allocs) cudaFree(p);
+    if (m->workspace) cudaFree(m->workspace);
+    if (m->lt) cublasLtDestroy(m->lt);
+    if (m->cap) { cudaStreamSynchronize(m->cap); cudaStreamDestroy(m->cap); }
+    if (m->ev_in) cudaEventDestroy(m->ev_in);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    delete m;
+    return PT_OK;
+}
+
+}  // extern "C"

@@ -31,3 +31,14 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     assert pt.lib() is not None
     assert isinstance(pt.last_error(), str)
+
+
+def test_former_library_exports_every_declared_symbol():
+    # the IsingFormer inference library (include/pt_former.h) builds, loads and exports its ABI
+    src = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "pt_former.h").read_text(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(pt_former_[a-z_]+)\s*\(", src)))
+    assert "pt_former_score" in names and "pt_former_sample" in names
+    B.build()
+    lib = ctypes.CDLL(str(B.FORMER_LIB))
+    for name in names:
+        assert hasattr(lib, name), name

@@ -1,0 +1,105 @@
+"""IsingFormer inference on the GPU (libptformer.so) against the float64 oracle
+(oracle/former.py), at the paper's spin-glass and factorization shape (d_model 256, 4
+heads, 5 layers, FFN 1024; Methods and Supplementary S6) with seeded bfloat16 weights.
+
+Tolerance. The GPU rounds every matrix-product input (layer-norm, attention and GELU
+outputs) to bfloat16, a relative error of at most 2^-9 each, and accumulates in FP32; the
+oracle keeps float64 throughout. Over 5 residual blocks these roundings leave logit errors of
+order 1e-2; the bound used is 0.05 + 0.02 |logit|, and for log q, a sum of N
+log-probabilities whose errors add with random signs, 0.02 sqrt(N) + 0.01 |log q|."""
+import numpy as np
+import pytest
+
+import instances as I
+import oracle as O
+from oracle import former as F
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _model(N, index=0, shape=None):
+    from paper_2509_23043_gb300.former import Former
+    shp = shape or I.FormerShape(n_spins=N)
+    W, packed = I.former_weights(shp, index=index)
+    return shp, W, Former(shp, packed)
+
+
+@pytest.mark.parametrize("N,B", [(37, 6), (200, 4), (300, 3)])
+def test_score_matches_oracle(N, B):
+    shp, W, m = _model(N, index=N)
+    g = np.random.default_rng(N)
+    X = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
+    beta = g.uniform(0.1, 3.0, B)
+    lq, lg = m.score(torch.from_numpy(X).cuda(), torch.from_numpy(beta.astype(np.float32)).cuda(), logits=True)
+    lg_o, lq_o = F.score(W, shp, X, beta.astype(np.float32).astype(np.float64))
+    lg, lq = lg.cpu().numpy().astype(np.float64), lq.cpu().numpy().astype(np.float64)
+    err = np.abs(lg - lg_o)
+    print("max logit error", err.max(), "max |logit|", np.abs(lg_o).max(), "log q errors", np.abs(lq - lq_o))
+    assert np.all(err <= 0.05 + 0.02 * np.abs(lg_o)), err.max()
+    assert np.all(np.abs(lq - lq_o) <= 0.02 * np.sqrt(N) + 0.01 * np.abs(lq_o)), (lq, lq_o)
+
+
+def _philox_u(seed, t, b, stream):
+    w = O.philox([t, b, 6 << 24, stream], [seed & 0xFFFFFFFF, seed >> 32])[0]
+    return (int(w) >> 8) * 2.0 ** -24
+
+
+def test_sampling_matches_the_oracle_decisions():
+    # every drawn spin is the threshold decision of the oracle's q(+1 | prefix) at the GPU's
+    # own prefix, except within 0.02 of a tie; the first spins are the given prefix; the log q
+    # the sampler reports (key/value-cache path) agrees with the scoring pass
+    N, B, npre, seed, sid = 40, 24, 5, 0x1234_5678_9ABC, 7
+    shp, W, m = _model(N, index=3)
+    g = np.random.default_rng(11)
+    beta = g.uniform(0.2, 2.5, B).astype(np.float32)
+    pre = np.where(g.random((B, npre)) < 0.5, 1, -1).astype(np.int8)
+    bt, pt_ = torch.from_numpy(beta).cuda(), torch.from_numpy(pre).cuda()
+    out = torch.empty((B, N), dtype=torch.int8, device="cuda")
+    lq = torch.empty(B, dtype=torch.float32, device="cuda")
+    m.sample(bt, seed, sid, prefix=pt_, out=out, logq=lq)
+    S = out.cpu().numpy()
+    assert np.array_equal(S[:, :npre], pre)
+    assert set(np.unique(S)) <= {-1, 1}
+    lg_o, lq_o = F.score(W, shp, S, beta.astype(np.float64))
+    p_plus = np.exp(F.log_softmax2(lg_o)[..., 1])
+    near = 0
+    for b in range(B):
+        for t in range(npre, N):
+            u = _philox_u(seed, t, b, sid)
+            if abs(u - p_plus[b, t]) < 0.02:
+                near += 1
+                continue
+            assert S[b, t] == (1 if u < p_plus[b, t] else -1), (b, t, u, p_plus[b, t])
+    assert near < 0.05 * B * (N - npre)
+    lq_gpu = lq.cpu().numpy().astype(np.float64)
+    lq_s = m.score(torch.from_numpy(S).cuda(), bt).cpu().numpy().astype(np.float64)
+    assert np.allclose(lq_gpu, lq_s, atol=1e-3 * np.sqrt(N), rtol=1e-4), (lq_gpu, lq_s)
+    assert np.all(np.abs(lq_gpu - lq_o) <= 0.02 * np.sqrt(N) + 0.01 * np.abs(lq_o))
+    # later calls with the same arrays replay the captured graph: the same seed gives the same
+    # draw, another seed another one
+    m.sample(bt, seed, sid, prefix=pt_, out=out, logq=lq)
+    assert np.array_equal(out.cpu().numpy(), S)
+    assert np.allclose(lq.cpu().numpy(), lq_gpu, atol=0, rtol=0)
+    m.sample(bt, seed + 1, sid, prefix=pt_, out=out, logq=lq)
+    assert not np.array_equal(out.cpu().numpy(), S)
+
+
+def test_sampled_frequencies_follow_q():
+    # a small model (d 64, one head, 2 layers) over N = 6 spins: the frequencies of 40000
+    # GPU draws follow the exact q(x | beta) of the oracle over all 64 configurations, within
+    # 5 sigma of the multinomial noise (plus the bfloat16 model error, below 1e-2 in total
+    # variation on these weights)
+    shp = I.FormerShape(n_spins=6, d_model=64, n_heads=1, n_layers=2, d_ff=128)
+    shp, W, m = _model(6, index=5, shape=shp)
+    X = np.array([[1 if (k >> (5 - i)) & 1 else -1 for i in range(6)] for k in range(64)], np.int8)
+    _, lq = F.score(W, shp, X, np.full(64, 1.4))
+    q = np.exp(lq)
+    n = 40000
+    S, _ = m.sample(torch.full((n,), 1.4, dtype=torch.float32, device="cuda"), 99, 0)
+    S = S.cpu().numpy()
+    code = ((S > 0).astype(np.int64) << np.arange(6)[::-1]).sum(1)
+    emp = np.bincount(code, minlength=64) / n
+    tv = 0.5 * np.abs(emp - q).sum()
+    assert tv < 5 * 0.5 * np.sum(np.sqrt(q * (1 - q) / n)) + 0.01, tv
