@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--serve-pool-gap", type=int, default=100)
     p.add_argument("--serve-hbm-frac", type=float, default=0.5,
                    help="device-memory budget of admitted requests, as a fraction of all slots")
+    p.add_argument("--profile-case", choices=("lattice", "lattice-gibbs", "graph", "former"),
+                   help="run one small case for a profiler capture and exit (no timing, no JSON)")
     p.add_argument("--cpu-sample-instances", type=int, default=16)
     p.add_argument("--cpu-sample-sweeps", type=int, default=60)
     return p.parse_args()
@@ -1107,11 +1109,71 @@ def run_reference(args):
     }), flush=True)
 
 
+# ------------------------------------------------------------------------------ profiler cases
+def profile_case(kind):
+    """Small cases for ncu captures (the commands are in profiles/). lattice, lattice-gibbs:
+    the benchmark workload (256 EA L=10, R=32, proposals every 10 from sweep 100) with random
+    pools of 1024 entries (1 GB, larger than L2), one launch at creation then four of 100
+    cycles. graph: 1000 clamped 8x8 multipliers, Gibbs, pools of 16, one launch at creation
+    then three of 1000 cycles. former: three IsingFormer scoring passes over 1024
+    configurations of N = 200."""
+    import torch
+    import instances as I
+    import paper_2509_23043_gb300 as pt
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(1)
+    if kind.startswith("lattice"):
+        class A:
+            L, R, threads = 10, 32, 0
+        n, P, L, R = 256, 1024, 10, 32
+        insts, betas, prop, ids = workload(A, 0, n)
+        cfg = pt.Config(update=1 if kind == "lattice-gibbs" else 0, sweeps_per_cycle=1, propose_every=10,
+                        propose_start=100, pool_size=P, seed=0x7A972509)
+        ctx = pt.create_instances(insts, betas, cfg, prop_enabled=prop, instance_ids=ids)
+        nw = (L ** 3 + 31) // 32
+        for e0 in range(0, P, 64):
+            words = rng.integers(0, 2 ** 32, size=(64, n, R, nw), dtype=np.uint64).astype(np.uint32)
+            pt.load_proposals_packed(ctx, words, e0, 64)
+            torch.cuda.synchronize()
+        for _ in range(4):
+            pt.run_cycles(ctx, 100)
+        out = pt.energies(ctx)[:4]
+    elif kind == "graph":
+        nB, R, P = 1000, 32, 16
+        mult = I.multiplier(8)
+        insts = [mult.instance(C) for C, _, _ in I.draw_prime_products(nB)]
+        betas = I.geometric_betas(0.05, 5.0, R)
+        cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+        ctx = pt.create_instances(insts, [betas] * nB, cfg, prop_enabled=[[1] * 23 + [0] * (R - 23)] * nB,
+                                  instance_ids=list(range(nB)))
+        nw = (mult.n_spins + 31) // 32
+        words = rng.integers(0, 2 ** 32, size=(P, nB, R, nw), dtype=np.uint64).astype(np.uint32)
+        pt.load_proposals_packed(ctx, words, 0, P)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            pt.run_cycles(ctx, 1000)
+        out = pt.energies(ctx)[:4]
+    else:
+        from paper_2509_23043_gb300.former import Former
+        shp = I.FormerShape(n_spins=200)
+        _, packed = I.former_weights(shp)
+        m = Former(shp, packed)
+        X = torch.from_numpy(np.where(rng.random((1024, 200)) < 0.5, 1, -1).astype(np.int8)).cuda()
+        beta = torch.full((1024,), 1.0, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            lq = m.score(X, beta)
+        out = lq[:4].cpu().numpy()
+    torch.cuda.synchronize()
+    print("profile case", kind, "ok", out)
+
+
 # ------------------------------------------------------------------------------ our arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args.profile_case)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

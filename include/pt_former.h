@@ -36,13 +36,18 @@ typedef struct pt_former pt_former;
 
 /* Model shape (the paper's spin-glass and factorization model: d_model 256, 4 heads, 5
  * layers, FFN 1024). n_spins N >= 1 is the sequence length; d_model a multiple of 64 and of
- * n_heads with d_model / n_heads = 64; d_ff a multiple of 8; n_layers >= 0. */
+ * n_heads with d_model / n_heads = 64; d_ff a multiple of 8; n_layers >= 0.
+ * attn_mode selects the scoring pass's attention: 0 = automatic (on the tensor cores, as
+ * batched bfloat16 products around a causal-softmax kernel, when the scores and probabilities
+ * of one layer, 6 B H N^2 bytes, fit 2 GiB; else the streaming kernel), 1 = always the
+ * streaming kernel (FP32, keys and values streamed through shared memory, softmax online). */
 typedef struct {
     int32_t n_spins;
     int32_t d_model;
     int32_t n_heads;
     int32_t n_layers;
     int32_t d_ff;
+    int32_t attn_mode;
 } pt_former_config;
 
 /* Number of bfloat16 parameters of a shape: 3d + 2d (embeddings), per layer

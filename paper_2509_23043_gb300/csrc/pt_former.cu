@@ -184,6 +184,43 @@ __global__ void __launch_bounds__(kAQ) attention_kernel(const float* __restrict_
     }
 }
 
+// Scoring attention on the tensor cores: Q (scaled by 1/sqrt(64), exact in bfloat16), K and V
+// of every head to bfloat16, head-major [B][H][N][64], the operands of the batched products
+__global__ void split_heads_kernel(const float* __restrict__ qkv, __nv_bfloat16* __restrict__ qh,
+                                   __nv_bfloat16* __restrict__ kh, __nv_bfloat16* __restrict__ vh,
+                                   int N, int d, int H) {
+    const size_t row = blockIdx.x;                      // b N + t
+    const int b = (int)(row / N), t = (int)(row - (size_t)b * N);
+    const float* r = qkv + row * 3 * d;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        const int hd = c / kDH, e = c - hd * kDH;
+        const size_t o = (((size_t)b * H + hd) * N + t) * kDH + e;
+        qh[o] = __float2bfloat16_rn(r[c] * 0.125f);
+        kh[o] = __float2bfloat16_rn(r[d + c]);
+        vh[o] = __float2bfloat16_rn(r[2 * d + c]);
+    }
+}
+
+// causal softmax of each score row S[bh][i][0..i] (one warp per row), to bfloat16 P with the
+// masked entries j > i set to 0 (the next product reads whole rows)
+__global__ void causal_softmax_kernel(const float* __restrict__ S, __nv_bfloat16* __restrict__ P,
+                                      size_t rows, int N) {
+    const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const int i = (int)(row % N);
+    const float* sr = S + row * N;
+    __nv_bfloat16* pr = P + row * N;
+    float mx = -INFINITY;
+    for (int j = lane; j <= i; j += 32) mx = fmaxf(mx, sr[j]);
+    mx = warp_max(mx);
+    float sum = 0.f;
+    for (int j = lane; j <= i; j += 32) sum += expf(sr[j] - mx);
+    const float inv = 1.f / warp_sum(sum);
+    for (int j = lane; j < N; j += 32)
+        pr[j] = __float2bfloat16_rn(j <= i ? expf(sr[j] - mx) * inv : 0.f);
+}
+
 // append the keys and values of step t to the cache [B][N][2d] of one layer
 __global__ void kv_append_kernel(const float* __restrict__ qkv, float* __restrict__ cache, int N, int d, int t) {
     const int b = blockIdx.x;
@@ -358,6 +395,10 @@ struct Act {                       // activation buffers for `rows` rows
     size_t rows = 0;
     float *h = nullptr, *qkv = nullptr, *f1 = nullptr, *lp = nullptr;
     __nv_bfloat16 *a = nullptr, *o = nullptr, *g = nullptr;
+    // scoring attention on the tensor cores: head-major operands, scores, probabilities
+    size_t att_elems = 0;           // B H N N
+    __nv_bfloat16 *qh = nullptr, *kh = nullptr, *vh = nullptr, *P = nullptr;
+    float* S = nullptr;
 };
 
 }  // namespace
@@ -414,7 +455,30 @@ pt_status upload_bf16(pt_former* m, __nv_bfloat16** dst, const uint16_t* src, si
 void free_act(Act& a) {
     cudaFree(a.h); cudaFree(a.qkv); cudaFree(a.f1); cudaFree(a.lp);
     cudaFree(a.a); cudaFree(a.o); cudaFree(a.g);
+    cudaFree(a.qh); cudaFree(a.kh); cudaFree(a.vh); cudaFree(a.P); cudaFree(a.S);
     a = Act{};
+}
+
+// the scores and probabilities of one layer's attention, B H N^2 entries of 6 bytes, are kept
+// when they fit this budget; longer sequences use the streaming attention kernel
+constexpr size_t kAttScratchBytes = size_t(2) << 30;
+
+pt_status ensure_att(pt_former* m, Act& a, int B) {
+    const size_t N = m->cfg.n_spins, H = m->cfg.n_heads, d = m->cfg.d_model;
+    const size_t elems = (size_t)B * H * N * N;
+    if (a.att_elems >= elems) return PT_OK;
+    cudaFree(a.qh); cudaFree(a.kh); cudaFree(a.vh); cudaFree(a.P); cudaFree(a.S);
+    a.qh = a.kh = a.vh = a.P = nullptr;
+    a.S = nullptr;
+    a.att_elems = 0;
+    const size_t rows = (size_t)B * N;
+    FCK(cudaMalloc(&a.qh, rows * d * 2));
+    FCK(cudaMalloc(&a.kh, rows * d * 2));
+    FCK(cudaMalloc(&a.vh, rows * d * 2));
+    FCK(cudaMalloc(&a.S, elems * 4));
+    FCK(cudaMalloc(&a.P, elems * 2));
+    a.att_elems = elems;
+    return PT_OK;
 }
 
 pt_status ensure_act(pt_former* m, Act& a, size_t rows) {
@@ -473,6 +537,73 @@ pt_status gemm(pt_former* m, float* Y, const __nv_bfloat16* X, const __nv_bfloat
     cublasLtMatmulDescDestroy(op);
     if (st != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "cublasLtMatmul: status %d", (int)st);
     return PT_OK;
+}
+
+// Strided-batched product on the tensor cores, column-major views: C [m][n] (type ct, leading
+// dimension ldc, batch stride sc) = op(A) [m][k] op(B) [k][n], bfloat16 operands, FP32
+// accumulation, no epilogue.
+pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const void* A, int lda, long long sa,
+                       const void* Bm, int ldb, long long sb, void* C, cudaDataType_t ct, int ldc,
+                       long long sc, int mm, int nn, int kk, int batch) {
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
+    LCK(cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F));
+    const cublasOperation_t nt = CUBLAS_OP_N;
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof ta));
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &nt, sizeof nt));
+    const int arows = ta == CUBLAS_OP_N ? mm : kk, acols = ta == CUBLAS_OP_N ? kk : mm;
+    LCK(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, arows, acols, lda));
+    LCK(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, kk, nn, ldb));
+    LCK(cublasLtMatrixLayoutCreate(&lc, ct, mm, nn, ldc));
+    for (auto [l, st] : {std::make_pair(la, sa), std::make_pair(lb, sb), std::make_pair(lc, sc)}) {
+        LCK(cublasLtMatrixLayoutSetAttribute(l, CUBLASLT_MATRIX_LAYOUT_BATCH_COUNT, &batch, sizeof batch));
+        LCK(cublasLtMatrixLayoutSetAttribute(l, CUBLASLT_MATRIX_LAYOUT_STRIDED_BATCH_OFFSET, &st, sizeof st));
+    }
+    const auto key = std::make_tuple((size_t)batch * 1000003 + (size_t)kk, mm, nn, ct == CUDA_R_32F ? 2 : 3);
+    auto it = m->algos.find(key);
+    if (it == m->algos.end()) {
+        cublasLtMatmulPreference_t pref = nullptr;
+        LCK(cublasLtMatmulPreferenceCreate(&pref));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES,
+                                                 &m->ws_bytes, sizeof m->ws_bytes));
+        cublasLtMatmulHeuristicResult_t res{};
+        int got = 0;
+        LCK(cublasLtMatmulAlgoGetHeuristic(m->lt, op, la, lb, lc, lc, pref, 1, &res, &got));
+        cublasLtMatmulPreferenceDestroy(pref);
+        if (got < 1) return ffail(PT_ENOTSUP, "no cuBLASLt algorithm for the batched %d x %d x %d", mm, nn, kk);
+        it = m->algos.emplace(key, res.algo).first;
+    }
+    const float one = 1.f, zero = 0.f;
+    const cublasStatus_t st = cublasLtMatmul(m->lt, op, &one, A, la, Bm, lb, &zero, C, lc, C, lc,
+                                             &it->second, m->workspace, m->ws_bytes, m->exec);
+    cublasLtMatrixLayoutDestroy(la);
+    cublasLtMatrixLayoutDestroy(lb);
+    cublasLtMatrixLayoutDestroy(lc);
+    cublasLtMatmulDescDestroy(op);
+    if (st != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "batched cublasLtMatmul: status %d", (int)st);
+    return PT_OK;
+}
+
+// Causal attention of the scoring pass on the tensor cores: S = Q K^T for every
+// (configuration, head) in one batched product (row-major S [N][N] is the column-major
+// S^T = K Q^T), the causal softmax, then O = P V per head, batched over configurations
+// (O^T = V^T P^T, written into the heads' columns of the [B N][d] output).
+pt_status attention_tc(pt_former* m, Act& x, int B) {
+    const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
+    const long long hs = (long long)N * kDH;           // one head's [N][64] block
+    split_heads_kernel<<<(unsigned)((size_t)B * N), 256, 0, m->exec>>>(x.qkv, x.qh, x.kh, x.vh, N, d, H);
+    FCK(cudaGetLastError());
+    pt_status s = gemm_batched(m, CUBLAS_OP_T, x.kh, kDH, hs, x.qh, kDH, hs, x.S, CUDA_R_32F, N,
+                               (long long)N * N, N, N, kDH, B * H);
+    if (s != PT_OK) return s;
+    const size_t rows = (size_t)B * H * N;
+    causal_softmax_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    FCK(cudaGetLastError());
+    for (int hd = 0; hd < H && s == PT_OK; ++hd)
+        s = gemm_batched(m, CUBLAS_OP_N, x.vh + (size_t)hd * hs, kDH, (long long)H * hs,
+                         x.P + (size_t)hd * N * N, N, (long long)H * N * N, x.o + (size_t)hd * kDH,
+                         CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B);
+    return s;
 }
 
 template <int D>
@@ -572,7 +703,8 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
     *out = nullptr;
     const int d = cfg->d_model, F = cfg->d_ff;
     if (cfg->n_spins < 1 || cfg->n_layers < 0 || cfg->n_heads < 1 || d != 64 * cfg->n_heads ||
-        (d != 64 && d != 128 && d != 256 && d != 512) || F < 8 || F % 8 != 0)
+        (d != 64 && d != 128 && d != 256 && d != 512) || F < 8 || F % 8 != 0 ||
+        cfg->attn_mode < 0 || cfg->attn_mode > 1)
         return ffail(PT_EINVAL, "unsupported shape (d_model must be 64 x n_heads, one of 64..512; d_ff a multiple of 8)");
     if (n_params != pt_former_param_count(cfg))
         return ffail(PT_EINVAL, "%zu parameters given, the shape has %zu", n_params, pt_former_param_count(cfg));
@@ -646,8 +778,14 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
     Act& x = m->score;
     embed_score_kernel<<<(unsigned)M, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, x.h, N, d);
     FCK(cudaGetLastError());
+    const bool tc = m->cfg.attn_mode == 0 && (size_t)B * H * N * N * 6 <= kAttScratchBytes;
+    if (tc) {
+        s = ensure_att(m, x, B);
+        if (s != PT_OK) return s;
+    }
     for (int l = 0; l < m->cfg.n_layers && s == PT_OK; ++l) {
         s = block(m, x, M, m->layers[l], [&]() -> pt_status {
+            if (tc) return attention_tc(m, x, B);
             attention_kernel<<<dim3((N + kAQ - 1) / kAQ, H, B), kAQ, 0, m->exec>>>(x.qkv, x.o, N, d);
             FCK(cudaGetLastError());
             return PT_OK;

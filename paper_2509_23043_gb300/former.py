@@ -19,7 +19,7 @@ _lib = None
 
 class _Cfg(C.Structure):
     _fields_ = [("n_spins", C.c_int32), ("d_model", C.c_int32), ("n_heads", C.c_int32),
-                ("n_layers", C.c_int32), ("d_ff", C.c_int32)]
+                ("n_layers", C.c_int32), ("d_ff", C.c_int32), ("attn_mode", C.c_int32)]
 
 
 def lib():
@@ -57,10 +57,12 @@ def _dp(t):
 class Former:
     """One IsingFormer on the current CUDA device and stream."""
 
-    def __init__(self, shape, packed_params: np.ndarray, stream=None):
+    def __init__(self, shape, packed_params: np.ndarray, stream=None, attn_mode: int = 0):
+        """attn_mode 0: scoring attention on the tensor cores where its scores fit, else the
+        streaming kernel; 1: always the streaming kernel."""
         import torch
         self.shape = shape
-        self.cfg = _Cfg(shape.n_spins, shape.d_model, shape.n_heads, shape.n_layers, shape.d_ff)
+        self.cfg = _Cfg(shape.n_spins, shape.d_model, shape.n_heads, shape.n_layers, shape.d_ff, attn_mode)
         p = np.ascontiguousarray(packed_params, dtype=np.uint16)
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         h = C.c_void_p()

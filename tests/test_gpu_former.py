@@ -19,16 +19,18 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _model(N, index=0, shape=None):
+def _model(N, index=0, shape=None, attn_mode=0):
     from paper_2509_23043_gb300.former import Former
     shp = shape or I.FormerShape(n_spins=N)
     W, packed = I.former_weights(shp, index=index)
-    return shp, W, Former(shp, packed)
+    return shp, W, Former(shp, packed, attn_mode=attn_mode)
 
 
+@pytest.mark.parametrize("attn_mode", [0, 1])
 @pytest.mark.parametrize("N,B", [(37, 6), (200, 4), (300, 3)])
-def test_score_matches_oracle(N, B):
-    shp, W, m = _model(N, index=N)
+def test_score_matches_oracle(N, B, attn_mode):
+    # attn_mode 0: attention as batched tensor-core products; 1: the streaming FP32 kernel
+    shp, W, m = _model(N, index=N, attn_mode=attn_mode)
     g = np.random.default_rng(N)
     X = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
     beta = g.uniform(0.1, 3.0, B)
@@ -51,7 +53,7 @@ def test_sampling_matches_the_oracle_decisions():
     # own prefix, except within 0.02 of a tie; the first spins are the given prefix; the log q
     # the sampler reports (key/value-cache path) agrees with the scoring pass
     N, B, npre, seed, sid = 40, 24, 5, 0x1234_5678_9ABC, 7
-    shp, W, m = _model(N, index=3)
+    shp, W, m = _model(N, index=3, attn_mode=1)   # the scoring pass with FP32 attention, as the sampler's
     g = np.random.default_rng(11)
     beta = g.uniform(0.2, 2.5, B).astype(np.float32)
     pre = np.where(g.random((B, npre)) < 0.5, 1, -1).astype(np.int8)
