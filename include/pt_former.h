@@ -12,9 +12,12 @@
  * norm and a linear head to two logits. Layer norms use eps = 1e-5.
  *
  * Numerics: weight matrices in bfloat16; each matrix product takes bfloat16 inputs and
- * accumulates in FP32 (tensor cores); embeddings, layer norms, attention, softmax, GELU and
- * the head run in FP32. The projections run as cuBLASLt matrix products with a bias (and
- * residual) epilogue; every other step runs in this library's kernels.
+ * accumulates in FP32 (tensor cores). The residual stream is FP32; the outputs of the first
+ * FFN map (GELU evaluated in FP32 and stored in place) and, for the tensor-core attention,
+ * the queries, keys, values and softmax probabilities are stored in bfloat16. Embeddings,
+ * layer norms, softmax and the head compute in FP32. The projections run as cuBLASLt matrix
+ * products with a bias (and residual) epilogue; every other step runs in this library's
+ * kernels.
  *
  * Conventions: every device pointer is caller-owned device memory on the device of the
  * context, read or written in stream order on the context's stream; host pointers are read

@@ -4,18 +4,22 @@
 //
 // Layout (row-major, one row per (configuration, position) for scoring, per configuration
 // for a sampling step): residual stream h FP32 [M][d]; layer-norm outputs, attention outputs
-// and GELU outputs bfloat16 (the inputs of the matrix products); query/key/value and the
-// first FFN map FP32. The matrix products run on the tensor cores through cuBLASLt (bfloat16
-// inputs, FP32 accumulation, bias and residual in the epilogue); the rest are the kernels
-// below. Sampling keeps an FP32 key/value cache [layer][B][N][2d].
+// and the first FFN map (GELU applied in place) bfloat16, the inputs of the next matrix
+// products; query/key/value bfloat16 [M][3d] for the tensor-core attention of the scoring
+// pass, FP32 for the streaming kernel and the sampler. The matrix products run on the tensor
+// cores through cuBLASLt (bfloat16 inputs, FP32 accumulation, bias and residual in the
+// epilogue); the rest are the kernels below. Sampling keeps an FP32 key/value cache
+// [layer][B][N][2d].
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <tuple>
@@ -121,11 +125,22 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
     }
 }
 
-// y = GELU(x) = x (1 + erf(x / sqrt 2)) / 2, to bfloat16
-__global__ void gelu_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float v = x[i];
-        y[i] = __float2bfloat16_rn(0.5f * v * (1.f + erff(v * 0.70710678118654752f)));
+// y = GELU(y) = y (1 + erf(y / sqrt 2)) / 2 in place on bfloat16, evaluated in FP32; eight
+// values (16 bytes) per access, n8 = n / 8
+__device__ __forceinline__ float gelu_erf(float v) {
+    return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+}
+__global__ void gelu_kernel(__nv_bfloat16* __restrict__ y, size_t n8) {
+    uint4* p = reinterpret_cast<uint4*>(y);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+        uint4 w = p[i];
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            h[k] = __floats2bfloat162_rn(gelu_erf(f.x), gelu_erf(f.y));
+        }
+        p[i] = w;
     }
 }
 
@@ -184,26 +199,44 @@ __global__ void __launch_bounds__(kAQ) attention_kernel(const float* __restrict_
     }
 }
 
-// Scoring attention on the tensor cores: Q (scaled by 1/sqrt(64), exact in bfloat16), K and V
-// of every head to bfloat16, head-major [B][H][N][64], the operands of the batched products
-__global__ void split_heads_kernel(const float* __restrict__ qkv, __nv_bfloat16* __restrict__ qh,
-                                   __nv_bfloat16* __restrict__ kh, __nv_bfloat16* __restrict__ vh,
-                                   int N, int d, int H) {
-    const size_t row = blockIdx.x;                      // b N + t
-    const int b = (int)(row / N), t = (int)(row - (size_t)b * N);
-    const float* r = qkv + row * 3 * d;
-    for (int c = threadIdx.x; c < d; c += blockDim.x) {
-        const int hd = c / kDH, e = c - hd * kDH;
-        const size_t o = (((size_t)b * H + hd) * N + t) * kDH + e;
-        qh[o] = __float2bfloat16_rn(r[c] * 0.125f);
-        kh[o] = __float2bfloat16_rn(r[d + c]);
-        vh[o] = __float2bfloat16_rn(r[2 * d + c]);
+// causal softmax of each score row S[bh][i][0..i] (one warp per row), to bfloat16 P with the
+// masked entries j > i set to 0 (the next product reads whole rows). Even N <= 64 K2: each
+// lane keeps the column pairs 2 (lane + 32 k), k < K2, in registers (one read of the row,
+// 8-byte loads, 4-byte stores); causal_softmax_loop_kernel takes any N.
+template <int K2>
+__global__ void causal_softmax_kernel(const float* __restrict__ S, __nv_bfloat16* __restrict__ P,
+                                      size_t rows, int N) {
+    const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const int i = (int)(row % N);
+    const float2* sr = reinterpret_cast<const float2*>(S + row * N);
+    __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(P + row * N);
+    float2 v[K2];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < K2; ++k) {
+        const int j = 2 * (lane + 32 * k);
+        v[k] = j <= i ? sr[lane + 32 * k] : make_float2(-INFINITY, -INFINITY);   // j + 1 < N: N even
+        if (j + 1 > i) v[k].y = -INFINITY;
+        mx = fmaxf(mx, fmaxf(v[k].x, v[k].y));
     }
+    mx = warp_max(mx);
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K2; ++k) {
+        const int j = 2 * (lane + 32 * k);
+        v[k].x = j <= i ? expf(v[k].x - mx) : 0.f;
+        v[k].y = j + 1 <= i ? expf(v[k].y - mx) : 0.f;
+        sum += v[k].x + v[k].y;
+    }
+    const float inv = 1.f / warp_sum(sum);
+#pragma unroll
+    for (int k = 0; k < K2; ++k)
+        if (2 * (lane + 32 * k) < N) pr[lane + 32 * k] = __floats2bfloat162_rn(v[k].x * inv, v[k].y * inv);
 }
 
-// causal softmax of each score row S[bh][i][0..i] (one warp per row), to bfloat16 P with the
-// masked entries j > i set to 0 (the next product reads whole rows)
-__global__ void causal_softmax_kernel(const float* __restrict__ S, __nv_bfloat16* __restrict__ P,
+__global__ void causal_softmax_loop_kernel(const float* __restrict__ S, __nv_bfloat16* __restrict__ P,
                                       size_t rows, int N) {
     const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -387,17 +420,19 @@ float bf16_bits_to_float(uint16_t v) {
 }
 
 struct Layer {
-    float *ln1_g, *ln1_b, *b_qkv, *b_o, *ln2_g, *ln2_b, *b_1, *b_2;
+    float *ln1_g, *ln1_b, *b_qkv, *b_o, *ln2_g, *ln2_b, *b_2;
     __nv_bfloat16 *w_qkv, *w_o, *w_1, *w_2;
+    __nv_bfloat16 *b_qkv16, *b_1;   // the biases of the products with bfloat16 output
 };
 
 struct Act {                       // activation buffers for `rows` rows
     size_t rows = 0;
-    float *h = nullptr, *qkv = nullptr, *f1 = nullptr, *lp = nullptr;
+    float *h = nullptr, *qkv = nullptr, *lp = nullptr;
     __nv_bfloat16 *a = nullptr, *o = nullptr, *g = nullptr;
-    // scoring attention on the tensor cores: head-major operands, scores, probabilities
+    // scoring attention on the tensor cores: bfloat16 query/key/value [rows][3d], scores
+    // S FP32 and probabilities P bfloat16, both [B][H][N][N]
     size_t att_elems = 0;           // B H N N
-    __nv_bfloat16 *qh = nullptr, *kh = nullptr, *vh = nullptr, *P = nullptr;
+    __nv_bfloat16 *qkv16 = nullptr, *P = nullptr;
     float* S = nullptr;
 };
 
@@ -422,7 +457,7 @@ struct pt_former {
     SampleArgs* d_sargs = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::tuple<int, int, const void*, const void*, const void*, const void*> gkey{};
-    std::map<std::tuple<size_t, int, int, int>, cublasLtMatmulAlgo_t> algos;
+    std::map<std::vector<long long>, cublasLtMatmulAlgo_t> algos;   // by product shape, layout, alignment
 };
 
 namespace {
@@ -453,9 +488,9 @@ pt_status upload_bf16(pt_former* m, __nv_bfloat16** dst, const uint16_t* src, si
 }
 
 void free_act(Act& a) {
-    cudaFree(a.h); cudaFree(a.qkv); cudaFree(a.f1); cudaFree(a.lp);
+    cudaFree(a.h); cudaFree(a.qkv); cudaFree(a.lp);
     cudaFree(a.a); cudaFree(a.o); cudaFree(a.g);
-    cudaFree(a.qh); cudaFree(a.kh); cudaFree(a.vh); cudaFree(a.P); cudaFree(a.S);
+    cudaFree(a.qkv16); cudaFree(a.P); cudaFree(a.S);
     a = Act{};
 }
 
@@ -467,14 +502,12 @@ pt_status ensure_att(pt_former* m, Act& a, int B) {
     const size_t N = m->cfg.n_spins, H = m->cfg.n_heads, d = m->cfg.d_model;
     const size_t elems = (size_t)B * H * N * N;
     if (a.att_elems >= elems) return PT_OK;
-    cudaFree(a.qh); cudaFree(a.kh); cudaFree(a.vh); cudaFree(a.P); cudaFree(a.S);
-    a.qh = a.kh = a.vh = a.P = nullptr;
+    cudaFree(a.qkv16); cudaFree(a.P); cudaFree(a.S);
+    a.qkv16 = a.P = nullptr;
     a.S = nullptr;
     a.att_elems = 0;
     const size_t rows = (size_t)B * N;
-    FCK(cudaMalloc(&a.qh, rows * d * 2));
-    FCK(cudaMalloc(&a.kh, rows * d * 2));
-    FCK(cudaMalloc(&a.vh, rows * d * 2));
+    FCK(cudaMalloc(&a.qkv16, rows * 3 * d * 2));
     FCK(cudaMalloc(&a.S, elems * 4));
     FCK(cudaMalloc(&a.P, elems * 2));
     a.att_elems = elems;
@@ -487,7 +520,6 @@ pt_status ensure_act(pt_former* m, Act& a, size_t rows) {
     const size_t d = m->cfg.d_model, F = m->cfg.d_ff;
     FCK(cudaMalloc(&a.h, rows * d * 4));
     FCK(cudaMalloc(&a.qkv, rows * 3 * d * 4));
-    FCK(cudaMalloc(&a.f1, rows * F * 4));
     FCK(cudaMalloc(&a.lp, rows * 4));
     FCK(cudaMalloc(&a.a, rows * d * 2));
     FCK(cudaMalloc(&a.o, rows * d * 2));
@@ -496,12 +528,51 @@ pt_status ensure_act(pt_former* m, Act& a, size_t rows) {
     return PT_OK;
 }
 
-// Y [rows][n] (FP32) = X [rows][k] (bf16) W [k][n] (bf16) + bias [n] (+ Y when residual):
-// column-major Y^T = W^T X^T, with W^T as the [n x k] column-major view of row-major W.
-pt_status gemm(pt_former* m, float* Y, const __nv_bfloat16* X, const __nv_bfloat16* W,
-               const float* bias, size_t rows, int n, int k, bool residual) {
+// largest power of two (<= 256) dividing every byte offset given: the alignment cuBLASLt may
+// assume for a matrix (its base pointer, leading dimension and batch stride in bytes)
+long long alignment(std::initializer_list<unsigned long long> bytes) {
+    unsigned long long a = 256;
+    for (unsigned long long v : bytes)
+        while (a > 1 && v % a) a >>= 1;
+    return (long long)a;
+}
+
+// the algorithm cuBLASLt's heuristic picks for one product description, chosen once per
+// key (shape, layouts, output type, alignments) and kept
+pt_status pick_algo(pt_former* m, const std::vector<long long>& key, cublasLtMatmulDesc_t op,
+                    cublasLtMatrixLayout_t la, cublasLtMatrixLayout_t lb, cublasLtMatrixLayout_t lc,
+                    const long long al[3], const cublasLtMatmulAlgo_t** algo) {
+    auto it = m->algos.find(key);
+    if (it == m->algos.end()) {
+        cublasLtMatmulPreference_t pref = nullptr;
+        LCK(cublasLtMatmulPreferenceCreate(&pref));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES,
+                                                 &m->ws_bytes, sizeof m->ws_bytes));
+        const uint32_t a0 = (uint32_t)al[0], a1 = (uint32_t)al[1], a2 = (uint32_t)al[2];
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MIN_ALIGNMENT_A_BYTES, &a0, sizeof a0));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MIN_ALIGNMENT_B_BYTES, &a1, sizeof a1));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MIN_ALIGNMENT_C_BYTES, &a2, sizeof a2));
+        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MIN_ALIGNMENT_D_BYTES, &a2, sizeof a2));
+        cublasLtMatmulHeuristicResult_t res{};
+        int got = 0;
+        const cublasStatus_t st = cublasLtMatmulAlgoGetHeuristic(m->lt, op, la, lb, lc, lc, pref, 1, &res, &got);
+        cublasLtMatmulPreferenceDestroy(pref);
+        if (st != CUBLAS_STATUS_SUCCESS || got < 1)
+            return ffail(PT_ENOTSUP, "no cuBLASLt algorithm for the product %lld x %lld x %lld", key[1], key[2], key[3]);
+        it = m->algos.emplace(key, res.algo).first;
+    }
+    *algo = &it->second;
+    return PT_OK;
+}
+
+// Y [rows][n] = X [rows][k] (bf16) W [k][n] (bf16) + bias [n] (+ Y when residual), Y FP32
+// (bias FP32) or bfloat16 (yt = CUDA_R_16BF, bias bfloat16): column-major Y^T = W^T X^T,
+// with W^T as the [n x k] column-major view of row-major W.
+pt_status gemm(pt_former* m, void* Y, cudaDataType_t yt, const __nv_bfloat16* X,
+               const __nv_bfloat16* W, const void* bias, size_t rows, int n, int k, bool residual) {
     cublasLtMatmulDesc_t op = nullptr;
     cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
+    const size_t ys = yt == CUDA_R_32F ? 4 : 2;
     LCK(cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F));
     const cublasOperation_t nt = CUBLAS_OP_N;
     LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &nt, sizeof nt));
@@ -509,44 +580,41 @@ pt_status gemm(pt_former* m, float* Y, const __nv_bfloat16* X, const __nv_bfloat
     const cublasLtEpilogue_t ep = CUBLASLT_EPILOGUE_BIAS;
     LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_EPILOGUE, &ep, sizeof ep));
     LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof bias));
-    const cudaDataType_t bt = CUDA_R_32F;
-    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_BIAS_DATA_TYPE, &bt, sizeof bt));
+    LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_BIAS_DATA_TYPE, &yt, sizeof yt));
     LCK(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, n, k, n));
     LCK(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, k, (uint64_t)rows, k));
-    LCK(cublasLtMatrixLayoutCreate(&lc, CUDA_R_32F, n, (uint64_t)rows, n));
-    const auto key = std::make_tuple(rows, n, k, residual ? 1 : 0);
-    auto it = m->algos.find(key);
-    if (it == m->algos.end()) {
-        cublasLtMatmulPreference_t pref = nullptr;
-        LCK(cublasLtMatmulPreferenceCreate(&pref));
-        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES,
-                                                 &m->ws_bytes, sizeof m->ws_bytes));
-        cublasLtMatmulHeuristicResult_t res{};
-        int got = 0;
-        LCK(cublasLtMatmulAlgoGetHeuristic(m->lt, op, la, lb, lc, lc, pref, 1, &res, &got));
-        cublasLtMatmulPreferenceDestroy(pref);
-        if (got < 1) return ffail(PT_ENOTSUP, "no cuBLASLt algorithm for %zu x %d x %d", rows, n, k);
-        it = m->algos.emplace(key, res.algo).first;
+    LCK(cublasLtMatrixLayoutCreate(&lc, yt, n, (uint64_t)rows, n));
+    const long long al[3] = {alignment({(unsigned long long)W, 2ull * n}),
+                             alignment({(unsigned long long)X, 2ull * k}),
+                             alignment({(unsigned long long)Y, ys * n})};
+    const std::vector<long long> key = {0, (long long)rows, n, k, residual ? 1 : 0, (long long)yt,
+                                        al[0], al[1], al[2]};
+    const cublasLtMatmulAlgo_t* algo = nullptr;
+    pt_status s = pick_algo(m, key, op, la, lb, lc, al, &algo);
+    cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+    if (s == PT_OK) {
+        const float one = 1.f, beta = residual ? 1.f : 0.f;
+        st = cublasLtMatmul(m->lt, op, &one, W, la, X, lb, &beta, Y, lc, Y, lc, algo, m->workspace,
+                            m->ws_bytes, m->exec);
     }
-    const float one = 1.f, beta = residual ? 1.f : 0.f;
-    const cublasStatus_t st = cublasLtMatmul(m->lt, op, &one, W, la, X, lb, &beta, Y, lc, Y, lc,
-                                             &it->second, m->workspace, m->ws_bytes, m->exec);
     cublasLtMatrixLayoutDestroy(la);
     cublasLtMatrixLayoutDestroy(lb);
     cublasLtMatrixLayoutDestroy(lc);
     cublasLtMatmulDescDestroy(op);
+    if (s != PT_OK) return s;
     if (st != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "cublasLtMatmul: status %d", (int)st);
     return PT_OK;
 }
 
 // Strided-batched product on the tensor cores, column-major views: C [m][n] (type ct, leading
-// dimension ldc, batch stride sc) = op(A) [m][k] op(B) [k][n], bfloat16 operands, FP32
+// dimension ldc, batch stride sc) = alpha op(A) [m][k] op(B) [k][n], bfloat16 operands, FP32
 // accumulation, no epilogue.
-pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const void* A, int lda, long long sa,
-                       const void* Bm, int ldb, long long sb, void* C, cudaDataType_t ct, int ldc,
-                       long long sc, int mm, int nn, int kk, int batch) {
+pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const __nv_bfloat16* A, int lda, long long sa,
+                       const __nv_bfloat16* Bm, int ldb, long long sb, void* C, cudaDataType_t ct, int ldc,
+                       long long sc, int mm, int nn, int kk, int batch, float alpha) {
     cublasLtMatmulDesc_t op = nullptr;
     cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
+    const unsigned long long cs = ct == CUDA_R_32F ? 4 : 2;
     LCK(cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F));
     const cublasOperation_t nt = CUBLAS_OP_N;
     LCK(cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &ta, sizeof ta));
@@ -559,50 +627,58 @@ pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const void* A, int ld
         LCK(cublasLtMatrixLayoutSetAttribute(l, CUBLASLT_MATRIX_LAYOUT_BATCH_COUNT, &batch, sizeof batch));
         LCK(cublasLtMatrixLayoutSetAttribute(l, CUBLASLT_MATRIX_LAYOUT_STRIDED_BATCH_OFFSET, &st, sizeof st));
     }
-    const auto key = std::make_tuple((size_t)batch * 1000003 + (size_t)kk, mm, nn, ct == CUDA_R_32F ? 2 : 3);
-    auto it = m->algos.find(key);
-    if (it == m->algos.end()) {
-        cublasLtMatmulPreference_t pref = nullptr;
-        LCK(cublasLtMatmulPreferenceCreate(&pref));
-        LCK(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES,
-                                                 &m->ws_bytes, sizeof m->ws_bytes));
-        cublasLtMatmulHeuristicResult_t res{};
-        int got = 0;
-        LCK(cublasLtMatmulAlgoGetHeuristic(m->lt, op, la, lb, lc, lc, pref, 1, &res, &got));
-        cublasLtMatmulPreferenceDestroy(pref);
-        if (got < 1) return ffail(PT_ENOTSUP, "no cuBLASLt algorithm for the batched %d x %d x %d", mm, nn, kk);
-        it = m->algos.emplace(key, res.algo).first;
+    const long long al[3] = {alignment({(unsigned long long)A, 2ull * lda, 2ull * sa}),
+                             alignment({(unsigned long long)Bm, 2ull * ldb, 2ull * sb}),
+                             alignment({(unsigned long long)C, cs * ldc, cs * sc})};
+    const std::vector<long long> key = {1, mm, nn, kk, batch, (long long)ta, lda, sa, ldb, sb, ldc, sc,
+                                        (long long)ct, al[0], al[1], al[2]};
+    const cublasLtMatmulAlgo_t* algo = nullptr;
+    pt_status s = pick_algo(m, key, op, la, lb, lc, al, &algo);
+    cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+    if (s == PT_OK) {
+        const float zero = 0.f;
+        st = cublasLtMatmul(m->lt, op, &alpha, A, la, Bm, lb, &zero, C, lc, C, lc, algo, m->workspace,
+                            m->ws_bytes, m->exec);
     }
-    const float one = 1.f, zero = 0.f;
-    const cublasStatus_t st = cublasLtMatmul(m->lt, op, &one, A, la, Bm, lb, &zero, C, lc, C, lc,
-                                             &it->second, m->workspace, m->ws_bytes, m->exec);
     cublasLtMatrixLayoutDestroy(la);
     cublasLtMatrixLayoutDestroy(lb);
     cublasLtMatrixLayoutDestroy(lc);
     cublasLtMatmulDescDestroy(op);
+    if (s != PT_OK) return s;
     if (st != CUBLAS_STATUS_SUCCESS) return ffail(PT_ECUDA, "batched cublasLtMatmul: status %d", (int)st);
     return PT_OK;
 }
 
-// Causal attention of the scoring pass on the tensor cores: S = Q K^T for every
-// (configuration, head) in one batched product (row-major S [N][N] is the column-major
-// S^T = K Q^T), the causal softmax, then O = P V per head, batched over configurations
-// (O^T = V^T P^T, written into the heads' columns of the [B N][d] output).
+// Causal attention of the scoring pass on the tensor cores, per head, batched over the B
+// configurations, reading the heads' columns of the bfloat16 [B N][3d] query/key/value in
+// place: S = Q K^T / 8 (row-major S [N][N] is the column-major S^T = K Q^T), the causal
+// softmax, then O = P V (O^T = V^T P^T, written into the head's columns of the [B N][d] output).
 pt_status attention_tc(pt_former* m, Act& x, int B) {
     const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
-    const long long hs = (long long)N * kDH;           // one head's [N][64] block
-    split_heads_kernel<<<(unsigned)((size_t)B * N), 256, 0, m->exec>>>(x.qkv, x.qh, x.kh, x.vh, N, d, H);
-    FCK(cudaGetLastError());
-    pt_status s = gemm_batched(m, CUBLAS_OP_T, x.kh, kDH, hs, x.qh, kDH, hs, x.S, CUDA_R_32F, N,
-                               (long long)N * N, N, N, kDH, B * H);
+    const int ld = 3 * d;
+    const long long cfg_stride = (long long)N * ld;     // one configuration's rows
+    const long long nn = (long long)N * N;
+    pt_status s = PT_OK;
+    for (int hd = 0; hd < H && s == PT_OK; ++hd)
+        s = gemm_batched(m, CUBLAS_OP_T, x.qkv16 + d + hd * kDH, ld, cfg_stride, x.qkv16 + hd * kDH, ld,
+                         cfg_stride, x.S + hd * nn, CUDA_R_32F, N, H * nn, N, N, kDH, B, 0.125f);
     if (s != PT_OK) return s;
     const size_t rows = (size_t)B * H * N;
-    causal_softmax_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    const unsigned grid = (unsigned)((rows + 7) / 8);
+    if (N % 2 == 0 && N <= 64)
+        causal_softmax_kernel<1><<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    else if (N % 2 == 0 && N <= 128)
+        causal_softmax_kernel<2><<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    else if (N % 2 == 0 && N <= 256)
+        causal_softmax_kernel<4><<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    else if (N % 2 == 0 && N <= 512)
+        causal_softmax_kernel<8><<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
+    else
+        causal_softmax_loop_kernel<<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
     FCK(cudaGetLastError());
     for (int hd = 0; hd < H && s == PT_OK; ++hd)
-        s = gemm_batched(m, CUBLAS_OP_N, x.vh + (size_t)hd * hs, kDH, (long long)H * hs,
-                         x.P + (size_t)hd * N * N, N, (long long)H * N * N, x.o + (size_t)hd * kDH,
-                         CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B);
+        s = gemm_batched(m, CUBLAS_OP_N, x.qkv16 + 2 * d + hd * kDH, ld, cfg_stride, x.P + hd * nn, N, H * nn,
+                         x.o + hd * kDH, CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B, 1.f);
     return s;
 }
 
@@ -637,22 +713,25 @@ void launch_head_sample(pt_former* m, const int8_t* prefix, int npre, int8_t* ou
                                                               m->cfg.n_spins, t);
 }
 
-// one pre-layer-norm block on rows [0, M) of `a` (attention by `attn`)
+// one pre-layer-norm block on rows [0, M) of `a` (attention by `attn`; query/key/value to
+// the bfloat16 buffer when qkv_bf16, the operand layout of the tensor-core attention)
 template <class AttnFn>
-pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, AttnFn attn) {
+pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, AttnFn attn) {
     const int d = m->cfg.d_model, F = m->cfg.d_ff;
     pt_status s = layernorm(m, x.h, Ly.ln1_g, Ly.ln1_b, x.a, M);
-    if (s == PT_OK) s = gemm(m, x.qkv, x.a, Ly.w_qkv, Ly.b_qkv, M, 3 * d, d, false);
+    if (s == PT_OK)
+        s = qkv_bf16 ? gemm(m, x.qkv16, CUDA_R_16BF, x.a, Ly.w_qkv, Ly.b_qkv16, M, 3 * d, d, false)
+                     : gemm(m, x.qkv, CUDA_R_32F, x.a, Ly.w_qkv, Ly.b_qkv, M, 3 * d, d, false);
     if (s == PT_OK) s = attn();
-    if (s == PT_OK) s = gemm(m, x.h, x.o, Ly.w_o, Ly.b_o, M, d, d, true);
+    if (s == PT_OK) s = gemm(m, x.h, CUDA_R_32F, x.o, Ly.w_o, Ly.b_o, M, d, d, true);
     if (s == PT_OK) s = layernorm(m, x.h, Ly.ln2_g, Ly.ln2_b, x.a, M);
-    if (s == PT_OK) s = gemm(m, x.f1, x.a, Ly.w_1, Ly.b_1, M, F, d, false);
+    if (s == PT_OK) s = gemm(m, x.g, CUDA_R_16BF, x.a, Ly.w_1, Ly.b_1, M, F, d, false);
     if (s == PT_OK) {
-        const size_t n = M * (size_t)F;
-        gelu_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 32), 256, 0, m->exec>>>(x.f1, x.g, n);
+        const size_t n8 = M * (size_t)F / 8;           // F is a multiple of 8
+        gelu_kernel<<<(unsigned)std::min<size_t>((n8 + 255) / 256, 152 * 16), 256, 0, m->exec>>>(x.g, n8);
         FCK(cudaGetLastError());
     }
-    if (s == PT_OK) s = gemm(m, x.h, x.g, Ly.w_2, Ly.b_2, M, d, F, true);
+    if (s == PT_OK) s = gemm(m, x.h, CUDA_R_32F, x.g, Ly.w_2, Ly.b_2, M, d, F, true);
     return s;
 }
 
@@ -665,7 +744,7 @@ pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* 
         FCK(cudaGetLastError());
         for (int l = 0; l < m->cfg.n_layers; ++l) {
             float* cl = m->cache + (size_t)l * B * N * 2 * d;
-            pt_status s = block(m, m->step, (size_t)B, m->layers[l], [&]() -> pt_status {
+            pt_status s = block(m, m->step, (size_t)B, m->layers[l], false, [&]() -> pt_status {
                 kv_append_kernel<<<B, 256, 0, m->exec>>>(m->step.qkv, cl, N, d, t);
                 attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(m->step.qkv, cl, m->step.o, N, d, t);
                 FCK(cudaGetLastError());
@@ -730,13 +809,15 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
         s = upload_f32(m, &L.ln1_g, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln1_b, take(d), d);
         if (s == PT_OK) s = upload_bf16(m, &L.w_qkv, take(3 * (size_t)d * d), 3 * (size_t)d * d);
-        if (s == PT_OK) s = upload_f32(m, &L.b_qkv, take(3 * (size_t)d), 3 * (size_t)d);
+        const uint16_t* bq = take(3 * (size_t)d);
+        if (s == PT_OK) s = upload_f32(m, &L.b_qkv, bq, 3 * (size_t)d);
+        if (s == PT_OK) s = upload_bf16(m, &L.b_qkv16, bq, 3 * (size_t)d);
         if (s == PT_OK) s = upload_bf16(m, &L.w_o, take((size_t)d * d), (size_t)d * d);
         if (s == PT_OK) s = upload_f32(m, &L.b_o, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln2_g, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln2_b, take(d), d);
         if (s == PT_OK) s = upload_bf16(m, &L.w_1, take((size_t)d * F), (size_t)d * F);
-        if (s == PT_OK) s = upload_f32(m, &L.b_1, take(F), F);
+        if (s == PT_OK) s = upload_bf16(m, &L.b_1, take(F), F);
         if (s == PT_OK) s = upload_bf16(m, &L.w_2, take((size_t)F * d), (size_t)F * d);
         if (s == PT_OK) s = upload_f32(m, &L.b_2, take(d), d);
     }
@@ -784,7 +865,7 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
         if (s != PT_OK) return s;
     }
     for (int l = 0; l < m->cfg.n_layers && s == PT_OK; ++l) {
-        s = block(m, x, M, m->layers[l], [&]() -> pt_status {
+        s = block(m, x, M, m->layers[l], tc, [&]() -> pt_status {
             if (tc) return attention_tc(m, x, B);
             attention_kernel<<<dim3((N + kAQ - 1) / kAQ, H, B), kAQ, 0, m->exec>>>(x.qkv, x.o, N, d);
             FCK(cudaGetLastError());
