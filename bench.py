@@ -616,14 +616,15 @@ def _mark_factored(ctx, mult, products, solved_at, sweeps):
 
 
 def graph_alu_ops_per_attempt(mean_degree: float) -> float:
-    """Algorithmic integer-ALU operations of one attempt of the graph engine (int8 spins, four
-    walkers of one site per thread, Gibbs or Metropolis): 5 for the three-input XORs of one
-    Philox4x32-10 call shared by the four walkers (20 / 4; its wide multiplies run on the FMA
-    pipe), mean_degree / 4 to decode the packed row entries (one per neighbour, shared by the
-    four walkers; the byte-sum multiply-add runs on the FMA pipe), and 6 per walker: extract
-    its byte of the field sum, form the field (Gibbs) or the energy change (Metropolis), index
-    the threshold row, compare, insert the new spin byte, and its energy term."""
-    return 5.0 + mean_degree / 4.0 + 6.0
+    """Algorithmic integer-ALU operations of one attempt of the graph engine (int8 spins,
+    eight walkers of one site per thread, Gibbs or Metropolis): 2.5 for the three-input XORs
+    of one Philox4x32-10 call shared by the eight walkers (20 / 8; its wide multiplies run on
+    the FMA pipe; the second call, for the low halves of the uniforms, runs only at a tie and
+    is not counted), mean_degree / 8 to decode the packed row entries (one per neighbour,
+    shared by the eight walkers; the byte-sum multiply-adds run on the FMA pipe), and 7 per
+    walker: extract its byte of the field sum, form the threshold index, compare the high
+    halves, test for a tie, form and insert the new spin byte, and its energy term."""
+    return 2.5 + mean_degree / 8.0 + 7.0
 
 
 def _oracle_worker_factor(a):

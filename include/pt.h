@@ -94,8 +94,7 @@ typedef struct {
  *                    (Fig. 3: start 100, then every sweep; Fig. S3: stop after 100.)
  *  pool_size         P, proposal-pool capacity per (instance, slot); 0 = no pools.
  *  seed              64-bit key of every random stream.
- *  threads_per_block 0 = automatic choice; else a multiple of 32 in [32, 512] (lattice
- *                    engine) or [32, 1024] (graph engine).
+ *  threads_per_block 0 = automatic choice; else a multiple of 32 in [32, 512].
  *  proposal_rule     acceptance of a global proposal: 0 = the paper's Delta-E-only rule
  *                    min[1, exp(beta_r (E_r - E^T))] (Eq. 2, an optimization heuristic);
  *                    1 = always accept, which is the independent Metropolis-Hastings move

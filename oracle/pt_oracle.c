@@ -373,8 +373,20 @@ static uint32_t local_uniform(const or_inst *o, int32_t site, int32_t walker) {
         }
         return u;
     }
-    uint32_t c2 = (2u << 24) | (uint32_t)(walker >> 2);
-    return philox_word(o->seed, (uint32_t)site, s, c2, o->id, walker & 3);
+    /* general graphs: two 16-bit halves, u = hi << 16 | lo, each the (walker odd: low, even:
+     * high) half of output word (walker & 7) / 2 of Philox(site, sweep, 2 << 24 | part << 16 |
+     * walker / 8, id), part 0 for hi and 1 for lo */
+    uint32_t c2 = (2u << 24) | (uint32_t)(walker >> 3);
+    uint32_t hi = philox_word(o->seed, (uint32_t)site, s, c2, o->id, (walker & 7) >> 1);
+    uint32_t lo = philox_word(o->seed, (uint32_t)site, s, c2 | (1u << 16), o->id, (walker & 7) >> 1);
+    if (walker & 1) {
+        hi &= 0xFFFFu;
+        lo &= 0xFFFFu;
+    } else {
+        hi >>= 16;
+        lo >>= 16;
+    }
+    return (hi << 16) | lo;
 }
 
 /* One sweep (Methods, "Local Monte Carlo sweeps"): every free spin of every replica once,

@@ -2,6 +2,7 @@
 // colouring, FP64 threshold tables, device allocation and kernel launches. No step of the
 // method's arithmetic on the spins runs here; it all runs in the kernels of pt_lattice.cu
 // and pt_graph.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <mutex>
@@ -25,7 +26,7 @@ cudaError_t launch_lattice_init(const LatInst*, int, uint64_t, cudaStream_t);
 cudaError_t launch_lattice_capture(const LatInst*, const LatInst*, int, int, cudaStream_t);
 cudaError_t launch_lattice_read(const LatInst*, int, int8_t*, int, cudaStream_t);
 cudaError_t launch_lattice_write(const LatInst*, int, const int8_t*, const int32_t*, int, cudaStream_t);
-cudaError_t launch_graph(const GraphInst*, int, int, size_t, const RunArgs&, int, cudaStream_t);
+cudaError_t launch_graph(const GraphInst*, int, int, size_t, const RunArgs&, int, bool, bool, cudaStream_t);
 cudaError_t launch_graph_init(const GraphInst*, int, uint64_t, cudaStream_t);
 cudaError_t launch_graph_capture(const GraphInst*, const GraphInst*, int, int, cudaStream_t);
 cudaError_t launch_graph_read(const GraphInst*, int, int8_t*, int, cudaStream_t);
@@ -132,6 +133,7 @@ struct Group {
     size_t smem = 0;
     int maxW = 1;
     int maxitems = 0;          // largest (colour class x walker blocks) of a member
+    bool packed_only = false;  // graph engine: every member has packed rows
     void* d_insts = nullptr;   // LatInst[] or GraphInst[] of the members
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -152,7 +154,7 @@ struct pt_ctx {
     int optin = 0;            // device limit on dynamic shared memory per block
     int sms = 0;              // streaming multiprocessors of the device
     int device = -1;          // the device current at creation; every call must run with it
-    std::vector<int> N, R, W, NW, R4, L;
+    std::vector<int> N, R, W, NW, Rp, L;
     std::vector<size_t> slab_off;  // words, instance offset inside one pool entry
     size_t slab = 0;               // words per pool entry (all instances, all slots)
     uint8_t* arena = nullptr;
@@ -232,7 +234,8 @@ cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, i
         return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, kb4, g.T, g.smem, a,
                               flags, s);
     }
-    return launch_graph(static_cast<const GraphInst*>(d_insts), count, g.T, g.smem, a, c->with_pool, s);
+    return launch_graph(static_cast<const GraphInst*>(d_insts), count, g.T, g.smem, a, c->with_pool,
+                        g.packed_only, c->cfg.update == 1, s);
 }
 
 // Launch one kernel per group on stream s; with several groups they fork from s onto their
@@ -471,7 +474,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         LatHost h;
         pt_status st = lattice_host(d, h, k, c->cfg.update == 1);
         if (st != PT_OK) return st;
-        c->N[k] = h.N; c->R[k] = h.R; c->W[k] = h.W; c->NW[k] = h.NW; c->R4[k] = h.W * 32; c->L[k] = h.L;
+        c->N[k] = h.N; c->R[k] = h.R; c->W[k] = h.W; c->NW[k] = h.NW; c->Rp[k] = h.W * 32; c->L[k] = h.L;
         maxitems[k] = h.maxitems;
         LatInst& I = c->lat[k];
         memset(&I, 0, sizeof I);
@@ -574,16 +577,16 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
     c->gr.resize(n);
     size_t maxsmem = 0;
     int T = c->cfg.threads_per_block > 0 ? c->cfg.threads_per_block : 128;
-    if (T % 32 != 0 || T < 32 || T > 1024) return fail(PT_EINVAL, "threads_per_block must be a multiple of 32 in [32, 1024]");
+    if (T % 32 != 0 || T < 32 || T > 512) return fail(PT_EINVAL, "graph engine: threads_per_block must be a multiple of 32 in [32, 512]");
     c->with_pool = c->cfg.pool_size > 0 ? 1 : 0;
     for (int k = 0; k < n; ++k) {
         const pt_instance_desc& d = descs[k];
-        const int N = d.n_spins, R = d.n_replicas, R4 = (R + 3) & ~3, NW = (N + 31) / 32, NE = d.n_edges;
+        const int N = d.n_spins, R = d.n_replicas, Rp = (R + 7) & ~7, NW = (N + 31) / 32, NE = d.n_edges;
         if (N > 65535) return fail(PT_ENOTSUP, "instance %d: graph engine supports N <= 65535", k);
-        c->N[k] = N; c->R[k] = R; c->W[k] = (R + 31) / 32; c->NW[k] = NW; c->R4[k] = R4;
+        c->N[k] = N; c->R[k] = R; c->W[k] = (R + 31) / 32; c->NW[k] = NW; c->Rp[k] = Rp;
         GraphInst& I = c->gr[k];
         memset(&I, 0, sizeof I);
-        I.iid = d.instance_id; I.N = N; I.R = R; I.R4 = R4; I.NW = NW; I.NE = NE; I.P = c->cfg.pool_size;
+        I.iid = d.instance_id; I.N = N; I.R = R; I.Rp = Rp; I.NW = NW; I.NE = NE; I.P = c->cfg.pool_size;
         // CSR with both directions of every edge
         std::vector<int32_t> rowp(N + 1, 0), adj(2 * (size_t)NE), adjJ(2 * (size_t)NE), h(N, 0);
         for (int e = 0; e < NE; ++e) { rowp[d.edge_i[e] + 1]++; rowp[d.edge_j[e] + 1]++; }
@@ -646,8 +649,9 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
             rowl[i] = lo;
         }
         // Packed local fields: four walkers' sums of J * [spin = -1] as bytes of one word
-        // (biased by 128), valid while every site's sum of |J| is at most 127.
-        bool packed = true;
+        // (biased by 128), valid while every site's sum of |J| is at most 127 (and the row
+        // offsets, in units of eight walkers, fit 24 bits).
+        bool packed = (long long)N * (Rp / 8) < (1ll << 24);
         for (int i = 0; i < N && packed; ++i) {
             int sa = 0;
             for (int a = rowp[i]; a < rowp[i + 1]; ++a) sa += std::abs(adjJ[a]);
@@ -656,7 +660,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         std::vector<int32_t> adjp(2 * (size_t)NE, 0);
         if (packed)
             for (size_t a = 0; a < adjp.size(); ++a)
-                adjp[a] = (int32_t)(((uint32_t)adj[a] * (uint32_t)(R4 / 4)) << 8 | ((uint32_t)adjJ[a] & 0xFFu));
+                adjp[a] = (int32_t)(((uint32_t)adj[a] * (uint32_t)(Rp / 8)) << 8 | ((uint32_t)adjJ[a] & 0xFFu));
         I.packed = packed ? 1 : 0;
         {
             long long ec = 0;
@@ -666,11 +670,19 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
                     ec -= (long long)d.edge_J[e] * clamp[d.edge_i[e]] * clamp[d.edge_j[e]];
             I.Eclamp = (int32_t)ec;
         }
+        // free sites colour by colour; within a colour by decreasing degree (then index), so
+        // the sites one warp updates together loop over similar numbers of neighbours. Sites
+        // of one colour share no edge and draw their random numbers by site index, so their
+        // order does not change the result.
         std::vector<int32_t> cs;
         I.col_off[0] = 0;
         for (int cc = 0; cc < ncol; ++cc) {
+            const size_t first = cs.size();
             for (int i = 0; i < N; ++i)
                 if (col[i] == cc && clamp[i] == 0) cs.push_back(i);
+            std::stable_sort(cs.begin() + first, cs.end(), [&](int32_t x, int32_t y) {
+                return rowp[x + 1] - rowp[x] > rowp[y + 1] - rowp[y];
+            });
             I.col_off[cc + 1] = (int)cs.size();
         }
         I.nfree = (int)cs.size();
@@ -686,11 +698,11 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
                 thr[(size_t)r * tw + v + I.Imax] = (c->cfg.update == 1)
                     ? gibbs_threshold(d.beta[r], v)
                     : (v > 0 ? metropolis_threshold(d.beta[r], 2 * v) : 0u);
-        std::vector<int16_t> sow(R4, -1), wos(R);
+        std::vector<int16_t> sow(Rp, -1), wos(R);
         for (int r = 0; r < R; ++r) { sow[r] = (int16_t)r; wos[r] = (int16_t)r; }
         std::vector<uint8_t> prop(R, 0);
         if (d.prop_enabled) for (int r = 0; r < R; ++r) prop[r] = d.prop_enabled[r] ? 1 : 0;
-        o[k].spins = A.zeros((size_t)N * R4);
+        o[k].spins = A.zeros((size_t)N * Rp);
         o[k].clamp = A.add(clamp.data(), N);
         o[k].rowp = A.add(rowp.data(), rowp.size() * 4);
         o[k].rowl = A.add(rowl.data(), rowl.size() * 4);
@@ -705,7 +717,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
                 for (int a = rowp[i]; a < rowl[i]; ++a) sc += adjJ[a];
                 for (int a = rowl[i]; a < rowp[i + 1]; ++a) sr += adjJ[a];
                 hk[2 * (size_t)i] = (int32_t)(h[i] + sc + 256);
-                hk[2 * (size_t)i + 1] = (int32_t)(h[i] + sc + sr + 512);
+                hk[2 * (size_t)i + 1] = (int32_t)(h[i] + sc + sr + 256);
             }
             o[k].hk = A.add(hk.data(), hk.size() * 4);
         }
@@ -743,7 +755,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         o[k].ph_i = A.add(ph_i.data(), std::max<size_t>(ph_i.size(), 1) * 4);
         o[k].ph_h = A.add(ph_h.data(), std::max<size_t>(ph_h.size(), 1) * 4);
         o[k].cb = A.add(cb.data(), cb.size() * 4);
-        o[k].E = A.zeros((size_t)R4 * 4);
+        o[k].E = A.zeros((size_t)Rp * 4);
         o[k].sow = A.add(sow.data(), sow.size() * 2);
         o[k].wos = A.add(wos.data(), wos.size() * 2);
         o[k].thr = A.add(thr.data(), thr.size() * 4);
@@ -758,14 +770,18 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
         c->slab_off[k] = c->slab;
         c->slab += (size_t)R * NW;
         c->NWmax = std::max(c->NWmax, NW);
-        const GraphLayout l = graph_layout(N, R, R4, NE, I.Imax, I.nfree, NW, c->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
+        const GraphLayout l = graph_layout(N, R, Rp, NE, I.Imax, I.nfree, NW, c->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
         maxsmem = std::max(maxsmem, l.total);
     }
     if (maxsmem > (size_t)c->optin)
         return fail(PT_ENOTSUP, "instance needs %zu B of shared memory (> %d)", maxsmem, c->optin);
     c->groups.assign(1, Group{});
     Group& grp = c->groups[0];
-    for (int k = 0; k < n; ++k) grp.members.push_back(k);
+    grp.packed_only = true;
+    for (int k = 0; k < n; ++k) {
+        grp.members.push_back(k);
+        grp.packed_only = grp.packed_only && c->gr[k].packed != 0;
+    }
     grp.T = T;
     grp.smem = maxsmem;
     c->group_of.assign(n, 0);
@@ -931,7 +947,7 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
     c->n = n;
     c->cfg = *cfg;
     c->stream = (cudaStream_t)cuda_stream;
-    c->N.resize(n); c->R.resize(n); c->W.resize(n); c->NW.resize(n); c->R4.resize(n); c->L.resize(n);
+    c->N.resize(n); c->R.resize(n); c->W.resize(n); c->NW.resize(n); c->Rp.resize(n); c->L.resize(n);
     c->slab_off.resize(n);
     {
         int dev = 0;
@@ -1043,7 +1059,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.Rp, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
                     smem = std::max(smem, l.total);
                 }
                 (void)I0;
@@ -1069,7 +1085,7 @@ pt_status pt_autotune(pt_ctx* ctx, int32_t probe_cycles, int32_t* threads_out) {
                 size_t smem = 0;
                 for (int k : g.members) {
                     const GraphInst& I = ctx->gr[k];
-                    const GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
+                    const GraphLayout l = graph_layout(I.N, I.R, I.Rp, I.NE, I.Imax, I.nfree, I.NW, ctx->with_pool != 0, I.packed != 0, I.nEb, I.nHb);
                     smem = std::max(smem, l.total);
                 }
                 g.T = bestT;
@@ -1336,7 +1352,7 @@ pt_status pt_write_state(pt_ctx* ctx, int32_t inst, const int8_t* spins, const i
                     return fail(PT_EINVAL, "spin %d of slot %d contradicts its clamp", i, r);
     }
     // walker labels
-    const int Wpad = ctx->engine == 0 ? ctx->W[inst] * 32 : ctx->R4[inst];
+    const int Wpad = ctx->engine == 0 ? ctx->W[inst] * 32 : ctx->Rp[inst];
     std::vector<int16_t> wos(R), sow(Wpad, -1);
     for (int r = 0; r < R; ++r) { wos[r] = (int16_t)walker[r]; sow[walker[r]] = (int16_t)r; }
     int8_t* d_sp = nullptr;

@@ -3,11 +3,11 @@
 // invertible multiplier of Supplementary S4), Gibbs (the paper's rule, Methods) or
 // Metropolis local moves, colour class by colour class (DSATUR colouring, Methods).
 //
-// Layout. Spin bytes [N][R4] (R4 = R rounded up to 4), 1 where the spin is -1 and 0 where
-// it is +1: one 32-bit word holds four walkers of one site, so a thread updates four walkers
-// of one site with one Philox call, whose four output words are the four walkers' uniforms,
-// and a neighbour word is directly the four walkers' [m = -1] flags. A walker keeps its storage column; exchange
-// permutes slot <-> walker labels, thresholds are looked up by the walker's current slot.
+// Layout. Spin bytes [N][Rp] (Rp = R rounded up to 8), 1 where the spin is -1 and 0 where
+// it is +1: a thread updates eight walkers of one site from one 8-byte load, and a neighbour's
+// 8-byte group is directly the eight walkers' [m = -1] flags. A walker keeps its storage
+// column; exchange permutes slot <-> walker labels, thresholds are looked up by the walker's
+// current slot.
 #include "pt_device.cuh"
 #include "pt_layout.h"
 #include "pt_graph.cuh"
@@ -40,7 +40,7 @@ struct GraphSmem {
 
 __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst& I,
                                                  bool with_pool) {
-    GraphLayout l = graph_layout(I.N, I.R, I.R4, I.NE, I.Imax, I.nfree, I.NW, with_pool,
+    GraphLayout l = graph_layout(I.N, I.R, I.Rp, I.NE, I.Imax, I.nfree, I.NW, with_pool,
                                  I.packed != 0, I.nEb, I.nHb);
     GraphSmem S;
     S.spins = reinterpret_cast<int8_t*>(base + l.spins);
@@ -67,41 +67,61 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     return S;
 }
 
+// four bits to the low bits of four bytes: bit k -> bit 8 k
+__device__ __forceinline__ uint32_t spread4(uint32_t x) {
+    return (x * 0x00204081u) & 0x01010101u;
+}
+
 // the spin (+1 or -1) of walker k of a stored word
 __device__ __forceinline__ int sbyte(uint32_t w, int k) {
     return 1 - 2 * (int)((w >> (8 * k)) & 1u);
 }
 
-// One sweep: every free site of every colour class, four walkers per thread. Thread t takes
-// quad t % Q of the sites t / Q, t / Q + Ts / Q, ... of each class (Ts, the threads used, a
-// multiple of Q), so it keeps one quad for the whole sweep and neighbouring lanes read
-// neighbouring words of one row.
-// With energy_on (the last sweep of a cycle) each thread adds, for its quad, the energy terms
-// of the free sites it updates: -m (h + the bonds to its counted neighbours, rowp..rowl),
-// which sum with Eclamp to the exact energy (each bond counted once, at the end updated
-// last); graph_energy_finish turns them into E.
-__device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
-                            uint32_t sweep_idx, int update, bool energy_on) {
+// One sweep: every free site of every colour class, eight walkers per thread. Thread t takes
+// the eight walkers of octet t % O (O = Rp / 8) at the sites t / O, t / O + Ts / O, ... of
+// each class (Ts, the threads used, a multiple of O), so it keeps one octet for the whole
+// sweep and neighbouring lanes read neighbouring 8-byte groups of one row.
+// Uniforms: walker w's 32-bit u at (site, sweep) is hi << 16 | lo, hi the 16-bit half
+// (w odd: low, even: high) of output word (w & 7) / 2 of Philox(site, sweep, 2 << 24 | w / 8,
+// id) and lo the same half of Philox(site, sweep, 2 << 24 | 1 << 16 | w / 8, id). u < thr
+// follows from hi alone unless hi equals the high half of thr (probability at most 2^-16 per
+// walker), so the second call runs only for a thread that meets such a tie.
+// With energy_on (the last sweep of a cycle) each thread adds, for its octet, the energy
+// terms of the free sites it updates: -m (h + the bonds to its counted neighbours,
+// rowp..rowl), which sum with Eclamp to the exact energy (each bond counted once, at the end
+// updated last); graph_energy_finish turns them into E.
+// the rare second draw of graph_sweep_t, out of line so that its registers are not reserved
+// across the common path
+__device__ __noinline__ uint4 philox_cold(uint4 c, uint32_t k0, uint32_t k1) {
+    return philox(c, k0, k1);
+}
+
+template <bool PACKED, bool GIBBS>
+__device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a,
+                              uint32_t sweep_idx, bool energy_on) {
     // the instance's scalars in registers: the descriptor lives in global memory, and the
     // shared-memory stores below would otherwise force it to be read again
-    const int Q = I.R4 >> 2, R = I.R, Imax = I.Imax, ncol = I.ncol;
-    const bool packed = I.packed != 0;
+    const int O = I.Rp >> 3, R = I.R, Imax = I.Imax, ncol = I.ncol;
     const uint32_t iid = I.iid;
     const int tw = 2 * Imax + 1;
-    const int Ts = (blockDim.x / Q) * Q;
+    const int Ts = (blockDim.x / O) * O;
     const int tid = threadIdx.x;
-    const int quad = tid % Q;
-    const int s0 = tid / Q, sstep = Ts / Q;         // the thread's first site, site stride
-    uint32_t* sp = reinterpret_cast<uint32_t*>(S.spins);
-    // the thread's four walkers: threshold rows of their slots (fixed during a sweep), -1 for
-    // walkers beyond R
-    int trow[4];
+    const int oct = tid % O;
+    const int s0 = tid / O, sstep = Ts / O;         // the thread's first site, site stride
+    uint2* sp = reinterpret_cast<uint2*>(S.spins);
+    // the thread's eight walkers: threshold rows of their slots (fixed during a sweep); the
+    // walkers beyond R draw nothing and keep their bytes
+    int trow[8];
+    uint32_t valid = 0;
 #pragma unroll
-    for (int k4 = 0; k4 < 4; ++k4) {
-        const int w = quad * 4 + k4;
-        trow[k4] = (w < R) ? S.sow[w] * tw + Imax : -1;
+    for (int j = 0; j < 8; ++j) {
+        const int w = oct * 8 + j;
+        trow[j] = (w < R) ? S.sow[w] * tw + Imax : Imax;
+        valid |= (uint32_t)(w < R) << j;
     }
-    int e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    // byte masks of the valid walkers in the two words
+    const uint32_t vbyte[2] = {spread4(valid & 0xFu), spread4(valid >> 4)};
+    int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int cbeg = I.col_off[0];
     for (int c = 0; c < ncol; ++c) {
         const int base = cbeg;
@@ -109,97 +129,149 @@ __device__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
         const int nc = cbeg - base;
         for (int si = s0; si < nc && tid < Ts; si += sstep) {
             const int site = S.csites[base + si];
-            int hg[4], f[4];            // h + counted-neighbour sums, local fields
             const int split = S.rowl[site], end = S.rowp[site + 1];
-            if (packed) {
-                // bytes of ac / ar: 128 + sum of J over the neighbours whose spin is -1. With
-                // sum J m = sum J - 2 sum_{m=-1} J, h + the counted sum is hk.x - 2 byte(ac),
-                // and the local field hk.y - 2 (byte(ac) + byte(ar)).
-                uint32_t ac = 0x80808080u, ar = 0x80808080u;
+            // packed rows: bytes of cw / tw_: 128 + the sum of J over the counted / all
+            // neighbours whose spin is -1 (tw_ = cw + rw - 128 per byte, exact: every byte stays
+            // within 1..255). With sum J m = sum J - 2 sum_{m=-1} J, h + the counted sum is
+            // hk.x - 2 byte(cw) and the local field hk.y - 2 byte(tw_).
+            // general rows: hg, f the sums themselves.
+            uint32_t cw[2], tw_[2];
+            int2 kk;
+            int hg[PACKED ? 1 : 8], f[PACKED ? 1 : 8];
+            if constexpr (PACKED) {
+                uint32_t c0 = 0x80808080u, c1 = 0x80808080u, r0 = 0x80808080u, r1 = 0x80808080u;
                 // unrolled: the loads of several neighbours are in flight together
 #pragma unroll 4
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
-                    const int J = (int)(int8_t)(pk & 0xFFu);
-                    ac += (uint32_t)J * sp[(pk >> 8) + quad];
+                    const uint32_t J = (uint32_t)(int)(int8_t)(pk & 0xFFu);
+                    const uint2 nb = sp[(pk >> 8) + oct];
+                    c0 += J * nb.x;
+                    c1 += J * nb.y;
                 }
 #pragma unroll 4
                 for (int a2 = split; a2 < end; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
-                    const int J = (int)(int8_t)(pk & 0xFFu);
-                    ar += (uint32_t)J * sp[(pk >> 8) + quad];
+                    const uint32_t J = (uint32_t)(int)(int8_t)(pk & 0xFFu);
+                    const uint2 nb = sp[(pk >> 8) + oct];
+                    r0 += J * nb.x;
+                    r1 += J * nb.y;
                 }
-                const int2 kk = S.hk[site];
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const int bc = (int)((ac >> (8 * k4)) & 0xFFu);
-                    const int br = (int)((ar >> (8 * k4)) & 0xFFu);
-                    hg[k4] = kk.x - 2 * bc;
-                    f[k4] = kk.y - 2 * (bc + br);
-                }
+                cw[0] = c0;
+                cw[1] = c1;
+                tw_[0] = c0 + r0 - 0x80808080u;
+                tw_[1] = c1 + r1 - 0x80808080u;
+                kk = S.hk[site];
             } else {
                 const int hs = S.h[site];
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) hg[k4] = hs;
+                for (int j = 0; j < 8; ++j) hg[j] = hs;
                 for (int a2 = S.rowp[site]; a2 < split; ++a2) {
-                    const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                    const uint2 wd = sp[S.adj[a2] * O + oct];
                     const int J = S.adjJ[a2];
 #pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) hg[k4] += J * sbyte(wd, k4);
+                    for (int j = 0; j < 8; ++j) hg[j] += J * sbyte(j < 4 ? wd.x : wd.y, j & 3);
                 }
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) f[k4] = hg[k4];
+                for (int j = 0; j < 8; ++j) f[j] = hg[j];
                 for (int a2 = split; a2 < end; ++a2) {
-                    const uint32_t wd = sp[S.adj[a2] * Q + quad];
+                    const uint2 wd = sp[S.adj[a2] * O + oct];
                     const int J = S.adjJ[a2];
 #pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) f[k4] += J * sbyte(wd, k4);
+                    for (int j = 0; j < 8; ++j) f[j] += J * sbyte(j < 4 ? wd.x : wd.y, j & 3);
                 }
             }
-            const uint32_t own = sp[site * Q + quad];
-            const uint4 r = philox_rk(make_uint4((uint32_t)site, sweep_idx,
-                                                 (kDomWord << 24) | (uint32_t)quad, iid), a);
-            const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-            int nmv[4];
-            uint32_t out = own;
+            auto field = [&](int j) -> int {
+                if constexpr (PACKED) return kk.y - 2 * (int)((tw_[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                else return f[j];
+            };
+            auto counted = [&](int j) -> int {
+                if constexpr (PACKED) return kk.x - 2 * (int)((cw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                else return hg[j];
+            };
+            const uint2 own = sp[site * O + oct];
+            const uint32_t ob[2] = {own.x, own.y};
+            // threshold index of walker j; Metropolis: moves with m I <= 0 are taken outright
+            auto index = [&](int j) -> int {
+                if constexpr (GIBBS) return trow[j] + field(j);
+                else return trow[j] + max(sbyte(ob[j >> 2], j & 3) * field(j), 0);
+            };
+            uint32_t forced = 0;
+            if constexpr (!GIBBS) {
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                const int m = sbyte(own, k4);
-                nmv[k4] = m;
-                if (trow[k4] < 0) continue;
-                int nm;
-                if (update == 1) {
-                    nm = (u[k4] < S.thr[trow[k4] + f[k4]]) ? 1 : -1;
-                } else {
-                    const int mI = m * f[k4];   // dE = 2 m I
-                    nm = (mI <= 0 || u[k4] < S.thr[trow[k4] + mI]) ? -m : m;
+                for (int j = 0; j < 8; ++j)
+                    forced |= (uint32_t)(sbyte(ob[j >> 2], j & 3) * field(j) <= 0) << j;   // dE = 2 m I
+                forced &= valid;
+            }
+            const uint4 rh = philox_rk(make_uint4((uint32_t)site, sweep_idx,
+                                                  (kDomWord << 24) | (uint32_t)oct, iid), a);
+            const uint32_t hw[4] = {rh.x, rh.y, rh.z, rh.w};
+            uint32_t below = 0, tie = 0;   // u < thr on the high halves; undecided there
+            const uint32_t drawn = valid & ~forced;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (!(drawn >> j & 1u)) continue;
+                const uint32_t t = S.thr[index(j)];
+                const uint32_t x = (j & 1) ? (hw[j >> 1] << 16) : (hw[j >> 1] & 0xFFFF0000u);
+                below |= (uint32_t)(x < t) << j;
+                tie |= (uint32_t)(((x ^ t) >> 16) == 0u) << j;
+            }
+            tie &= valid & ~forced;        // forced moves and padding walkers need no low half
+            if (tie) {
+                const uint4 rl = philox_cold(make_uint4((uint32_t)site, sweep_idx,
+                                                        (kDomWord << 24) | (1u << 16) | (uint32_t)oct, iid),
+                                             (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+                const uint32_t lw[4] = {rl.x, rl.y, rl.z, rl.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (!(tie >> j & 1u)) continue;
+                    const uint32_t x = (j & 1) ? (hw[j >> 1] << 16) : (hw[j >> 1] & 0xFFFF0000u);
+                    const uint32_t lo = (j & 1) ? (lw[j >> 1] & 0xFFFFu) : (lw[j >> 1] >> 16);
+                    below = (below & ~(1u << j)) | ((uint32_t)((x | lo) < S.thr[index(j)]) << j);
                 }
-                nmv[k4] = nm;
-                out = (out & ~(0xFFu << (8 * k4))) | ((uint32_t)(nm < 0) << (8 * k4));
             }
-            if (out != own) sp[site * Q + quad] = out;
+            // new [m = -1] flags: Gibbs m = +1 iff u < thr; Metropolis flips if forced or u < thr
+            uint32_t out[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t nib = ((GIBBS ? ~below : (forced | below)) >> (4 * h)) & 0xFu;
+                out[h] = GIBBS ? ((ob[h] & ~vbyte[h]) | (spread4(nib) & vbyte[h]))
+                               : (ob[h] ^ (spread4(nib) & vbyte[h]));
+            }
             if (energy_on) {
-                e0 -= nmv[0] * hg[0];
-                e1 -= nmv[1] * hg[1];
-                e2 -= nmv[2] * hg[2];
-                e3 -= nmv[3] * hg[3];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int g = counted(j);
+                    e[j] += ((out[j >> 2] >> (8 * (j & 3))) & 1u) ? g : -g;
+                }
             }
+            if (out[0] != ob[0] || out[1] != ob[1]) sp[site * O + oct] = make_uint2(out[0], out[1]);
         }
         if (energy_on && c == ncol - 1 && tid < Ts) {
-            const int w = quad * 4;
-            if (e0) atomicAdd(&S.Eacc[w + 0], e0);
-            if (e1) atomicAdd(&S.Eacc[w + 1], e1);
-            if (e2) atomicAdd(&S.Eacc[w + 2], e2);
-            if (e3) atomicAdd(&S.Eacc[w + 3], e3);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (e[j]) atomicAdd(&S.Eacc[oct * 8 + j], e[j]);
         }
         __syncthreads();
+    }
+}
+
+// KIND 1: every instance of the launch has packed rows; 0: either kind, chosen per instance
+template <int KIND, bool GIBBS>
+__device__ __forceinline__ void graph_sweep(const GraphInst& I, GraphSmem& S, const RunArgs& a,
+                                            uint32_t sweep_idx, bool energy_on) {
+    if constexpr (KIND == 1) {
+        graph_sweep_t<true, GIBBS>(I, S, a, sweep_idx, energy_on);
+    } else {
+        if (I.packed) graph_sweep_t<true, GIBBS>(I, S, a, sweep_idx, energy_on);
+        else graph_sweep_t<false, GIBBS>(I, S, a, sweep_idx, energy_on);
     }
 }
 
 // E = Eclamp + the terms the last sweep accumulated; clears the accumulators. Ends
 // synchronised.
 __device__ void graph_energy_finish(const GraphInst& I, GraphSmem& S) {
-    for (int w = threadIdx.x; w < I.R4; w += blockDim.x) {
+    for (int w = threadIdx.x; w < I.Rp; w += blockDim.x) {
         S.E[w] = I.Eclamp + S.Eacc[w];
         S.Eacc[w] = 0;
     }
@@ -219,19 +291,19 @@ __device__ void graph_energy(const GraphInst& I, GraphSmem& S) {
                 if (I.packed) {
                     for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a) {
                         const uint32_t pk = (uint32_t)S.adjp[a];
-                        f += (int)(int8_t)(pk & 0xFFu) * (1 - 2 * (int)S.spins[(pk >> 8) * 4 + w]);
+                        f += (int)(int8_t)(pk & 0xFFu) * (1 - 2 * (int)S.spins[(pk >> 8) * 8 + w]);
                     }
                 } else {
                     for (int a = S.rowp[site]; a < S.rowp[site + 1]; ++a)
-                        f += S.adjJ[a] * (1 - 2 * (int)S.spins[S.adj[a] * I.R4 + w]);
+                        f += S.adjJ[a] * (1 - 2 * (int)S.spins[S.adj[a] * I.Rp + w]);
                 }
-                acc += (1 - 2 * (int)S.spins[site * I.R4 + w]) * (f + hs);
+                acc += (1 - 2 * (int)S.spins[site * I.Rp + w]) * (f + hs);
             }
             atomicAdd(&S.Eacc[w], acc);
         }
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < I.R4; w += blockDim.x) {
+    for (int w = threadIdx.x; w < I.Rp; w += blockDim.x) {
         S.E[w] = -(S.Eacc[w] / 2);
         S.Eacc[w] = 0;
     }
@@ -333,7 +405,7 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
             long long d = 0;
             for (int i = lane; i < N; i += 32) {
                 const long long wi = __ldg(lw + i);
-                if (S.spins[i * I.R4 + w] == 0) d += wi;          // current spin +1
+                if (S.spins[i * I.Rp + w] == 0) d += wi;          // current spin +1
                 if ((buf[i >> 5] >> (i & 31)) & 1u) d -= wi;      // proposed spin +1
             }
 #pragma unroll
@@ -378,24 +450,26 @@ __device__ void graph_propose(const GraphInst& I, GraphSmem& S, uint32_t k0, uin
         const int w = S.wos[r];
         const uint32_t* buf = S.pbuf + r * NW;
         for (int i = lane; i < N; i += 32)
-            S.spins[i * I.R4 + w] = (int8_t)(((buf[i >> 5] >> (i & 31)) & 1u) ^ 1u);
+            S.spins[i * I.Rp + w] = (int8_t)(((buf[i >> 5] >> (i & 31)) & 1u) ^ 1u);
     }
     __syncthreads();
     for (int r = tid; r < R; r += T) S.Eacc[r] = 0;
 }
 
-__global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict__ insts,
-                                                     RunArgs a, int with_pool) {
+// The fused cycle kernel's body (one block per instance); the kernels below instantiate it.
+template <int KIND, bool GIBBS>
+__device__ __forceinline__ void graph_body(const GraphInst* __restrict__ insts, const RunArgs& a,
+                                           int with_pool) {
     extern __shared__ __align__(16) uint8_t smem[];
     const GraphInst& I = insts[blockIdx.x];
     if (!*I.active) return;
     GraphSmem S = carve_graph(smem, I, with_pool != 0);
     const int tid = threadIdx.x, T = blockDim.x;
-    const int N = I.N, R = I.R, R4 = I.R4;
+    const int N = I.N, R = I.R, Rp = I.Rp;
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(I.spins);
         uint32_t* dst = reinterpret_cast<uint32_t*>(S.spins);
-        for (int i = tid; i < N * R4 / 4; i += T) dst[i] = src[i];
+        for (int i = tid; i < N * Rp / 4; i += T) dst[i] = src[i];
     }
     const int tw = 2 * I.Imax + 1;
     for (int i = tid; i < R * tw; i += T) S.thr[i] = I.thr[i];
@@ -421,7 +495,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
         for (int k = tid; k < I.nHb; k += T) S.ph_h[k] = I.ph_h[k];
     }
     for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
-    for (int i = tid; i < R4; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
+    for (int i = tid; i < Rp; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
     for (int i = tid; i < R; i += T) S.wos[i] = I.wos[i];
     for (int i = tid; i < 4 * R; i += T) S.st[i] = 0u;
     long long sweeps = I.ctr->sweeps, n_ex = I.ctr->n_ex, n_prop = I.ctr->n_prop;
@@ -431,7 +505,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeEnergy) graph_energy(I, S);
     if (a.mode & kModeSweeps) {
         for (int k = 0; k < a.n; ++k) {
-            graph_sweep(I, S, a, (uint32_t)sweeps, a.update, k == a.n - 1);
+            graph_sweep<KIND, GIBBS>(I, S, a, (uint32_t)sweeps, k == a.n - 1);
             ++sweeps;
         }
         if (a.n > 0) graph_energy_finish(I, S);
@@ -448,7 +522,7 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     if (a.mode & kModeCycles) {
         for (int cyc = 0; cyc < a.n; ++cyc) {
             for (int m = 0; m < a.M; ++m) {
-                graph_sweep(I, S, a, (uint32_t)sweeps, a.update, m == a.M - 1);
+                graph_sweep<KIND, GIBBS>(I, S, a, (uint32_t)sweeps, m == a.M - 1);
                 ++sweeps;
             }
             graph_energy_finish(I, S);
@@ -465,9 +539,9 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(S.spins);
         uint32_t* dst = reinterpret_cast<uint32_t*>(I.spins);
-        for (int i = tid; i < N * R4 / 4; i += T) dst[i] = src[i];
+        for (int i = tid; i < N * Rp / 4; i += T) dst[i] = src[i];
     }
-    for (int i = tid; i < R4; i += T) { I.E[i] = S.E[i]; I.sow[i] = S.sow[i]; }
+    for (int i = tid; i < Rp; i += T) { I.E[i] = S.E[i]; I.sow[i] = S.sow[i]; }
     for (int i = tid; i < R; i += T) I.wos[i] = S.wos[i];
     for (int i = tid; i < 4 * R; i += T)
         if (S.st[i]) I.stats[i] += S.st[i];
@@ -478,14 +552,29 @@ __global__ void __launch_bounds__(1024) graph_kernel(const GraphInst* __restrict
     }
 }
 
+// Launches whose instances all have packed rows: the register cap lets seven blocks of 128
+// threads share an SM (the shared-memory limit of the 8x8 multiplier) where the uncapped
+// kernel fits four.
+template <bool GIBBS>
+__global__ void __maxnreg__(72) graph_kernel_packed(const GraphInst* __restrict__ insts, RunArgs a,
+                                                    int with_pool) {
+    graph_body<1, GIBBS>(insts, a, with_pool);
+}
+
+template <bool GIBBS>
+__global__ void __launch_bounds__(512) graph_kernel(const GraphInst* __restrict__ insts, RunArgs a,
+                                                    int with_pool) {
+    graph_body<0, GIBBS>(insts, a, with_pool);
+}
+
 // Random initial state: walker w's spin at a free site is bit (w & 31) of output word 0 of
 // Philox(site, 0, w >> 5, id); clamped sites take their clamp value.
 __global__ void graph_init_kernel(const GraphInst* __restrict__ insts, uint64_t seed) {
     const GraphInst& I = insts[blockIdx.x];
     const int8_t* cl = I.clamp;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int idx = threadIdx.x; idx < I.N * I.R4; idx += blockDim.x) {
-        const int i = idx / I.R4, w = idx - i * I.R4;
+    for (int idx = threadIdx.x; idx < I.N * I.Rp; idx += blockDim.x) {
+        const int i = idx / I.Rp, w = idx - i * I.Rp;
         int8_t s = -1;
         if (w < I.R) {
             if (cl[i] != 0) {
@@ -511,7 +600,7 @@ __global__ void graph_capture_kernel(const GraphInst* __restrict__ dst,
         uint32_t word = 0;
         for (int b = 0; b < 32; ++b) {
             const int i = k * 32 + b;
-            if (i < N && Sr.spins[i * Sr.R4 + w] == 0) word |= 1u << b;
+            if (i < N && Sr.spins[i * Sr.Rp + w] == 0) word |= 1u << b;
         }
         const_cast<uint32_t*>(D.pool)[(size_t)entry * D.pstride + (size_t)r * NW + k] = word;
     }
@@ -522,7 +611,7 @@ __global__ void graph_read_kernel(const GraphInst* __restrict__ insts, int inst,
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
          idx += gridDim.x * blockDim.x) {
         const int r = idx / I.N, i = idx - r * I.N;
-        out[idx] = (int8_t)(1 - 2 * I.spins[i * I.R4 + I.wos[r]]);
+        out[idx] = (int8_t)(1 - 2 * I.spins[i * I.Rp + I.wos[r]]);
     }
 }
 
@@ -532,17 +621,28 @@ __global__ void graph_write_kernel(const GraphInst* __restrict__ insts, int inst
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < I.R * I.N;
          idx += gridDim.x * blockDim.x) {
         const int r = idx / I.N, i = idx - r * I.N;
-        I.spins[i * I.R4 + walker[r]] = (int8_t)(in[idx] < 0);
+        I.spins[i * I.Rp + walker[r]] = (int8_t)(in[idx] < 0);
     }
 }
 
 cudaError_t configure_graph_kernels(int smem) {
-    return cudaFuncSetAttribute(graph_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(graph_kernel_packed<true>, at, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_kernel_packed<false>, at, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_kernel<true>, at, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(graph_kernel<false>, at, smem);
+    return e;
 }
 
+// packed_only: every instance of d_insts has packed rows; gibbs: the Gibbs rule (else
+// Metropolis)
 cudaError_t launch_graph(const GraphInst* d_insts, int n, int threads, size_t smem,
-                         const RunArgs& a, int with_pool, cudaStream_t stream) {
-    graph_kernel<<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+                         const RunArgs& a, int with_pool, bool packed_only, bool gibbs,
+                         cudaStream_t stream) {
+    if (packed_only && gibbs) graph_kernel_packed<true><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else if (packed_only) graph_kernel_packed<false><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else if (gibbs) graph_kernel<true><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
+    else graph_kernel<false><<<n, threads, smem, stream>>>(d_insts, a, with_pool);
     return cudaGetLastError();
 }
 cudaError_t launch_graph_init(const GraphInst* d, int n, uint64_t seed, cudaStream_t s) {

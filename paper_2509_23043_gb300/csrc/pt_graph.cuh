@@ -6,26 +6,27 @@
 
 namespace pt {
 
-// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spin bytes [N][R4].
+// Graph engine: CSR couplings, fields, clamps, Gibbs or Metropolis. Spin bytes [N][Rp], Rp = R rounded up to 8.
 struct GraphInst {
     uint32_t iid;
-    int32_t N, R, R4, NW, ncol, P, NE, Imax, nfree;
+    int32_t N, R, Rp, NW, ncol, P, NE, Imax, nfree;
     int32_t Eclamp;          // energy of the clamped spins: their fields and mutual bonds
     int32_t col_off[33];
-    int8_t* spins;           // [N][R4]: 1 where the spin is -1, 0 where it is +1
+    int8_t* spins;           // [N][Rp]: 1 where the spin is -1, 0 where it is +1
     const int8_t* clamp;     // [N]: 0 free, +-1 clamped
     const int32_t* rowp;     // [N+1] CSR row offsets (each edge seen from both ends)
     const int32_t* rowl;     // [N] a free site's row lists first its "counted" neighbours
                              // (clamped or of a lower colour), rowp[i] .. rowl[i]-1
     const int32_t* adj;      // [2 NE] neighbour index
     const int32_t* adjJ;     // [2 NE] coupling
-    const int32_t* adjp;     // [2 NE] packed = (neighbour * R4/4) << 8 | (uint8) coupling, used
-                             // when `packed` (every |coupling| and every site's sum of them <= 127)
+    const int32_t* adjp;     // [2 NE] packed = (neighbour * Rp/8) << 8 | (uint8) coupling, the
+                             // neighbour's row in units of eight walkers; used when `packed`
+                             // (every |coupling| and every site's sum of them <= 127)
     int32_t packed;
     const int32_t* h;        // [N]
     const int2* hk;          // [N] packed rows only: {h + sum of J over the counted neighbours
-                             // + 256, that + sum of J over the others + 256}, the constants of
-                             // the biased byte sums (graph_sweep)
+                             // + 256, that + sum of J over the others}, the constants of the
+                             // biased byte sums (graph_sweep)
     const int32_t* csites;   // [nfree] free sites in colour order
     // proposal energies: E = Kprop + 2 (sum_e J_e [m_a != m_b] - sum_i h_i [m_i = +1]), with
     // the edges and the sites of nonzero field in blocks of 32 of one coupling (field) value,
@@ -36,8 +37,8 @@ struct GraphInst {
     const int32_t* ph_i;     // [32 nHb] site
     const int32_t* ph_h;     // [nHb]
     const uint32_t* cbits;   // [2][NW]: clamped mask, clamp value (+1) bits
-    int32_t* E;              // [R4] per walker
-    int16_t* sow;            // [R4]
+    int32_t* E;              // [Rp] per walker
+    int16_t* sow;            // [Rp]
     int16_t* wos;            // [R]
     const uint32_t* thr;     // [R][2*Imax+1]
     const double* beta;      // [R]
@@ -61,11 +62,11 @@ struct GraphLayout {
 // only adj, adjJ and the fields h. With a pool: every slot's staged proposal (bit-packed,
 // [R][NW]), the same transposed to one word per site and group of 32 slots ([ceil(R/32)][N+1],
 // word N zero), and the proposal-energy blocks.
-PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, int nfree, int NW,
+PT_HD inline GraphLayout graph_layout(int N, int R, int Rp, int NE, int Imax, int nfree, int NW,
                                       bool with_pool, bool packed, int nEb, int nHb) {
     GraphLayout l;
     size_t o = 0;
-    l.spins = o;  o = align16(o + (size_t)N * R4);
+    l.spins = o;  o = align16(o + (size_t)N * Rp);
     l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
     l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
     l.rowl = o;   o = align16(o + (size_t)N * 4);
@@ -75,10 +76,10 @@ PT_HD inline GraphLayout graph_layout(int N, int R, int R4, int NE, int Imax, in
     l.h = o;      o = align16(o + (packed ? 0 : (size_t)N * 4));
     l.hk = o;     o = align16(o + (packed ? (size_t)N * 8 : 0));
     l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
-    l.E = o;      o = align16(o + (size_t)R4 * 4);
-    l.Eacc = o;   o = align16(o + (size_t)R4 * 4);
+    l.E = o;      o = align16(o + (size_t)Rp * 4);
+    l.Eacc = o;   o = align16(o + (size_t)Rp * 4);
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
-    l.sow = o;    o = align16(o + (size_t)R4 * 2);
+    l.sow = o;    o = align16(o + (size_t)Rp * 2);
     l.wos = o;    o = align16(o + (size_t)R * 2);
     const size_t wp = with_pool ? 1 : 0;
     l.pbuf = o;   o = align16(o + wp * R * NW * 4);
