@@ -18,13 +18,12 @@ struct GraphSmem {
     int8_t* spins;
     uint32_t* thr;
     int32_t* rowp;
-    int32_t* rowl;
+    int4* smeta;                 // [nfree] {site, row begin, row split, row end}, colour order
     int32_t* adj;
     int32_t* adjJ;
     int32_t* adjp;
     int32_t* h;
-    int2* hk;
-    int32_t* csites;
+    int2* hk;                    // [nfree] colour order
     int32_t* E;
     int32_t* Eacc;
     uint32_t* st;
@@ -46,13 +45,12 @@ __device__ __forceinline__ GraphSmem carve_graph(uint8_t* base, const GraphInst&
     S.spins = reinterpret_cast<int8_t*>(base + l.spins);
     S.thr = reinterpret_cast<uint32_t*>(base + l.thr);
     S.rowp = reinterpret_cast<int32_t*>(base + l.rowp);
-    S.rowl = reinterpret_cast<int32_t*>(base + l.rowl);
+    S.smeta = reinterpret_cast<int4*>(base + l.smeta);
     S.adj = reinterpret_cast<int32_t*>(base + l.adj);
     S.adjJ = reinterpret_cast<int32_t*>(base + l.adjJ);
     S.adjp = reinterpret_cast<int32_t*>(base + l.adjp);
     S.h = reinterpret_cast<int32_t*>(base + l.h);
     S.hk = reinterpret_cast<int2*>(base + l.hk);
-    S.csites = reinterpret_cast<int32_t*>(base + l.csites);
     S.E = reinterpret_cast<int32_t*>(base + l.E);
     S.Eacc = reinterpret_cast<int32_t*>(base + l.Eacc);
     S.st = reinterpret_cast<uint32_t*>(base + l.st);
@@ -128,8 +126,8 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
         cbeg = I.col_off[c + 1];
         const int nc = cbeg - base;
         for (int si = s0; si < nc && tid < Ts; si += sstep) {
-            const int site = S.csites[base + si];
-            const int split = S.rowl[site], end = S.rowp[site + 1];
+            const int4 meta = S.smeta[base + si];
+            const int site = meta.x, split = meta.z, end = meta.w;
             // packed rows: bytes of cw / tw_: 128 + the sum of J over the counted / all
             // neighbours whose spin is -1 (tw_ = cw + rw - 128 per byte, exact: every byte stays
             // within 1..255). With sum J m = sum J - 2 sum_{m=-1} J, h + the counted sum is
@@ -142,7 +140,7 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
                 uint32_t c0 = 0x80808080u, c1 = 0x80808080u, r0 = 0x80808080u, r1 = 0x80808080u;
                 // unrolled: the loads of several neighbours are in flight together
 #pragma unroll 4
-                for (int a2 = S.rowp[site]; a2 < split; ++a2) {
+                for (int a2 = meta.y; a2 < split; ++a2) {
                     const uint32_t pk = (uint32_t)S.adjp[a2];
                     const uint32_t J = (uint32_t)(int)(int8_t)(pk & 0xFFu);
                     const uint2 nb = sp[(pk >> 8) + oct];
@@ -161,12 +159,12 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
                 cw[1] = c1;
                 tw_[0] = c0 + r0 - 0x80808080u;
                 tw_[1] = c1 + r1 - 0x80808080u;
-                kk = S.hk[site];
+                kk = S.hk[base + si];
             } else {
                 const int hs = S.h[site];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) hg[j] = hs;
-                for (int a2 = S.rowp[site]; a2 < split; ++a2) {
+                for (int a2 = meta.y; a2 < split; ++a2) {
                     const uint2 wd = sp[S.adj[a2] * O + oct];
                     const int J = S.adjJ[a2];
 #pragma unroll
@@ -474,7 +472,6 @@ __device__ __forceinline__ void graph_body(const GraphInst* __restrict__ insts, 
     const int tw = 2 * I.Imax + 1;
     for (int i = tid; i < R * tw; i += T) S.thr[i] = I.thr[i];
     for (int i = tid; i <= N; i += T) S.rowp[i] = I.rowp[i];
-    for (int i = tid; i < N; i += T) S.rowl[i] = I.rowl[i];
     if (I.packed) {
         for (int i = tid; i < 2 * I.NE; i += T) S.adjp[i] = I.adjp[i];
     } else {
@@ -483,18 +480,19 @@ __device__ __forceinline__ void graph_body(const GraphInst* __restrict__ insts, 
             S.adjJ[i] = I.adjJ[i];
         }
     }
-    if (I.packed) {
-        for (int i = tid; i < N; i += T) S.hk[i] = I.hk[i];
-    } else {
-        for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
+    for (int i = tid; i < I.nfree; i += T) {
+        const int site = I.csites[i];
+        S.smeta[i] = make_int4(site, I.rowp[site], I.rowl[site], I.rowp[site + 1]);
+        if (I.packed) S.hk[i] = I.hk[site];
     }
+    if (!I.packed)
+        for (int i = tid; i < N; i += T) S.h[i] = I.h[i];
     if (with_pool) {
         for (int k = tid; k < 32 * I.nEb; k += T) S.pe_ab[k] = I.pe_ab[k];
         for (int k = tid; k < I.nEb; k += T) S.pe_J[k] = I.pe_J[k];
         for (int k = tid; k < 32 * I.nHb; k += T) S.ph_i[k] = I.ph_i[k];
         for (int k = tid; k < I.nHb; k += T) S.ph_h[k] = I.ph_h[k];
     }
-    for (int i = tid; i < I.nfree; i += T) S.csites[i] = I.csites[i];
     for (int i = tid; i < Rp; i += T) { S.E[i] = I.E[i]; S.Eacc[i] = 0; S.sow[i] = I.sow[i]; }
     for (int i = tid; i < R; i += T) S.wos[i] = I.wos[i];
     for (int i = tid; i < 4 * R; i += T) S.st[i] = 0u;

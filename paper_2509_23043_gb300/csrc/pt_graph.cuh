@@ -54,12 +54,13 @@ struct GraphInst {
 };
 
 struct GraphLayout {
-    size_t spins, thr, rowp, rowl, adj, adjJ, adjp, h, hk, csites, E, Eacc, st, sow, wos, pbuf, pM,
+    size_t spins, thr, rowp, smeta, adj, adjJ, adjp, h, hk, E, Eacc, st, sow, wos, pbuf, pM,
         pe_ab, pe_J, ph_i, ph_h, total;
 };
 
-// Packed instances keep only the packed rows (adjp) and the per-site constants hk; the others
-// only adj, adjJ and the fields h. With a pool: every slot's staged proposal (bit-packed,
+// The free sites in colour order as records {site, row begin, row split, row end} (smeta).
+// Packed instances keep only the packed rows (adjp) and the per-site constants hk, in colour
+// order beside smeta; the others only adj, adjJ and the fields h (by site). With a pool: every slot's staged proposal (bit-packed,
 // [R][NW]), the same transposed to one word per site and group of 32 slots ([ceil(R/32)][N+1],
 // word N zero), and the proposal-energy blocks.
 PT_HD inline GraphLayout graph_layout(int N, int R, int Rp, int NE, int Imax, int nfree, int NW,
@@ -69,13 +70,12 @@ PT_HD inline GraphLayout graph_layout(int N, int R, int Rp, int NE, int Imax, in
     l.spins = o;  o = align16(o + (size_t)N * Rp);
     l.thr = o;    o = align16(o + (size_t)R * (2 * Imax + 1) * 4);
     l.rowp = o;   o = align16(o + (size_t)(N + 1) * 4);
-    l.rowl = o;   o = align16(o + (size_t)N * 4);
+    l.smeta = o;  o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 16);
     l.adj = o;    o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
     l.adjJ = o;   o = align16(o + (packed ? 0 : (size_t)2 * NE * 4));
     l.adjp = o;   o = align16(o + (packed ? (size_t)2 * NE * 4 : 0));
     l.h = o;      o = align16(o + (packed ? 0 : (size_t)N * 4));
-    l.hk = o;     o = align16(o + (packed ? (size_t)N * 8 : 0));
-    l.csites = o; o = align16(o + (size_t)(nfree > 0 ? nfree : 1) * 4);
+    l.hk = o;     o = align16(o + (packed ? (size_t)(nfree > 0 ? nfree : 1) * 8 : 0));
     l.E = o;      o = align16(o + (size_t)Rp * 4);
     l.Eacc = o;   o = align16(o + (size_t)Rp * 4);
     l.st = o;     o = align16(o + (size_t)4 * R * 4);
