@@ -15,9 +15,10 @@
  * accumulates in FP32 (tensor cores). The residual stream is FP32; the outputs of the first
  * FFN map (GELU evaluated in FP32 and stored in place) and, for the tensor-core attention,
  * the queries, keys, values and softmax probabilities are stored in bfloat16. Embeddings,
- * layer norms, softmax and the head compute in FP32. The projections run as cuBLASLt matrix
- * products with a bias (and residual) epilogue; every other step runs in this library's
- * kernels.
+ * layer norms, softmax and the head compute in FP32. The projections run as this library's
+ * tcgen05 matrix products or as cuBLASLt products (proj_mode), with the bias (and GELU or the
+ * residual add) in the epilogue; the attention's two batched products run on cuBLASLt; every
+ * other step runs in this library's kernels.
  *
  * Conventions: every device pointer is caller-owned device memory on the device of the
  * context, read or written in stream order on the context's stream; host pointers are read
@@ -43,7 +44,17 @@ typedef struct pt_former pt_former;
  * attn_mode selects the scoring pass's attention: 0 = automatic (on the tensor cores, as
  * batched bfloat16 products around a causal-softmax kernel, when the scores and probabilities
  * of one layer, 6 B H N^2 bytes, fit 2 GiB; else the streaming kernel), 1 = always the
- * streaming kernel (FP32, keys and values streamed through shared memory, softmax online). */
+ * streaming kernel (FP32, keys and values streamed through shared memory, softmax online).
+ * proj_mode selects the projections' matrix products. This library's tcgen05 kernels
+ * (TMA-fed, FP32 accumulators in tensor memory, the bias and GELU or the residual add in the
+ * epilogue) take projections whose output width is a multiple of 256 and input width a
+ * multiple of 64.
+ *   0 = automatic: the first FFN map (bias and GELU fused) on the tcgen05 kernel when a call
+ *       has at least 16384 rows (B N for scoring); every other product on cuBLASLt, the GELU
+ *       in a kernel of its own otherwise;
+ *   1 = cuBLASLt products throughout;
+ *   2 = the tcgen05 kernels for every projection that suits them (the output map, both FFN
+ *       maps, and the query/key/value map of the tensor-core attention), at any row count. */
 typedef struct {
     int32_t n_spins;
     int32_t d_model;
@@ -51,6 +62,7 @@ typedef struct {
     int32_t n_layers;
     int32_t d_ff;
     int32_t attn_mode;
+    int32_t proj_mode;
 } pt_former_config;
 
 /* Number of bfloat16 parameters of a shape: 3d + 2d (embeddings), per layer
@@ -92,6 +104,11 @@ pt_status pt_former_sample(pt_former *m, int32_t B, const float *beta, const int
 /* Floating-point operations of the matrix products of one scoring pass over B configurations
  * (2 M K N per product, M = B N rows), for roofline accounting. */
 double pt_former_score_gemm_flops(const pt_former *m, int32_t B);
+
+/* Wait for the model's stream and report whether a bounded wait inside a tcgen05 product kernel
+ * ran out since creation (PT_ECUDA, with the wait's code in the message; the flag stays set).
+ * PT_OK otherwise. Synchronises the stream. */
+pt_status pt_former_check(pt_former *m);
 
 /* Release the model and its buffers. NULL is allowed. */
 pt_status pt_former_destroy(pt_former *m);

@@ -27,6 +27,7 @@
 
 #include "../../include/pt_former.h"
 #include "pt_device.cuh"
+#include "pt_gemm_tc.h"
 
 namespace {
 
@@ -423,6 +424,8 @@ struct Layer {
     float *ln1_g, *ln1_b, *b_qkv, *b_o, *ln2_g, *ln2_b, *b_2;
     __nv_bfloat16 *w_qkv, *w_o, *w_1, *w_2;
     __nv_bfloat16 *b_qkv16, *b_1;   // the biases of the products with bfloat16 output
+    // the weight matrices transposed ([out][in], K-major), for the tcgen05 products
+    __nv_bfloat16 *w_qkvt, *w_ot, *w_1t, *w_2t;
 };
 
 struct Act {                       // activation buffers for `rows` rows
@@ -458,6 +461,9 @@ struct pt_former {
     cudaGraphExec_t gexec = nullptr;
     std::tuple<int, int, const void*, const void*, const void*, const void*> gkey{};
     std::map<std::vector<long long>, cublasLtMatmulAlgo_t> algos;   // by product shape, layout, alignment
+    bool proj_tc = false;          // the tcgen05 kernels are set up (proj_mode 0 or 2)
+    int num_sms = 0;
+    int* d_err = nullptr;          // nonzero once a wait of a tcgen05 kernel ran out
 };
 
 namespace {
@@ -485,6 +491,14 @@ pt_status upload_bf16(pt_former* m, __nv_bfloat16** dst, const uint16_t* src, si
     if (s != PT_OK) return s;
     FCK(cudaMemcpy(*dst, src, n * 2, cudaMemcpyHostToDevice));
     return PT_OK;
+}
+
+// a row-major [rows][cols] bfloat16 matrix, uploaded transposed ([cols][rows])
+pt_status upload_transposed(pt_former* m, __nv_bfloat16** dst, const uint16_t* src, int rows, int cols) {
+    std::vector<uint16_t> t((size_t)rows * cols);
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = src[(size_t)r * cols + c];
+    return upload_bf16(m, dst, t.data(), t.size());
 }
 
 void free_act(Act& a) {
@@ -713,25 +727,52 @@ void launch_head_sample(pt_former* m, const int8_t* prefix, int npre, int8_t* ou
                                                               m->cfg.n_spins, t);
 }
 
+// rows from which proj_mode 0 takes the first FFN map to the tcgen05 kernel: 128 tiles of
+// 128 rows, enough to keep the persistent grid busy (sampling steps, one row per
+// configuration, stay on cuBLASLt)
+constexpr size_t kTcMinRows = 16384;
+
 // one pre-layer-norm block on rows [0, M) of `a` (attention by `attn`; query/key/value to
-// the bfloat16 buffer when qkv_bf16, the operand layout of the tensor-core attention)
+// the bfloat16 buffer when qkv_bf16, the operand layout of the tensor-core attention). The
+// products run on this library's tcgen05 kernels (bias, GELU and residual in their
+// epilogues) or on cuBLASLt as proj_mode says (include/pt_former.h).
 template <class AttnFn>
 pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, AttnFn attn) {
     const int d = m->cfg.d_model, F = m->cfg.d_ff;
+    const bool tc = m->cfg.proj_mode == 2;                        // every suitable projection
+    const bool tc_ffn1 = tc || (m->cfg.proj_mode == 0 && M >= kTcMinRows);
+    auto tc_gemm = [&](int epi, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const void* b, void* C, int n,
+                       int k) -> pt_status {
+        FCK(gemm_tc(epi, A, Wt, b, C, (int)M, n, k, m->num_sms, m->d_err, m->exec));
+        return PT_OK;
+    };
     pt_status s = layernorm(m, x.h, Ly.ln1_g, Ly.ln1_b, x.a, M);
-    if (s == PT_OK)
-        s = qkv_bf16 ? gemm(m, x.qkv16, CUDA_R_16BF, x.a, Ly.w_qkv, Ly.b_qkv16, M, 3 * d, d, false)
-                     : gemm(m, x.qkv, CUDA_R_32F, x.a, Ly.w_qkv, Ly.b_qkv, M, 3 * d, d, false);
-    if (s == PT_OK) s = attn();
-    if (s == PT_OK) s = gemm(m, x.h, CUDA_R_32F, x.o, Ly.w_o, Ly.b_o, M, d, d, true);
-    if (s == PT_OK) s = layernorm(m, x.h, Ly.ln2_g, Ly.ln2_b, x.a, M);
-    if (s == PT_OK) s = gemm(m, x.g, CUDA_R_16BF, x.a, Ly.w_1, Ly.b_1, M, F, d, false);
     if (s == PT_OK) {
-        const size_t n8 = M * (size_t)F / 8;           // F is a multiple of 8
-        gelu_kernel<<<(unsigned)std::min<size_t>((n8 + 255) / 256, 152 * 16), 256, 0, m->exec>>>(x.g, n8);
-        FCK(cudaGetLastError());
+        if (qkv_bf16 && tc && gemm_tc_supported(3 * d, d))
+            s = tc_gemm(kEpiBias, x.a, Ly.w_qkvt, Ly.b_qkv16, x.qkv16, 3 * d, d);
+        else if (qkv_bf16)
+            s = gemm(m, x.qkv16, CUDA_R_16BF, x.a, Ly.w_qkv, Ly.b_qkv16, M, 3 * d, d, false);
+        else
+            s = gemm(m, x.qkv, CUDA_R_32F, x.a, Ly.w_qkv, Ly.b_qkv, M, 3 * d, d, false);
     }
-    if (s == PT_OK) s = gemm(m, x.h, CUDA_R_32F, x.g, Ly.w_2, Ly.b_2, M, d, F, true);
+    if (s == PT_OK) s = attn();
+    if (s == PT_OK)
+        s = tc && gemm_tc_supported(d, d) ? tc_gemm(kEpiResid, x.o, Ly.w_ot, Ly.b_o, x.h, d, d)
+                                          : gemm(m, x.h, CUDA_R_32F, x.o, Ly.w_o, Ly.b_o, M, d, d, true);
+    if (s == PT_OK) s = layernorm(m, x.h, Ly.ln2_g, Ly.ln2_b, x.a, M);
+    if (s == PT_OK && tc_ffn1 && gemm_tc_supported(F, d)) {
+        s = tc_gemm(kEpiGelu, x.a, Ly.w_1t, Ly.b_1, x.g, F, d);
+    } else if (s == PT_OK) {
+        s = gemm(m, x.g, CUDA_R_16BF, x.a, Ly.w_1, Ly.b_1, M, F, d, false);
+        if (s == PT_OK) {
+            const size_t n8 = M * (size_t)F / 8;       // F is a multiple of 8
+            gelu_kernel<<<(unsigned)std::min<size_t>((n8 + 255) / 256, 152 * 16), 256, 0, m->exec>>>(x.g, n8);
+            FCK(cudaGetLastError());
+        }
+    }
+    if (s == PT_OK)
+        s = tc && gemm_tc_supported(d, F) ? tc_gemm(kEpiResid, x.g, Ly.w_2t, Ly.b_2, x.h, d, F)
+                                          : gemm(m, x.h, CUDA_R_32F, x.g, Ly.w_2, Ly.b_2, M, d, F, true);
     return s;
 }
 
@@ -783,7 +824,7 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
     const int d = cfg->d_model, F = cfg->d_ff;
     if (cfg->n_spins < 1 || cfg->n_layers < 0 || cfg->n_heads < 1 || d != 64 * cfg->n_heads ||
         (d != 64 && d != 128 && d != 256 && d != 512) || F < 8 || F % 8 != 0 ||
-        cfg->attn_mode < 0 || cfg->attn_mode > 1)
+        cfg->attn_mode < 0 || cfg->attn_mode > 1 || cfg->proj_mode < 0 || cfg->proj_mode > 2)
         return ffail(PT_EINVAL, "unsupported shape (d_model must be 64 x n_heads, one of 64..512; d_ff a multiple of 8)");
     if (n_params != pt_former_param_count(cfg))
         return ffail(PT_EINVAL, "%zu parameters given, the shape has %zu", n_params, pt_former_param_count(cfg));
@@ -808,17 +849,25 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
         Layer& L = m->layers[l];
         s = upload_f32(m, &L.ln1_g, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln1_b, take(d), d);
-        if (s == PT_OK) s = upload_bf16(m, &L.w_qkv, take(3 * (size_t)d * d), 3 * (size_t)d * d);
+        const uint16_t* wq = take(3 * (size_t)d * d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_qkv, wq, 3 * (size_t)d * d);
+        if (s == PT_OK) s = upload_transposed(m, &L.w_qkvt, wq, d, 3 * d);
         const uint16_t* bq = take(3 * (size_t)d);
         if (s == PT_OK) s = upload_f32(m, &L.b_qkv, bq, 3 * (size_t)d);
         if (s == PT_OK) s = upload_bf16(m, &L.b_qkv16, bq, 3 * (size_t)d);
-        if (s == PT_OK) s = upload_bf16(m, &L.w_o, take((size_t)d * d), (size_t)d * d);
+        const uint16_t* wo = take((size_t)d * d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_o, wo, (size_t)d * d);
+        if (s == PT_OK) s = upload_transposed(m, &L.w_ot, wo, d, d);
         if (s == PT_OK) s = upload_f32(m, &L.b_o, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln2_g, take(d), d);
         if (s == PT_OK) s = upload_f32(m, &L.ln2_b, take(d), d);
-        if (s == PT_OK) s = upload_bf16(m, &L.w_1, take((size_t)d * F), (size_t)d * F);
+        const uint16_t* w1 = take((size_t)d * F);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_1, w1, (size_t)d * F);
+        if (s == PT_OK) s = upload_transposed(m, &L.w_1t, w1, d, F);
         if (s == PT_OK) s = upload_bf16(m, &L.b_1, take(F), F);
-        if (s == PT_OK) s = upload_bf16(m, &L.w_2, take((size_t)F * d), (size_t)F * d);
+        const uint16_t* w2 = take((size_t)F * d);
+        if (s == PT_OK) s = upload_bf16(m, &L.w_2, w2, (size_t)F * d);
+        if (s == PT_OK) s = upload_transposed(m, &L.w_2t, w2, F, d);
         if (s == PT_OK) s = upload_f32(m, &L.b_2, take(d), d);
     }
     if (s == PT_OK) s = upload_f32(m, &m->lnf_g, take(d), d);
@@ -840,6 +889,17 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
             s = ffail(PT_ECUDA, "positional code upload");
     }
     if (s == PT_OK) s = dalloc(m, &m->d_sargs, 1);
+    if (s == PT_OK) s = dalloc(m, &m->d_err, 1);
+    if (s == PT_OK && cudaMemset(m->d_err, 0, sizeof(int)) != cudaSuccess) s = ffail(PT_ECUDA, "error flag");
+    m->proj_tc = cfg->proj_mode != 1;
+    if (s == PT_OK && m->proj_tc) {
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        const cudaError_t e2 = e == cudaSuccess ? gemm_tc_setup() : e;
+        if (e2 != cudaSuccess || m->num_sms < 1)
+            s = ffail(PT_ECUDA, "tcgen05 product set-up: %s", cudaGetErrorString(e2));
+    }
     if (s != PT_OK) {
         pt_former_destroy(m);
         return s;
@@ -944,6 +1004,15 @@ double pt_former_score_gemm_flops(const pt_former* m, int32_t B) {
     if (!m) return 0.0;
     const double M = (double)B * m->cfg.n_spins, d = m->cfg.d_model, F = m->cfg.d_ff;
     return m->cfg.n_layers * 2.0 * M * (d * 3 * d + d * d + d * F + F * d);
+}
+
+pt_status pt_former_check(pt_former* m) {
+    if (!m) return ffail(PT_EINVAL, "NULL argument");
+    FCK(cudaStreamSynchronize(m->stream));
+    int e = 0;
+    FCK(cudaMemcpy(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) return ffail(PT_ECUDA, "tcgen05 product kernel: a wait ran out (code %d)", e);
+    return PT_OK;
 }
 
 pt_status pt_former_destroy(pt_former* m) {

@@ -19,7 +19,8 @@ _lib = None
 
 class _Cfg(C.Structure):
     _fields_ = [("n_spins", C.c_int32), ("d_model", C.c_int32), ("n_heads", C.c_int32),
-                ("n_layers", C.c_int32), ("d_ff", C.c_int32), ("attn_mode", C.c_int32)]
+                ("n_layers", C.c_int32), ("d_ff", C.c_int32), ("attn_mode", C.c_int32),
+                ("proj_mode", C.c_int32)]
 
 
 def lib():
@@ -38,8 +39,9 @@ def lib():
     L.pt_former_score_gemm_flops.argtypes = [vp, C.c_int32]
     L.pt_former_score_gemm_flops.restype = C.c_double
     L.pt_former_destroy.argtypes = [vp]
+    L.pt_former_check.argtypes = [vp]
     L.pt_former_last_error.restype = C.c_char_p
-    for f in ("pt_former_create", "pt_former_score", "pt_former_sample", "pt_former_destroy"):
+    for f in ("pt_former_create", "pt_former_score", "pt_former_sample", "pt_former_destroy", "pt_former_check"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -57,12 +59,15 @@ def _dp(t):
 class Former:
     """One IsingFormer on the current CUDA device and stream."""
 
-    def __init__(self, shape, packed_params: np.ndarray, stream=None, attn_mode: int = 0):
+    def __init__(self, shape, packed_params: np.ndarray, stream=None, attn_mode: int = 0, proj_mode: int = 0):
         """attn_mode 0: scoring attention on the tensor cores where its scores fit, else the
-        streaming kernel; 1: always the streaming kernel."""
+        streaming kernel; 1: always the streaming kernel. proj_mode 0: the first FFN map by
+        this library's tcgen05 kernel (bias and GELU fused) from 16384 rows, cuBLASLt for the
+        rest; 1: cuBLASLt products and a GELU kernel; 2: the tcgen05 kernels for every
+        projection whose shape suits them (bias, GELU, residual fused), at any size."""
         import torch
         self.shape = shape
-        self.cfg = _Cfg(shape.n_spins, shape.d_model, shape.n_heads, shape.n_layers, shape.d_ff, attn_mode)
+        self.cfg = _Cfg(shape.n_spins, shape.d_model, shape.n_heads, shape.n_layers, shape.d_ff, attn_mode, proj_mode)
         p = np.ascontiguousarray(packed_params, dtype=np.uint16)
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         h = C.c_void_p()
@@ -94,6 +99,10 @@ class Former:
         _check(lib().pt_former_sample(self.handle, B, _dp(beta), _dp(prefix), npre, seed & 0xFFFFFFFFFFFFFFFF,
                                       stream_id & 0xFFFFFFFF, _dp(out), _dp(logq)))
         return out, logq
+
+    def check(self):
+        """Raise if a bounded wait of a tcgen05 product kernel ran out (synchronises)."""
+        _check(lib().pt_former_check(self.handle))
 
     def score_gemm_flops(self, B: int) -> float:
         return float(lib().pt_former_score_gemm_flops(self.handle, B))

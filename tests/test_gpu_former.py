@@ -43,6 +43,63 @@ def test_score_matches_oracle(N, B, attn_mode):
     assert np.all(np.abs(lq - lq_o) <= 0.02 * np.sqrt(N) + 0.01 * np.abs(lq_o)), (lq, lq_o)
 
 
+@pytest.mark.parametrize("N,B", [(37, 3), (200, 5), (64, 2)])
+def test_tcgen05_projections_match_library_products(N, B):
+    # Every projection by this library's tcgen05 kernels (proj_mode 2: bias, GELU and the
+    # residual add in their epilogues) against cuBLASLt products and the GELU kernel
+    # (proj_mode 1): the same bfloat16 operands and FP32 accumulation, so the paths differ by
+    # accumulation order and by the rounding of the FFN activations (one rounding to bfloat16
+    # in the kernel, two in the library path). Rows M = B N = 111, 1000 and 128: a partial
+    # tile, several tiles with a ragged tail, one tile.
+    from paper_2509_23043_gb300.former import Former
+    shp = I.FormerShape(n_spins=N)
+    W, packed = I.former_weights(shp, index=N + 1)
+    tc = Former(shp, packed, proj_mode=2)
+    lib = Former(shp, packed, proj_mode=1)
+    g = np.random.default_rng(N + 7)
+    X = torch.from_numpy(np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)).cuda()
+    beta = torch.from_numpy(g.uniform(0.1, 3.0, B).astype(np.float32)).cuda()
+    for _ in range(2):                        # two calls in a row on the same buffers
+        lq0, lg0 = tc.score(X, beta, logits=True)
+        lq1, lg1 = lib.score(X, beta, logits=True)
+        tc.check()
+        lg0, lg1 = lg0.cpu().numpy(), lg1.cpu().numpy()
+        assert np.isfinite(lg0).all()
+        d = np.abs(lg0 - lg1)
+        print("tcgen05 vs library: max logit difference", d.max())
+        assert d.max() < 0.02, d.max()
+        assert np.abs(lq0.cpu().numpy() - lq1.cpu().numpy()).max() < 0.02 * np.sqrt(N)
+        assert d.max() > 0                    # the two paths are distinct code
+    lg_o, _ = F.score(W, shp, X.cpu().numpy(), beta.cpu().numpy().astype(np.float64))
+    assert np.all(np.abs(lg0 - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
+
+
+def test_tcgen05_first_ffn_map_at_scale():
+    # proj_mode 0 at 25600 rows (B = 128 configurations of N = 200): the first FFN map runs on
+    # the tcgen05 kernel (200 tiles on the persistent grid), everything else on cuBLASLt; the
+    # logits agree with the library path and with the float64 oracle on sampled rows
+    from paper_2509_23043_gb300.former import Former
+    N, B = 200, 128
+    shp = I.FormerShape(n_spins=N)
+    W, packed = I.former_weights(shp, index=3)
+    auto = Former(shp, packed, proj_mode=0)
+    lib = Former(shp, packed, proj_mode=1)
+    g = np.random.default_rng(5)
+    Xh = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
+    bh = g.uniform(0.1, 3.0, B).astype(np.float32)
+    X, beta = torch.from_numpy(Xh).cuda(), torch.from_numpy(bh).cuda()
+    _, lg0 = auto.score(X, beta, logits=True)
+    _, lg1 = lib.score(X, beta, logits=True)
+    auto.check()
+    lg0, lg1 = lg0.cpu().numpy(), lg1.cpu().numpy()
+    d = np.abs(lg0 - lg1)
+    print("tcgen05 first FFN map at 25600 rows: max logit difference", d.max())
+    assert 0 < d.max() < 0.02
+    rows = [0, 57, 127]
+    lg_o, _ = F.score(W, shp, Xh[rows], bh[rows].astype(np.float64))
+    assert np.all(np.abs(lg0[rows] - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
+
+
 def _philox_u(seed, t, b, stream):
     w = O.philox([t, b, 6 << 24, stream], [seed & 0xFFFFFFFF, seed >> 32])[0]
     return (int(w) >> 8) * 2.0 ** -24
