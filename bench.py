@@ -997,8 +997,11 @@ def isingformer_workload(stream, B=1024, reps=5):
                        "roofline": {"bound": "tensor", "achieved": gemm / (ms * 1e-3) / 1e12,
                                     "peak": peak_tf, "unit": "TFLOP/s",
                                     "frac": gemm / (ms * 1e-3) / 1e12 / peak_tf if peak_tf else None,
-                                    "traffic": None, "kernel": "the scoring pass (cuBLASLt projections "
-                                    "and this library's attention, norms and head)",
+                                    "traffic": None, "kernel": "the scoring pass (the first FFN map "
+                                    "on this library's tcgen05 kernel with bias and GELU fused; "
+                                    "the other projections and the attention's batched products "
+                                    "on cuBLASLt; softmax, norms, embedding and head in this "
+                                    "library's kernels)",
                                     "flops_per_call": gemm, "attention_flops_per_call": attn,
                                     "note": "matrix-product FLOPs over the whole pass's time; the "
                                             "attention's FP32 FLOPs are reported beside it"}},
@@ -1006,6 +1009,14 @@ def isingformer_workload(stream, B=1024, reps=5):
                         "gpu_launches_per_call": "one CUDA graph of N steps"},
              "e2e": {"value": B / (ms_e * 1e-3), "unit": "configs/s", "h2d_bytes_per_step": B * N,
                      "d2h_bytes_per_step": B * 4}}
+    # the same pass with every projection on cuBLASLt (proj_mode 1) and with every suitable
+    # projection on the tcgen05 kernels (proj_mode 2)
+    for mode in (1, 2):
+        alt = Former(shp, packed, stream=stream.cuda_stream, proj_mode=mode)
+        out_d["score"][f"ms_per_call_proj_mode_{mode}"] = _time_ms(lambda: alt.score(X, beta), reps, stream)
+        alt.check()
+        del alt
+    m.check()
     # the oracle on the host cores (numpy float64, BLAS threads): a few configurations
     from oracle import former as F
     t0 = time.perf_counter()
