@@ -661,12 +661,13 @@ def factorization(stream, sweeps_total, n=1000, R=32, P=512, burn=100_000, gap=2
     insts = [mult.instance(C) for C, _, _ in prods]
     ctxs = {}
     for name, upd in (("gibbs", pt.GIBBS), ("metropolis", pt.METROPOLIS)):
+        # colour classes of at most 32 free sites: one pass each of a 128-thread block
         cfg = pt.Config(update=upd, seed=0x7A972509, propose_every=10, propose_start=0,
-                        pool_size=P)
+                        pool_size=P, colour_cap=32)
         ctxs[name] = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[prop] * n,
                                          instance_ids=list(range(n)), stream=stream.cuda_stream)
     t0 = time.perf_counter()
-    gen = pt.create_instances(insts, [betas] * n, pt.Config(update=pt.GIBBS, seed=0x9001),
+    gen = pt.create_instances(insts, [betas] * n, pt.Config(update=pt.GIBBS, seed=0x9001, colour_cap=32),
                               instance_ids=[7_000_000 + k for k in range(n)],
                               stream=stream.cuda_stream)
     left = burn
@@ -1126,8 +1127,8 @@ def profile_case(kind):
     """Small cases for ncu captures (the commands are in profiles/). lattice, lattice-gibbs:
     the benchmark workload (256 EA L=10, R=32, proposals every 10 from sweep 100) with random
     pools of 1024 entries (1 GB, larger than L2), one launch at creation then four of 100
-    cycles. graph: 1000 clamped 8x8 multipliers, Gibbs, pools of 16, one launch at creation
-    then three of 1000 cycles. former: three IsingFormer scoring passes over 1024
+    cycles. graph: 1000 clamped 8x8 multipliers, Gibbs, colour classes of at most 32 free
+    sites, pools of 16, one launch at creation then three of 1000 cycles. former: three IsingFormer scoring passes over 1024
     configurations of N = 200."""
     import torch
     import instances as I
@@ -1155,7 +1156,8 @@ def profile_case(kind):
         mult = I.multiplier(8)
         insts = [mult.instance(C) for C, _, _ in I.draw_prime_products(nB)]
         betas = I.geometric_betas(0.05, 5.0, R)
-        cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P)
+        cfg = pt.Config(update=pt.GIBBS, seed=0x7A972509, propose_every=10, propose_start=0, pool_size=P,
+                        colour_cap=32)
         ctx = pt.create_instances(insts, [betas] * nB, cfg, prop_enabled=[[1] * 23 + [0] * (R - 23)] * nB,
                                   instance_ids=list(range(nB)))
         nw = (mult.n_spins + 31) // 32

@@ -115,6 +115,17 @@ typedef struct {
  *                    sweeps at its beta, and the result is accepted by proposal_rule. Pools
  *                    are not used. Violations: PT_EINVAL, or PT_ENOTSUP for the graph engine,
  *                    Gibbs sweeps or more than 32 enabled slots.
+ *  colour_cap        graph engine, general graphs (lattice_L = 0): 0 = the DSATUR colour
+ *                    classes (Methods, graph coloring) as they are; C > 0 = classes of at most
+ *                    C free sites where the graph allows it: with k = max(DSATUR's count,
+ *                    ceil(free sites / C)) colours available, repeatedly take the largest class
+ *                    above C (lowest colour among equals) and move its highest-index free site
+ *                    that has no free neighbour in some other class below C to the smallest such
+ *                    class (lowest colour among equals), until no class is above C or none of
+ *                    its sites can move; clamped sites keep their colours; empty colours are
+ *                    dropped, the others keeping their order. Any proper colouring gives a valid
+ *                    sweep; C = 32 fills the 32-site passes of a 128-thread block at R <= 32.
+ *                    More than 32 colours: PT_ENOTSUP. Negative: PT_EINVAL.
  */
 typedef struct {
     int32_t update;
@@ -129,6 +140,7 @@ typedef struct {
     int32_t proposal_source;
     int32_t context_log2;
     int32_t context_sweeps;
+    int32_t colour_cap;
 } pt_config;
 
 /* Create a batch of n >= 1 instances (all lattices with J = +-1 and no field or clamp, which

@@ -70,6 +70,8 @@ def lib():
         L.or_stats.argtypes = [C.c_void_p] + [C.c_void_p] * 4
         L.or_colouring.argtypes = [C.c_void_p, C.c_void_p]
         L.or_colouring.restype = C.c_int32
+        L.or_cap_colours.argtypes = [C.c_void_p, C.c_int32]
+        L.or_cap_colours.restype = C.c_int32
         L.or_bitplane.argtypes = [C.c_void_p]
         L.or_bitplane.restype = C.c_int32
         _lib = L
@@ -117,7 +119,7 @@ class Oracle:
                  update: int = 0, sweeps_per_cycle: int = 1, propose_every: int = 0,
                  propose_start: int = 0, propose_stop: int = 0, seed: int = 0,
                  pool_size: int = 0, proposal_rule: int = 0, proposal_source: int = 0,
-                 context_log2: int = 1, context_sweeps: int = 1):
+                 context_log2: int = 1, context_sweeps: int = 1, colour_cap: int = 0):
         self.inst = inst
         self.N = int(inst.n_spins)
         self.R = len(betas)
@@ -137,6 +139,8 @@ class Oracle:
                                  context_sweeps)
         if not self.h:
             raise ValueError("oracle rejected the instance")
+        if colour_cap > 0:
+            lib().or_cap_colours(self.h, colour_cap)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -594,6 +594,69 @@ void or_stats(const or_inst *o, int64_t *swap_acc, int64_t *swap_att,
     }
 }
 
+/* 1 if site i has a free neighbour of colour c */
+static int free_neighbour_coloured(const or_inst *o, int32_t i, int32_t c) {
+    for (int32_t a = o->adj_off[i]; a < o->adj_off[i + 1]; ++a) {
+        int32_t j = o->adj_j[a];
+        if (o->clamp[j] == 0 && o->colour[j] == c) return 1;
+    }
+    return 0;
+}
+
+/* Colour classes of at most `cap` free sites (the colour_cap option of the library; general
+ * graphs only, a lattice keeps its checkerboard). The DSATUR classes are a proper colouring
+ * of the free sites; so is the result, which only moves a site into a class holding none of
+ * its free neighbours. With k = max(ncol, ceil(free sites / cap)) colours to use: while some
+ * class holds more than cap free sites, take the fullest (the lowest colour among equally
+ * full ones) and scan its free sites from the highest index down; the first one that has no
+ * free neighbour in some other class holding fewer than cap free sites moves to the least full
+ * such class (the lowest colour among equally full ones). Stop when no class is over cap or
+ * no site of the fullest can move. Clamped sites keep their colours. Colours left without a
+ * site are removed and the others renumbered in order. Returns the number of colours. */
+int32_t or_cap_colours(or_inst *o, int32_t cap) {
+    if (cap <= 0 || o->L > 0) return o->ncol;
+    int32_t nfree = 0;
+    for (int32_t i = 0; i < o->N; ++i) nfree += (o->clamp[i] == 0);
+    int32_t k = (nfree + cap - 1) / cap;
+    if (k < o->ncol) k = o->ncol;
+    int32_t *fill = (int32_t *)xcalloc((size_t)k, 4);
+    for (int32_t i = 0; i < o->N; ++i)
+        if (o->clamp[i] == 0) fill[o->colour[i]]++;
+    for (;;) {
+        int32_t over = -1;
+        for (int32_t c = 0; c < k; ++c)
+            if (fill[c] > cap && (over < 0 || fill[c] > fill[over])) over = c;
+        if (over < 0) break;
+        int32_t moved = 0;
+        for (int32_t i = o->N - 1; i >= 0 && !moved; --i) {
+            if (o->clamp[i] != 0 || o->colour[i] != over) continue;
+            int32_t to = -1;
+            for (int32_t c = 0; c < k; ++c) {
+                if (c == over || fill[c] >= cap || free_neighbour_coloured(o, i, c)) continue;
+                if (to < 0 || fill[c] < fill[to]) to = c;
+            }
+            if (to >= 0) {
+                o->colour[i] = to;
+                fill[over]--;
+                fill[to]++;
+                moved = 1;
+            }
+        }
+        if (!moved) break;
+    }
+    int32_t *renum = (int32_t *)xcalloc((size_t)k, 4);
+    for (int32_t c = 0; c < k; ++c) renum[c] = -1;
+    for (int32_t i = 0; i < o->N; ++i) renum[o->colour[i]] = 1;
+    int32_t n = 0;
+    for (int32_t c = 0; c < k; ++c)
+        if (renum[c] > 0) renum[c] = n++;
+    for (int32_t i = 0; i < o->N; ++i) o->colour[i] = renum[o->colour[i]];
+    free(renum);
+    free(fill);
+    o->ncol = n;
+    return n;
+}
+
 int32_t or_colouring(const or_inst *o, int32_t *colour) {
     if (colour) memcpy(colour, o->colour, (size_t)o->N * 4);
     return o->ncol;

@@ -97,6 +97,9 @@ void or_stats(const or_inst *o, int64_t *swap_acc, int64_t *swap_att,
               int64_t *prop_acc, int64_t *prop_att);
 /* colour of every site (clamped sites included) and the number of colours. */
 int32_t or_colouring(const or_inst *o, int32_t *colour);
+/* Rebalance the colour classes to at most cap free sites each (general graphs; see the .c
+ * file); call before the first sweep. Returns the number of colours. */
+int32_t or_cap_colours(or_inst *o, int32_t cap);
 /* 1 when the instance uses the bit-plane random layout (lattice, +-1, no field, no clamps;
  * Metropolis or Gibbs), else 0. */
 int32_t or_bitplane(const or_inst *o);

@@ -44,7 +44,7 @@ class _Config(C.Structure):
                 ("propose_stop", C.c_int32), ("pool_size", C.c_int32), ("seed", C.c_uint64),
                 ("threads_per_block", C.c_int32), ("proposal_rule", C.c_int32),
                 ("proposal_source", C.c_int32), ("context_log2", C.c_int32),
-                ("context_sweeps", C.c_int32)]
+                ("context_sweeps", C.c_int32), ("colour_cap", C.c_int32)]
 
 
 EXPORTS = ["pt_create_instances", "pt_load_proposals", "pt_load_proposals_packed",
@@ -148,13 +148,14 @@ class Config:
     proposal_source: int = POOL
     context_log2: int = 1
     context_sweeps: int = 1
+    colour_cap: int = 0
 
     def _c(self) -> _Config:
         return _Config(self.update, self.sweeps_per_cycle, self.propose_every,
                        self.propose_start, self.propose_stop, self.pool_size,
                        self.seed & 0xFFFFFFFFFFFFFFFF, self.threads_per_block,
                        self.proposal_rule, self.proposal_source, self.context_log2,
-                       self.context_sweeps)
+                       self.context_sweeps, self.colour_cap)
 
 
 class Context:

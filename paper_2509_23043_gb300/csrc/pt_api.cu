@@ -116,6 +116,55 @@ int dsatur(int N, const std::vector<std::vector<int>>& nbr, std::vector<int>& co
     return ncol;
 }
 
+// Colour classes of at most `cap` free sites, where the graph allows it. With
+// k = max(ncol, ceil(nfree / cap)) colours available, repeatedly take the largest class above
+// cap (the lowest colour among equals) and move its highest-index free site that has no free
+// neighbour in some other class below cap, to the smallest such class (the lowest colour
+// among equals); stop when no class is above cap or no site of it can move. Clamped sites are
+// never updated and keep their colours. Empty colours are then dropped, the others keeping
+// their order. Returns the number of colours.
+int balance_colours(int N, const std::vector<std::vector<int>>& nbr, const std::vector<int8_t>& clamp,
+                    std::vector<int>& col, int ncol, int cap) {
+    int nfree = 0;
+    for (int i = 0; i < N; ++i) nfree += clamp[i] == 0;
+    const int k = std::max(ncol, (nfree + cap - 1) / cap);
+    std::vector<int> size(k, 0);
+    for (int i = 0; i < N; ++i)
+        if (clamp[i] == 0) ++size[col[i]];
+    for (;;) {
+        int c = -1;
+        for (int x = 0; x < k; ++x)
+            if (size[x] > cap && (c < 0 || size[x] > size[c])) c = x;
+        if (c < 0) break;
+        bool moved = false;
+        for (int i = N - 1; i >= 0 && !moved; --i) {
+            if (clamp[i] != 0 || col[i] != c) continue;
+            int d = -1;
+            for (int y = 0; y < k; ++y) {
+                if (y == c || size[y] >= cap) continue;
+                bool free_of = true;
+                for (int j : nbr[i])
+                    if (clamp[j] == 0 && col[j] == y) { free_of = false; break; }
+                if (free_of && (d < 0 || size[y] < size[d])) d = y;
+            }
+            if (d >= 0) {
+                col[i] = d;
+                --size[c];
+                ++size[d];
+                moved = true;
+            }
+        }
+        if (!moved) break;
+    }
+    std::vector<int> used(k, 0), remap(k, -1);
+    for (int i = 0; i < N; ++i) used[col[i]] = 1;
+    int n = 0;
+    for (int x = 0; x < k; ++x)
+        if (used[x]) remap[x] = n++;
+    for (int i = 0; i < N; ++i) col[i] = remap[col[i]];
+    return n;
+}
+
 int lattice_colour(int n, int L) {
     const int x = n % L, y = (n / L) % L, z = n / (L * L);
     if (L % 2 == 0) return (x + y + z) % 2;
@@ -626,6 +675,7 @@ pt_status build_graph(pt_ctx* c, const pt_instance_desc* descs) {
                 }
             }
             ncol = dsatur(N, nbr, col);
+            if (c->cfg.colour_cap > 0) ncol = balance_colours(N, nbr, clamp, col, ncol, c->cfg.colour_cap);
         }
         if (ncol > 32) return fail(PT_ENOTSUP, "instance %d: colouring needs %d > 32 colours", k, ncol);
         I.ncol = ncol;
@@ -919,6 +969,7 @@ pt_status pt_create_instances(pt_ctx** out, const pt_instance_desc* descs, int32
         return fail(PT_EINVAL, "proposal_rule 2 needs pool proposals (proposal_source 0)");
     if (cfg->proposal_source != 0 && cfg->proposal_source != 1)
         return fail(PT_EINVAL, "proposal_source must be 0 or 1");
+    if (cfg->colour_cap < 0) return fail(PT_EINVAL, "colour_cap must be >= 0");
     if (cfg->proposal_source == 1) {
         if (cfg->context_log2 < 1 || cfg->context_log2 > 3)
             return fail(PT_EINVAL, "context_log2 must be 1, 2 or 3");

@@ -15,7 +15,37 @@ def _oracle(inst, betas, cfg, iid, prop=None):
     return O.Oracle(inst, betas, instance_id=iid, prop_enabled=prop, update=cfg.update,
                     sweeps_per_cycle=cfg.sweeps_per_cycle, propose_every=cfg.propose_every,
                     propose_start=cfg.propose_start, propose_stop=cfg.propose_stop,
-                    seed=cfg.seed, pool_size=cfg.pool_size)
+                    seed=cfg.seed, pool_size=cfg.pool_size, colour_cap=cfg.colour_cap)
+
+
+@pytest.mark.parametrize("bits,cap,update", [(4, 4, 1), (4, 8, 0), (8, 32, 1)])
+def test_capped_colour_classes_match_oracle(bits, cap, update):
+    # colour_cap: DSATUR classes rebalanced to at most `cap` free sites (ten classes of 4 and
+    # five of 8 on the 4x4 multiplier's 40 free sites; five of 32 and one of 16 on the 8x8
+    # multiplier's 176, the bench's setting); the chain follows the oracle's with the same
+    # classes bit for bit
+    mult = I.multiplier(bits)
+    C = 11 * 13 if bits == 4 else 251 * 241
+    inst = mult.instance(C)
+    R, P = 16, 8
+    betas = I.geometric_betas(0.05, 5.0, R)
+    prop = [1] * 11 + [0] * 5
+    cfg = pt.Config(update=update, seed=4242 + cap, propose_every=3, pool_size=P, colour_cap=cap)
+    ctx = pt.create_instances([inst], [betas], cfg, prop_enabled=[prop], instance_ids=[C])
+    o = _oracle(inst, betas, cfg, C, prop)
+    col, n = o.colouring()
+    free = inst.clamp == 0
+    sizes = [int(((col == c) & free).sum()) for c in range(n)]
+    assert max(sizes) <= cap
+    pools = [I.random_configs(inst.n_spins, P, seed=9, index=r) for r in range(R)]
+    for r in range(R):
+        pt.load_proposals(ctx, 0, r, pools[r])
+        o.load_pool(r, pools[r])
+    for chunk in (1, 7, 40):
+        pt.run_cycles(ctx, chunk)
+        o.run_cycles(chunk)
+        _assert_same(ctx, 0, o, f"colour_cap {cap}")
+    _stats_same(ctx, 0, o)
 
 
 def _assert_same(ctx, k, o, what=""):

@@ -521,3 +521,57 @@ def test_initial_state_respects_clamps():
     assert abs(free.mean()) < 5 / np.sqrt(free.size)
     for r in range(s.shape[0]):
         assert E[r] == O.energy(inst, s[r])
+
+
+def _free_adjacent_same_colour(inst, col):
+    free = inst.clamp == 0 if inst.clamp is not None else np.ones(inst.n_spins, bool)
+    ei, ej = np.asarray(inst.edge_i), np.asarray(inst.edge_j)
+    both = free[ei] & free[ej]
+    return bool(np.any(col[ei][both] == col[ej][both]))
+
+
+@pytest.mark.parametrize("cap", [1, 3, 8, 32])
+def test_capped_colouring_is_proper_and_within_cap(cap):
+    # colour_cap: every class is an independent set of free sites (a valid parallel update),
+    # holds at most cap free sites where the graph allows it, and no colour is left empty.
+    # With cap 1 every free site is a class of its own; at caps that DSATUR's classes already
+    # meet the colouring is DSATUR's.
+    mult = I.multiplier(4)
+    inst = mult.instance(11 * 13)
+    free = inst.clamp == 0
+    base, n0 = O.Oracle(inst, I.geometric_betas(0.1, 2.0, 4), update=1).colouring()
+    col, n = O.Oracle(inst, I.geometric_betas(0.1, 2.0, 4), update=1, colour_cap=cap).colouring()
+    assert not _free_adjacent_same_colour(inst, col)
+    sizes = [int(((col == c) & free).sum()) for c in range(n)]
+    assert max(sizes) <= cap
+    assert sorted(set(col.tolist())) == list(range(n))
+    if cap == 1:
+        assert all(s <= 1 for s in sizes) and sum(sizes) == int(free.sum())
+    if cap >= max(int(((base == c) & free).sum()) for c in range(n0)):
+        assert np.array_equal(col, base) and n == n0
+
+
+def test_capped_colouring_keeps_boltzmann_on_a_small_graph():
+    # the capped sweep is still a product of Gibbs updates over independent sets: a long Gibbs
+    # run of the oracle at one temperature on a 5-spin frustrated graph with cap 1 (five
+    # single-site classes) reproduces the exact Boltzmann law of its 32 states
+    ei = np.array([0, 0, 1, 1, 2, 3, 0], np.int32)
+    ej = np.array([1, 2, 2, 3, 3, 4, 4], np.int32)
+    eJ = np.array([1, -2, 1, 1, -1, 2, 1], np.int32)
+    h = np.array([1, 0, -1, 0, 1], np.int32)
+    inst = I.Instance(n_spins=5, edge_i=ei, edge_j=ej, edge_J=eJ, h=h, clamp=np.zeros(5, np.int8))
+    beta = 0.4
+    o = O.Oracle(inst, [beta], update=1, seed=11, colour_cap=1)
+    col, n = o.colouring()
+    assert n == 5 and sorted(col.tolist()) == [0, 1, 2, 3, 4]
+    states = np.array([[1 if (k >> (4 - i)) & 1 else -1 for i in range(5)] for k in range(32)], np.int8)
+    E = np.array([O.energy(inst, s) for s in states], float)
+    p = np.exp(-beta * (E - E.min()))
+    p /= p.sum()
+    counts = np.zeros(32)
+    for _ in range(20000):
+        o.sweeps(1)
+        s = o.read()[0][0]
+        counts[int(((s > 0).astype(int) << np.arange(4, -1, -1)).sum())] += 1
+    q = counts / counts.sum()
+    assert 0.5 * np.abs(q - p).sum() < 0.02
