@@ -108,7 +108,7 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
     const int s0 = tid / O, sstep = Ts / O;         // the thread's first site, site stride
     uint2* sp = reinterpret_cast<uint2*>(S.spins);
     // the thread's eight walkers: threshold rows of their slots (fixed during a sweep); the
-    // walkers beyond R draw nothing and keep their bytes
+    // walkers beyond R keep their bytes
     int trow[8];
     uint32_t valid = 0;
 #pragma unroll
@@ -208,7 +208,9 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
             const uint32_t drawn = valid & ~forced;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                if (!(drawn >> j & 1u)) continue;
+                // Gibbs draws for every walker (a padding walker reads slot 0's row, always in
+                // the table, and its byte is masked below); Metropolis skips the forced moves
+                if (!GIBBS && !(drawn >> j & 1u)) continue;
                 const uint32_t t = S.thr[index(j)];
                 const uint32_t x = (j & 1) ? (hw[j >> 1] << 16) : (hw[j >> 1] & 0xFFFF0000u);
                 below |= (uint32_t)(x < t) << j;
