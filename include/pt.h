@@ -48,8 +48,10 @@ typedef struct pt_ctx pt_ctx;   /* opaque; owns all device memory of a batch */
  * temperature ladder {beta_r} and proposal-enabled set R_prop.
  *  instance_id   caller's identifier; it keys every random stream of the instance, so an
  *                instance evolves identically whatever batch or position it runs in.
- *  n_spins       N >= 1 (lattice engine: N <= 8192; graph engine: N <= 65535; both: the
- *                instance's state and tables must fit in one SM's shared memory, else
+ *  n_spins       N >= 1 (lattice engine: N <= 8192; an instance whose spins and neighbour
+ *                table do not fit one block's shared memory keeps both in global memory,
+ *                except with contextual proposals (PT_ENOTSUP); graph engine: N <= 65535, and
+ *                the instance's state and tables must fit in one block's shared memory, else
  *                PT_ENOTSUP).
  *  lattice_L     > 0: a periodic L^3 lattice (N = L^3, L >= 2); the edges must then be the
  *                3N bonds in canonical order: for site n = x + L(y + L z), its +x, +y, +z

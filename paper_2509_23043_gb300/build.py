@@ -22,7 +22,7 @@ LIB = OUT_DIR / "libpt.so"
 FORMER_LIB = OUT_DIR / "libptformer.so"
 FORMER_SOURCES = ["pt_former.cu", "pt_gemm_tc.cu"]
 CUDA_LIB_DIR = "/usr/local/cuda/lib64"
-SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_lattice_gibbs.cu", "pt_graph.cu", "pt_calib.cu"]
+SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_lattice_gibbs.cu", "pt_lattice_big.cu", "pt_graph.cu", "pt_calib.cu"]
 HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh", "pt_lattice.cuh", "pt_gemm_tc.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ffp-contract=off on the host: FP64 threshold tables are evaluated exactly as written.

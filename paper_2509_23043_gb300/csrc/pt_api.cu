@@ -183,13 +183,14 @@ struct Group {
     int maxW = 1;
     int maxitems = 0;          // largest (colour class x walker blocks) of a member
     bool packed_only = false;  // graph engine: every member has packed rows
+    bool gsp = false;          // lattice engine: the members' spins and tables in global memory
     void* d_insts = nullptr;   // LatInst[] or GraphInst[] of the members
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
 };
 
 // Arena offsets of one lattice instance's arrays (for slot replacement).
-struct LatOff { size_t spins, itab, pos, E, sow, wos, thr, beta, prop, cur, eb, ctr, st, active, lw; };
+struct LatOff { size_t spins, itab, pos, E, sow, wos, thr, beta, prop, cur, eb, ctr, st, active, lw, gsp; };
 
 struct pt_ctx {
     int engine = 0;           // 0 lattice, 1 graph
@@ -279,7 +280,7 @@ cudaError_t launch_group(const pt_ctx* c, const Group& g, const void* d_insts, i
         const int counting = (c->L[g.members[0]] % 2 == 0) ? 1 : 2;
         const int kb4 = 6 * per_thread * counting < 16 ? 1 : 0;
         const int flags = (c->with_pool ? kWithPool : 0) | (c->with_ctx ? kWithContext : 0) |
-                          (c->cfg.update == 1 ? kGibbs : 0);
+                          (c->cfg.update == 1 ? kGibbs : 0) | (g.gsp ? kGlobalSpins : 0);
         return launch_lattice(static_cast<const LatInst*>(d_insts), count, g.maxW, kb4, g.T, g.smem, a,
                               flags, s);
     }
@@ -500,7 +501,7 @@ pt_status lattice_group_shape(pt_ctx* c, Group& g, int T) {
     size_t smem = 0;
     for (int k : g.members) {
         const LatLayout l = lattice_layout(c->W[k], c->N[k], c->NW[k], c->R[k], T / 32, c->with_pool != 0,
-                                           c->with_ctx != 0, c->cfg.update == 1);
+                                           c->with_ctx != 0, c->cfg.update == 1, g.gsp);
         smem = std::max(smem, l.total);
     }
     if (smem > (size_t)c->optin)
@@ -545,6 +546,14 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         o.st = A.zeros((size_t)4 * h.R * 8);
         o.active = A.add(&one, 4);
         o.lw = c->cfg.proposal_rule == 2 ? A.zeros((size_t)h.R * h.N * 8) : 0;
+        // spins and table too large for shared memory: a global working copy of the
+        // {word, complement} spins (the kernel reads the table in place)
+        const bool gsp = lattice_layout(h.W, h.N, h.NW, h.R, 1, c->with_pool != 0, c->with_ctx != 0,
+                                        c->cfg.update == 1).total > (size_t)c->optin;
+        if (gsp && c->with_ctx)
+            return fail(PT_ENOTSUP, "instance %d: contextual proposals need the instance's spins in "
+                                    "shared memory (at most %d bytes)", k, c->optin);
+        o.gsp = gsp ? A.zeros((size_t)h.W * h.N * 8) : 0;
         c->slab_off[k] = c->slab;
         c->slab += (size_t)h.R * h.NW;
         c->NWmax = std::max(c->NWmax, h.NW);
@@ -555,9 +564,16 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         int gk = -1;
         for (size_t g = 0; g < c->groups.size(); ++g) {
             const int m = c->groups[g].members[0];
-            if (c->W[m] == c->W[k] && c->L[m] == c->L[k]) { gk = (int)g; break; }
+            if (c->W[m] == c->W[k] && c->L[m] == c->L[k] && (c->loff[m].gsp != 0) == (c->loff[k].gsp != 0)) {
+                gk = (int)g;
+                break;
+            }
         }
-        if (gk < 0) { c->groups.emplace_back(); gk = (int)c->groups.size() - 1; }
+        if (gk < 0) {
+            c->groups.emplace_back();
+            gk = (int)c->groups.size() - 1;
+            c->groups[gk].gsp = c->loff[k].gsp != 0;
+        }
         c->groups[gk].members.push_back(k);
         c->group_of[k] = gk;
     }
@@ -586,6 +602,7 @@ pt_status build_lattice(pt_ctx* c, const pt_instance_desc* descs) {
         LatInst& I = c->lat[k];
         const LatOff& o = c->loff[k];
         I.spins = (uint32_t*)(b + o.spins);
+        I.gspins = o.gsp ? (uint2*)(b + o.gsp) : nullptr;
         I.itab = (const uint4*)(b + o.itab);
         I.pos = (const uint16_t*)(b + o.pos);
         I.E = (int32_t*)(b + o.E);

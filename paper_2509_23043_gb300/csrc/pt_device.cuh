@@ -123,6 +123,9 @@ struct LatInst {
                            //         colour-major) of the neighbour's word, or of its
                            //         complement (+4) when the bond is -1
     const uint16_t* pos;   // [N] colour-major position of each site
+    uint2* gspins;         // [W][N] {word, complement}, colour-major, in global memory: the
+                           // working copy of an instance whose spins and table do not fit
+                           // shared memory (the GSP kernels read itab in place); else nullptr
     const int32_t* active; // nonzero: the instance takes part in launches
     int32_t* E;            // [W*32] per walker
     int16_t* sow;          // [W*32] slot of walker (-1: padding lane)
@@ -149,7 +152,7 @@ __device__ __forceinline__ double mh_exponent(double beta, int dE, long long d) 
 }
 
 // Lattice kernel flags: pool proposals, contextual proposals
-constexpr int kWithPool = 1, kWithContext = 2, kGibbs = 4;
+constexpr int kWithPool = 1, kWithContext = 2, kGibbs = 4, kGlobalSpins = 8;
 
 // Kernel modes
 enum : int32_t {

@@ -75,6 +75,11 @@ cudaError_t configure_lattice_gibbs_kernels(int smem);
 cudaError_t launch_lattice_gibbs(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
                                  size_t smem, const RunArgs& a, int flags, cudaStream_t stream);
 
+// Defined in pt_lattice_big.cu: the instantiations with the spins in global memory.
+cudaError_t configure_lattice_gsp_kernels(int smem);
+cudaError_t launch_lattice_gsp(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
+                               size_t smem, const RunArgs& a, int flags, cudaStream_t stream);
+
 // The kernels' dynamic shared-memory limit is raised once, outside any stream capture.
 cudaError_t configure_lattice_kernels(int smem) {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -89,6 +94,7 @@ cudaError_t configure_lattice_kernels(int smem) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<2, 8, true, false>, A, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lattice_kernel<4, 8, true, false>, A, smem);
     if (e == cudaSuccess) e = configure_lattice_gibbs_kernels(smem);
+    if (e == cudaSuccess) e = configure_lattice_gsp_kernels(smem);
     return e;
 }
 
@@ -111,6 +117,8 @@ cudaError_t launch_lattice_t(const LatInst* d_insts, int n, int maxW, int kb4, i
 
 cudaError_t launch_lattice(const LatInst* d_insts, int n, int maxW, int kb4, int threads,
                            size_t smem, const RunArgs& a, int flags, cudaStream_t stream) {
+    if (flags & kGlobalSpins)
+        return launch_lattice_gsp(d_insts, n, maxW, kb4, threads, smem, a, flags, stream);
     if (flags & kGibbs)
         return launch_lattice_gibbs(d_insts, n, maxW, kb4, threads, smem, a, flags, stream);
     if (flags & kWithContext)

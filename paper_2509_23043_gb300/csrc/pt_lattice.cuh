@@ -81,13 +81,20 @@ struct LatSmem {
     int32_t* cmisc;    // [2]  number of enabled slots, mask of accepted lanes
 };
 
+// GSP: the spins are the instance's global working copy and the table is read in place
+template <bool GSP>
 __device__ __forceinline__ LatSmem carve_lattice(uint8_t* base, const LatInst& I, int nwarps,
                                                  bool with_pool, bool with_ctx, bool gibbs) {
-    const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool, with_ctx, gibbs);
+    const LatLayout l = lattice_layout(I.W, I.N, I.NW, I.R, nwarps, with_pool, with_ctx, gibbs, GSP);
     LatSmem S;
     S.tw = reinterpret_cast<uint4*>(base + l.tw);
-    S.spins = reinterpret_cast<uint2*>(base + l.spins);
-    S.itab = reinterpret_cast<uint4*>(base + l.itab);
+    if constexpr (GSP) {
+        S.spins = I.gspins;
+        S.itab = const_cast<uint4*>(I.itab);
+    } else {
+        S.spins = reinterpret_cast<uint2*>(base + l.spins);
+        S.itab = reinterpret_cast<uint4*>(base + l.itab);
+    }
     S.beta = reinterpret_cast<double*>(base + l.beta);
     S.dbeta = reinterpret_cast<double*>(base + l.dbeta);
     S.fbeta = reinterpret_cast<float*>(base + l.fbeta);
@@ -694,17 +701,20 @@ __device__ void lattice_context_propose(const LP& P, LatSmem& S, const RunArgs& 
 
 // CTX: built with the contextual-proposal step (a separate instantiation, so the kernels
 // without it keep their code and registers).
-template <int MAXW, int KB, bool CTX, bool GIBBS>
+// GSP: spins and neighbour table in global memory (instances too large for shared memory;
+// L2 keeps them resident), a separate instantiation so the others keep shared addressing.
+template <int MAXW, int KB, bool CTX, bool GIBBS, bool GSP = false>
 __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict__ insts,
                                                       RunArgs a, int flags) {
     static_assert(!(CTX && GIBBS), "contextual proposals refill with Metropolis sweeps");
+    static_assert(!(CTX && GSP), "contextual proposals are built for shared-memory instances");
     extern __shared__ __align__(16) uint8_t smem[];
     const LatInst& I = insts[blockIdx.x];
     if (!*I.active) return;   // a free serving slot: the whole block leaves at once
     const int nwarps = blockDim.x >> 5;
     const bool with_pool = (flags & kWithPool) != 0;
     constexpr bool with_ctx = CTX;
-    LatSmem S = carve_lattice(smem, I, nwarps, with_pool, with_ctx, GIBBS);
+    LatSmem S = carve_lattice<GSP>(smem, I, nwarps, with_pool, with_ctx, GIBBS);
     const int tid = threadIdx.x, T = blockDim.x;
     const LP P = load_lp(I);
     const int N = P.N, W = P.W, R = P.R, WR = W * 32;
@@ -715,7 +725,8 @@ __global__ void __launch_bounds__(512) lattice_kernel(const LatInst* __restrict_
         const uint32_t v = I.spins[i];
         S.spins[wb * N + I.pos[site]] = make_uint2(v, ~v);
     }
-    for (int i = tid; i < N; i += T) S.itab[i] = I.itab[i];
+    if constexpr (!GSP)
+        for (int i = tid; i < N; i += T) S.itab[i] = I.itab[i];
     for (int i = tid; i < WR; i += T) {
         S.E[i] = I.E[i];
         S.Eacc[i] = 0;

@@ -21,17 +21,18 @@ struct LatLayout {
 
 // with_ctx (contextual proposals): one more walker block of spins and threshold planes (the
 // scratch lanes), the kept-site masks and the per-lane bookkeeping. gibbs: seven thresholds
-// per slot instead of three, so two uint4 per slot and per threshold plane.
+// per slot instead of three, so two uint4 per slot and per threshold plane. gsp: the spins and
+// the neighbour table stay in global memory (instances too large for shared memory).
 PT_HD inline LatLayout lattice_layout(int W, int N, int NW, int R, int nwarps, bool with_pool,
-                                      bool with_ctx, bool gibbs) {
+                                      bool with_ctx, bool gibbs, bool gsp = false) {
     LatLayout l;
     const size_t WR = (size_t)W * 32;
     const size_t WB = (size_t)W + (with_ctx ? 1 : 0);   // walker blocks held, scratch included
     const size_t TS = gibbs ? 2 : 1;                      // uint4 per plane and per slot
     size_t o = 0;
     l.tw = o;     o = align16(o + WB * 32 * 16 * TS);
-    l.spins = o;  o = align16(o + WB * N * 8);          // word and complement
-    l.itab = o;   o = align16(o + (size_t)N * 16);
+    l.spins = o;  o = align16(o + (gsp ? 0 : WB * N * 8));     // word and complement
+    l.itab = o;   o = align16(o + (gsp ? 0 : (size_t)N * 16));
     l.beta = o;   o = align16(o + (size_t)R * 8);
     l.dbeta = o;  o = align16(o + (size_t)R * 8);
     l.fbeta = o;  o = align16(o + (size_t)R * 4);

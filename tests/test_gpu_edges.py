@@ -32,10 +32,17 @@ def test_largest_lattice_L20_R32(update):
 
 
 def test_lattice_beyond_limits_rejected():
-    with pytest.raises(pt.PTError):
+    with pytest.raises(pt.PTError):                    # N > 8192
         pt.create_instances([I.ea_instance(21)], [I.geometric_betas(0.2, 2.0, 4)], pt.Config())
-    with pytest.raises(pt.PTError):                    # does not fit in shared memory
-        pt.create_instances([I.ea_instance(20)], [I.geometric_betas(0.2, 2.0, 64)], pt.Config())
+    # too large for shared memory: accepted, spins and table in global memory ...
+    ctx = pt.create_instances([I.ea_instance(20)], [I.geometric_betas(0.2, 2.0, 64)], pt.Config())
+    assert pt.group_info(ctx)[0]["smem"] < 2 * 8000 * 8
+    pt.destroy(ctx)
+    # ... except with contextual proposals, which need the spins in shared memory
+    with pytest.raises(pt.PTError):
+        pt.create_instances([I.ea_instance(20)], [I.geometric_betas(0.2, 2.0, 64)],
+                            pt.Config(proposal_source=1, propose_every=2, context_sweeps=1),
+                            prop_enabled=[[1] * 8 + [0] * 56])
 
 
 def _graph(n, edges, h=None, clamp=None):

@@ -73,6 +73,35 @@ def _ea_pool(inst, R, P, seed):
 
 
 @pytest.mark.parametrize("update", [0, 1])
+@pytest.mark.parametrize("L,R", [(20, 40), (19, 72)])
+def test_lattice_larger_than_shared_memory_matches_oracle(L, R, update):
+    # L = 20 with two walker blocks (and L = 19, odd: three colours, with three blocks):
+    # the {word, complement} spins and the neighbour table need more than the 227 KB of shared
+    # memory a block can hold, so the instance runs on the kernels that keep them in global
+    # memory; with a pool and proposals every 2 cycles the chain follows the oracle's bit for
+    # bit, and the group's shared memory holds neither
+    inst = I.ea_instance(L, index=L + R)
+    P = 4
+    betas = I.geometric_betas(0.2, 3.0, R)
+    cfg = pt.Config(seed=0xB16 + L, sweeps_per_cycle=1, update=update, propose_every=2, pool_size=P)
+    ctx = pt.create_instances([inst], [betas], cfg, instance_ids=[23])
+    assert pt.info(ctx)["engine"] == "lattice"
+    W, N = (R + 31) // 32, L ** 3
+    assert pt.group_info(ctx)[0]["smem"] < W * N * 8          # the spins are not in shared memory
+    o = _oracle(inst, betas, cfg, 23)
+    pools = _ea_pool(inst, R, P, seed=L)
+    for r in range(R):
+        pt.load_proposals(ctx, 0, r, pools[r])
+        o.load_pool(r, pools[r])
+    _assert_same(ctx, 0, o, "initial")
+    for chunk in (1, 2):
+        pt.run_cycles(ctx, chunk)
+        o.run_cycles(chunk)
+        _assert_same(ctx, 0, o, f"global-memory lattice L={L} R={R} update={update}")
+    _stats_same(ctx, 0, o)
+
+
+@pytest.mark.parametrize("update", [0, 1])
 @pytest.mark.parametrize("L,R", [(6, 16), (4, 32), (2, 5), (3, 8), (5, 33), (4, 70)])
 def test_lattice_cycles_match_oracle(L, R, update):
     inst = I.ea_instance(L, index=L * 7 + R)
