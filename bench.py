@@ -998,11 +998,11 @@ def isingformer_workload(stream, B=1024, reps=5):
                        "roofline": {"bound": "tensor", "achieved": gemm / (ms * 1e-3) / 1e12,
                                     "peak": peak_tf, "unit": "TFLOP/s",
                                     "frac": gemm / (ms * 1e-3) / 1e12 / peak_tf if peak_tf else None,
-                                    "traffic": None, "kernel": "the scoring pass (the first FFN map "
-                                    "on this library's tcgen05 kernel with bias and GELU fused; "
-                                    "the other projections and the attention's batched products "
-                                    "on cuBLASLt; softmax, norms, embedding and head in this "
-                                    "library's kernels)",
+                                    "traffic": None, "kernel": "the scoring pass (this library's "
+                                    "tcgen05 kernels for the first FFN map with bias and GELU "
+                                    "fused and for the attention scores with the causal softmax "
+                                    "fused; the other projections and O = P V on cuBLASLt; norms, "
+                                    "embedding and head in this library's kernels)",
                                     "flops_per_call": gemm, "attention_flops_per_call": attn,
                                     "note": "matrix-product FLOPs over the whole pass's time; the "
                                             "attention's FP32 FLOPs are reported beside it"}},

@@ -462,6 +462,7 @@ struct pt_former {
     std::tuple<int, int, const void*, const void*, const void*, const void*> gkey{};
     std::map<std::vector<long long>, cublasLtMatmulAlgo_t> algos;   // by product shape, layout, alignment
     bool proj_tc = false;          // the tcgen05 kernels are set up (proj_mode 0 or 2)
+    bool tc_ready = false;         // gemm_tc_setup succeeded
     int num_sms = 0;
     int* d_err = nullptr;          // nonzero once a wait of a tcgen05 kernel ran out
 };
@@ -663,6 +664,8 @@ pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const __nv_bfloat16* 
     return PT_OK;
 }
 
+pt_status attention_scores_softmax(pt_former* m, Act& x, int B);
+
 // Causal attention of the scoring pass on the tensor cores, per head, batched over the B
 // configurations, reading the heads' columns of the bfloat16 [B N][3d] query/key/value in
 // place: S = Q K^T / 8 (row-major S [N][N] is the column-major S^T = K Q^T), the causal
@@ -671,6 +674,26 @@ pt_status attention_tc(pt_former* m, Act& x, int B) {
     const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
     const int ld = 3 * d;
     const long long cfg_stride = (long long)N * ld;     // one configuration's rows
+    const long long nn = (long long)N * N;
+    pt_status s = PT_OK;
+    if (m->cfg.attn_mode == 0 && m->tc_ready && attn_softmax_tc_supported(N, d)) {
+        // the scores and the causal softmax in one tcgen05 kernel, P written directly
+        FCK(attn_softmax_tc(x.qkv16, x.P, B, N, H, d, m->num_sms, m->d_err, m->exec));
+    } else {
+        s = attention_scores_softmax(m, x, B);
+        if (s != PT_OK) return s;
+    }
+    for (int hd = 0; hd < H && s == PT_OK; ++hd)
+        s = gemm_batched(m, CUBLAS_OP_N, x.qkv16 + 2 * d + hd * kDH, ld, cfg_stride, x.P + hd * nn, N, H * nn,
+                         x.o + hd * kDH, CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B, 1.f);
+    return s;
+}
+
+// S = Q K^T / 8 per head as cuBLASLt batched products (FP32), then the causal-softmax kernel
+pt_status attention_scores_softmax(pt_former* m, Act& x, int B) {
+    const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
+    const int ld = 3 * d;
+    const long long cfg_stride = (long long)N * ld;
     const long long nn = (long long)N * N;
     pt_status s = PT_OK;
     for (int hd = 0; hd < H && s == PT_OK; ++hd)
@@ -690,9 +713,6 @@ pt_status attention_tc(pt_former* m, Act& x, int B) {
     else
         causal_softmax_loop_kernel<<<grid, 256, 0, m->exec>>>(x.S, x.P, rows, N);
     FCK(cudaGetLastError());
-    for (int hd = 0; hd < H && s == PT_OK; ++hd)
-        s = gemm_batched(m, CUBLAS_OP_N, x.qkv16 + 2 * d + hd * kDH, ld, cfg_stride, x.P + hd * nn, N, H * nn,
-                         x.o + hd * kDH, CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B, 1.f);
     return s;
 }
 
@@ -824,7 +844,7 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
     const int d = cfg->d_model, F = cfg->d_ff;
     if (cfg->n_spins < 1 || cfg->n_layers < 0 || cfg->n_heads < 1 || d != 64 * cfg->n_heads ||
         (d != 64 && d != 128 && d != 256 && d != 512) || F < 8 || F % 8 != 0 ||
-        cfg->attn_mode < 0 || cfg->attn_mode > 1 || cfg->proj_mode < 0 || cfg->proj_mode > 2)
+        cfg->attn_mode < 0 || cfg->attn_mode > 2 || cfg->proj_mode < 0 || cfg->proj_mode > 2)
         return ffail(PT_EINVAL, "unsupported shape (d_model must be 64 x n_heads, one of 64..512; d_ff a multiple of 8)");
     if (n_params != pt_former_param_count(cfg))
         return ffail(PT_EINVAL, "%zu parameters given, the shape has %zu", n_params, pt_former_param_count(cfg));
@@ -892,13 +912,15 @@ pt_status pt_former_create(pt_former** out, const pt_former_config* cfg, const u
     if (s == PT_OK) s = dalloc(m, &m->d_err, 1);
     if (s == PT_OK && cudaMemset(m->d_err, 0, sizeof(int)) != cudaSuccess) s = ffail(PT_ECUDA, "error flag");
     m->proj_tc = cfg->proj_mode != 1;
-    if (s == PT_OK && m->proj_tc) {
+    if (s == PT_OK && (m->proj_tc || cfg->attn_mode == 0)) {
         int dev = 0;
         const cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
         const cudaError_t e2 = e == cudaSuccess ? gemm_tc_setup() : e;
         if (e2 != cudaSuccess || m->num_sms < 1)
             s = ffail(PT_ECUDA, "tcgen05 product set-up: %s", cudaGetErrorString(e2));
+        else
+            m->tc_ready = true;
     }
     if (s != PT_OK) {
         pt_former_destroy(m);
@@ -919,7 +941,7 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
     Act& x = m->score;
     embed_score_kernel<<<(unsigned)M, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, x.h, N, d);
     FCK(cudaGetLastError());
-    const bool tc = m->cfg.attn_mode == 0 && (size_t)B * H * N * N * 6 <= kAttScratchBytes;
+    const bool tc = m->cfg.attn_mode != 1 && (size_t)B * H * N * N * 6 <= kAttScratchBytes;
     if (tc) {
         s = ensure_att(m, x, B);
         if (s != PT_OK) return s;

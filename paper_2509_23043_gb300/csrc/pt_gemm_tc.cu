@@ -379,6 +379,202 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+
+// Causal attention probabilities of the scoring pass for sequences of at most 256 positions:
+// P[b][h][i][j] = softmax_j(Q_i . K_j / 8) over j <= i (bfloat16, zero for j > i), for every
+// configuration b and head h, Q and K read in place from the bfloat16 [B N][3d] QKV buffer
+// (head h at columns 64 h and d + 64 h; head dimension 64). One tile per (b, h, block of 128
+// queries): S = Q K^T for the 128 queries against all N keys in one tcgen05.mma group (K 64,
+// N 256: the whole score row is in TMEM), so the scores never leave the SM. The epilogue is
+// two groups of four warps, one per TMEM accumulator, taking alternate tiles; a thread owns a
+// row: one pass over its 256 columns keeps the running maximum and sum, a second writes
+// exp(s - max) / sum (fast exponential: the probabilities are stored in bfloat16). Keys past
+// the configuration's N rows (the next configuration's, or zero fill past the buffer) fall
+// beyond every query's causal range.
+constexpr int ATT_EPI_WARPS = 8;
+constexpr int ATT_THREADS = 64 + 32 * ATT_EPI_WARPS;
+constexpr size_t ATT_SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + (size_t)ATT_EPI_WARPS * STG_BYTES;
+
+__global__ void __launch_bounds__(ATT_THREADS, 1)
+    attn_softmax_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmK,
+                        __nv_bfloat16* __restrict__ P, int B, int N, int H, int d, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t ring = (raw + 1023u) & ~1023u;
+    uint8_t* ring_ptr = smem_raw + (ring - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring_ptr + (size_t)STAGES * STAGE_BYTES);
+    const uint32_t bar0 = smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+    auto tempty = [&](int a) { return bar0 + 8u * (2 * STAGES + NUM_ACC + a); };
+    const uint32_t done = bar0 + 8u * (2 * STAGES + 2 * NUM_ACC);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 * NUM_ACC + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint8_t* staging = ring_ptr + (size_t)STAGES * STAGE_BYTES + BAR_BYTES;
+    auto sA = [&](int s) { return ring + (uint32_t)s * STAGE_BYTES; };
+    auto sB = [&](int s) { return ring + (uint32_t)s * STAGE_BYTES + A_BYTES; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_tiles = (N + BM - 1) / BM;
+    const int tiles = B * H * m_tiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            bar_init(full(s), 1);
+            bar_init(empty(s), 1);
+        }
+        for (int a = 0; a < NUM_ACC; ++a) {
+            bar_init(tfull(a), 1);
+            bar_init(tempty(a), 32 * ATT_EPI_WARPS / NUM_ACC);   // one group per accumulator
+        }
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, armed = 0, armed_par = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+                const int bh = t / m_tiles, mt = t - bh * m_tiles;
+                const int b = bh / H, h = bh - b * H;
+                if (!bar_wait(empty(stage), phase ^ 1u, abort_flag, err, 11)) {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (armed >> s & 1u) {
+                            const unsigned long long t0 = now_ns();
+                            while (!bar_try(full(s), armed_par >> s & 1u) && now_ns() - t0 < WAIT_NS) {}
+                        }
+                    break;
+                }
+                bar_expect_tx(full(stage), STAGE_BYTES);
+                tma_load_2d(sA(stage), &tmQ, h * 64, b * N + mt * BM, full(stage));   // 128 queries
+                tma_load_2d(sB(stage), &tmK, d + h * 64, b * N, full(stage));         // 256 keys
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+                if (!bar_wait(tempty(acc), acc_phase ^ 1u, abort_flag, err, 12)) break;
+                tc_fence_after();
+                if (!bar_wait(full(stage), phase, abort_flag, err, 13)) break;
+                tc_fence_after();
+                const uint32_t dcol = tmem + (uint32_t)(acc * BN);
+                const uint64_t ad = sw128_desc(sA(stage)), bd = sw128_desc(sB(stage));
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) mma_f16(dcol, ad + 2u * k, bd + 2u * k, k != 0 ? 1u : 0u);
+                mma_commit(empty(stage));
+                mma_commit(tfull(acc));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                if (++acc == NUM_ACC) { acc = 0; acc_phase ^= 1u; }
+            }
+            mma_commit(done);
+            const unsigned long long t0 = now_ns();
+            while (!bar_try(done, 0) && now_ns() - t0 < WAIT_NS) {}
+        }
+    } else {
+        const int q = warp & 3;                   // TMEM lane quarter: rows 32 q .. 32 q + 31
+        const int grp = (warp - 2) >> 2;          // accumulator (and tile parity) of this group
+        uint8_t* stg = staging + (size_t)(warp - 2) * STG_BYTES;
+        const int rr = lane >> 2, part = lane & 3;
+        const int row = 32 * q + lane;            // the thread's row of the tile
+        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(grp * BN);
+        uint32_t ph = 0;
+        for (int t = blockIdx.x + grp * gridDim.x; t < tiles; t += NUM_ACC * gridDim.x) {
+            // a group's four warps leave together only through this wait: every one of them
+            // sees the same phase complete, or every one runs out of time or sees the abort
+            const bool ok = bar_wait(tfull(grp), ph, abort_flag, err, 14);
+            if (!__all_sync(0xFFFFFFFFu, ok)) break;
+            ph ^= 1u;
+            tc_fence_after();
+            const int bh = t / m_tiles, mt = t - bh * m_tiles;
+            const int i = mt * BM + row;                   // query position
+            const int jmax = min(i, N - 1);                // keys 0 .. jmax
+            // the warp's last key (its last row's): tcgen05.ld is warp-collective, so every
+            // lane runs the same chunks and masks its own keys
+            const int jwarp = min(mt * BM + 32 * q + 31, N - 1);
+            // pass 1: running maximum and sum of exp over the row, 32 columns at a time
+            float mx = -INFINITY, sum = 0.f;
+#pragma unroll 1
+            for (int ch = 0; ch * 32 <= jwarp; ++ch) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(32 * ch), v);
+                float cm = -INFINITY;
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (32 * ch + c <= jmax) cm = fmaxf(cm, __uint_as_float(v[c]) * 0.125f);
+                const float nm = fmaxf(mx, cm);
+                float cs = 0.f;
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (32 * ch + c <= jmax) cs += __expf(__uint_as_float(v[c]) * 0.125f - nm);
+                sum = sum * __expf(mx - nm) + cs;
+                mx = nm;
+            }
+            const float inv = 1.f / sum;
+            // pass 2: the probabilities, 32 keys (64 bytes) per row at a time through the
+            // staging buffer; four lanes write a row's 64 bytes; rows and keys past N are not
+            // written, keys j > i are zeros
+            const size_t prow0 = ((size_t)bh * N + (size_t)mt * BM + 32 * q) * N;
+            const int nch = (N + 31) / 32;
+#pragma unroll 1
+            for (int ch = 0; ch < nch; ++ch) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(32 * ch), v);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 8 * k4 + 2 * e;
+                        const float p0 = 32 * ch + c <= jmax ? __expf(__uint_as_float(v[c]) * 0.125f - mx) * inv : 0.f;
+                        const float p1 =
+                            32 * ch + c + 1 <= jmax ? __expf(__uint_as_float(v[c + 1]) * 0.125f - mx) * inv : 0.f;
+                        const __nv_bfloat162 r2 = __floats2bfloat162_rn(p0, p1);
+                        w[e] = *reinterpret_cast<const uint32_t*>(&r2);
+                    }
+                    *reinterpret_cast<uint4*>(stg + lane * STG_PITCH + 16 * k4) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                __syncwarp();
+                const int c0 = 32 * ch;
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int r = rr + 8 * it;
+                    const int qi = mt * BM + 32 * q + r;
+                    if (qi < N && c0 + 8 * part < N)
+                        *reinterpret_cast<uint4*>(P + prow0 + (size_t)r * N + c0 + 8 * part) =
+                            *reinterpret_cast<const uint4*>(stg + r * STG_PITCH + 16 * part);
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            bar_arrive(tempty(grp));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
 }  // namespace tcg
 
 namespace {
@@ -412,6 +608,7 @@ cudaError_t gemm_tc_setup() {
     cudaError_t e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiGelu>, at, (int)tcg::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiBias>, at, (int)tcg::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiResid>, at, (int)tcg::SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::attn_softmax_kernel, at, (int)tcg::ATT_SMEM_BYTES);
     return e;
 }
 
@@ -442,5 +639,25 @@ cudaError_t gemm_tc(int epi, const __nv_bfloat16* A, const __nv_bfloat16* Wt, co
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+bool attn_softmax_tc_supported(int N, int d) {
+    return N >= 1 && N <= tcg::BN && N % 8 == 0 && d % 64 == 0;
+}
+
+cudaError_t attn_softmax_tc(const __nv_bfloat16* qkv, __nv_bfloat16* P, int B, int N, int H, int d, int num_sms,
+                            int* d_err, cudaStream_t stream) {
+    if (!g_encode || !attn_softmax_tc_supported(N, d) || B < 1) return cudaErrorInvalidValue;
+    if (((uintptr_t)qkv | (uintptr_t)P) & 15u) return cudaErrorMisalignedAddress;
+    // two maps over the same buffer: query tiles of 64 columns by 128 rows, key tiles of 64
+    // columns by 256 rows
+    CUtensorMap tq, tk;
+    if (!encode_2d(&tq, qkv, (uint64_t)3 * d, (uint64_t)B * N, tcg::BK, tcg::BM) ||
+        !encode_2d(&tk, qkv, (uint64_t)3 * d, (uint64_t)B * N, tcg::BK, tcg::BN))
+        return cudaErrorInvalidValue;
+    const int tiles = B * H * ((N + tcg::BM - 1) / tcg::BM);
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    tcg::attn_softmax_kernel<<<grid, tcg::ATT_THREADS, tcg::ATT_SMEM_BYTES, stream>>>(tq, tk, P, B, N, H, d, d_err);
     return cudaGetLastError();
 }

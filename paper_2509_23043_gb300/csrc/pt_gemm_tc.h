@@ -20,3 +20,14 @@ bool gemm_tc_supported(int N, int K);
 // memory) and the kernel returns.
 cudaError_t gemm_tc(int epi, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const void* bias, void* C,
                     int M, int N, int K, int num_sms, int* d_err, cudaStream_t stream);
+
+// Whether the fused causal-softmax kernel takes sequences of N positions and model width d:
+// N <= 256 (one key tile), N a multiple of 8, d a multiple of 64 (head dimension 64).
+bool attn_softmax_tc_supported(int N, int d);
+
+// P[b][h][i][j] = softmax over j <= i of Q_i . K_j / 8 (0 for j > i), bfloat16 [B][H][N][N],
+// from the bfloat16 query/key/value buffer qkv [B N][3d] (head h: queries at columns 64 h,
+// keys at d + 64 h). One persistent block per SM; a wait that runs out records a nonzero code
+// in *d_err and the kernel returns.
+cudaError_t attn_softmax_tc(const __nv_bfloat16* qkv, __nv_bfloat16* P, int B, int N, int H, int d, int num_sms,
+                            int* d_err, cudaStream_t stream);

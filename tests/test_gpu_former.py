@@ -26,10 +26,12 @@ def _model(N, index=0, shape=None, attn_mode=0):
     return shp, W, Former(shp, packed, attn_mode=attn_mode)
 
 
-@pytest.mark.parametrize("attn_mode", [0, 1])
+@pytest.mark.parametrize("attn_mode", [0, 1, 2])
 @pytest.mark.parametrize("N,B", [(37, 6), (200, 4), (300, 3)])
 def test_score_matches_oracle(N, B, attn_mode):
-    # attn_mode 0: attention as batched tensor-core products; 1: the streaming FP32 kernel
+    # attn_mode 0: tensor-core attention, scores and softmax fused for N = 200 (37 is not a
+    # multiple of 8 and 300 exceeds one key tile: those take mode 2's path); 1: the streaming
+    # FP32 kernel; 2: cuBLASLt scores and the softmax kernel
     shp, W, m = _model(N, index=N, attn_mode=attn_mode)
     g = np.random.default_rng(N)
     X = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
@@ -71,6 +73,36 @@ def test_tcgen05_projections_match_library_products(N, B):
         assert np.abs(lq0.cpu().numpy() - lq1.cpu().numpy()).max() < 0.02 * np.sqrt(N)
         assert d.max() > 0                    # the two paths are distinct code
     lg_o, _ = F.score(W, shp, X.cpu().numpy(), beta.cpu().numpy().astype(np.float64))
+    assert np.all(np.abs(lg0 - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
+
+
+@pytest.mark.parametrize("N,B", [(8, 5), (64, 3), (136, 2), (200, 4), (256, 2)])
+def test_fused_attention_matches_library_attention(N, B):
+    # attn_mode 0: the scores and the causal softmax in one tcgen05 kernel (one tile per 128
+    # queries, the whole score row in TMEM) against attn_mode 2 (cuBLASLt scores in FP32 and
+    # the softmax kernel): the same bfloat16 queries and keys and FP32 scores, so the
+    # probabilities differ only by the order of the exponential sums; N = 8 .. 256 covers one
+    # query tile, a ragged second tile (136 = 128 + 8) and the largest key tile; the logits
+    # also agree with the float64 oracle
+    from paper_2509_23043_gb300.former import Former
+    shp = I.FormerShape(n_spins=N)
+    W, packed = I.former_weights(shp, index=2 * N + 1)
+    fused = Former(shp, packed, attn_mode=0)
+    lib = Former(shp, packed, attn_mode=2)
+    g = np.random.default_rng(N + 3)
+    Xh = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
+    bh = g.uniform(0.1, 3.0, B).astype(np.float32)
+    X, beta = torch.from_numpy(Xh).cuda(), torch.from_numpy(bh).cuda()
+    for _ in range(2):
+        lq0, lg0 = fused.score(X, beta, logits=True)
+        lq1, lg1 = lib.score(X, beta, logits=True)
+        fused.check()
+        lg0, lg1 = lg0.cpu().numpy(), lg1.cpu().numpy()
+        assert np.isfinite(lg0).all()
+        d = np.abs(lg0 - lg1)
+        print("fused attention vs library attention: max logit difference", d.max())
+        assert d.max() < 0.01, d.max()
+    lg_o, _ = F.score(W, shp, Xh, bh.astype(np.float64))
     assert np.all(np.abs(lg0 - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
 
 
