@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-configs", action="store_true")
-    p.add_argument("--workloads", default="plain,engines,ragged,factor,ladder,context,tts,former",
+    p.add_argument("--workloads", default="plain,engines,ragged,factor,ladder,large,context,tts,former",
                    help="other workloads to measure after the main one")
     p.add_argument("--factor-sweeps", type=int, default=20000)
     p.add_argument("--factor-pool-size", type=int, default=512)
@@ -873,6 +873,52 @@ def tts_scaling(stream, ws=(8, 9, 10), n_products=32, runs=23,
                              for m, d in per[n]["modes"].items()} for n in per}}
 
 
+def large_lattice(stream, n=152, L=20, R=64, P=16, cycles=20, reps=3):
+    """Lattices too large for shared memory: n EA instances of L = 20 (N = 8000) with R = 64
+    (two walker blocks: 128 KB of spins and 128 KB of neighbour table per instance, kept in
+    global memory and L2), Metropolis, proposals every 10 cycles from random pools of P,
+    autotuned, with the same ALU roofline count as the main workload."""
+    import paper_2509_23043_gb300 as pt
+    import instances as I
+    insts = [I.ea_instance(L, index=50_000 + k) for k in range(n)]
+    betas = I.geometric_betas(0.1, 3.0, R)
+    cfg = pt.Config(seed=0x1A46E, propose_every=10, propose_start=0, pool_size=P)
+    ctx = pt.create_instances(insts, [betas] * n, cfg, prop_enabled=[[1] * (R - 2) + [0, 0]] * n,
+                              instance_ids=list(range(n)), stream=stream.cuda_stream)
+    nw = (L ** 3 + 31) // 32
+    rng = np.random.default_rng(0x1A46E)
+    for e0 in range(0, P, 4):
+        words = rng.integers(0, 2 ** 32, size=(4, n, R, nw), dtype=np.uint64).astype(np.uint32)
+        pt.load_proposals_packed(ctx, words, e0, 4)
+        stream.synchronize()
+    pt.autotune(ctx, probe_cycles=5)
+    pt.run_cycles(ctx, 40)
+    stream.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        s0, e0 = _ev_pair()
+        s0.record(stream)
+        pt.run_cycles(ctx, cycles)
+        e0.record(stream)
+        e0.synchronize()
+        best = min(best, s0.elapsed_time(e0))
+    rate = n * R * L ** 3 * cycles / (best * 1e6)
+    e_blocks = plane_blocks_of(ctx, 0, insts[0], "metropolis")
+    ops = alu_ops_per_word(e_blocks) / 32
+    peak = pt.calibrate_int(0)[0] / 1e12
+    g = pt.group_info(ctx)[0]
+    pt.destroy(ctx)
+    return {"workload": f"{n} EA +-J instances, L={L} (N={L ** 3}), R={R}, Metropolis, proposals every 10 "
+                        f"cycles from random pools of {P}, spins and neighbour table in global memory "
+                        f"(the instance does not fit shared memory), autotuned, {cycles} cycles per launch",
+            "attempts_per_ns": rate, "ms_per_launch": best, "threads_per_block": g["threads"],
+            "shared_memory_per_block": g["smem"],
+            "roofline": {"bound": "alu", "achieved": rate * ops * 1e9 / 1e12, "peak": peak, "unit": "TOP/s",
+                         "frac": rate * ops * 1e9 / 1e12 / peak, "traffic": None, "kernel": "lattice_kernel (GSP)",
+                         "alu_ops_per_attempt": ops, "plane_blocks_per_word": e_blocks,
+                         "peak_basis": "measured in this run by pt_calibrate_int"}}
+
+
 def ladder_workload(stream, n=64, R=32, iterations=6, sweeps=2000):
     """Ladder optimisation for uniform swap acceptance on the EA L=10 family (a shared
     ladder, R=32 on 0.1 -> 3.0, starting geometric): swap acceptance per pair before and
@@ -1348,6 +1394,8 @@ def main():
                                                     gap=args.factor_pool_gap, cpu_pool=cpu_pool)
         if "ladder" in wl:
             others["ladder"] = ladder_workload(stream)
+        if "large" in wl:
+            others["large_lattice"] = large_lattice(stream)
         if "tts" in wl:
             others["factorization_tts"] = factorization_tts(stream)
         if "tts_scaling" in wl:
