@@ -509,9 +509,15 @@ void free_act(Act& a) {
     a = Act{};
 }
 
-// the scores and probabilities of one layer's attention, B H N^2 entries of 6 bytes, are kept
-// when they fit this budget; longer sequences use the streaming attention kernel
+// the probabilities of one layer's attention (B H N^2 entries of 2 bytes, and 4 more for the
+// FP32 scores of the unfused path) are kept when they fit this budget; else the streaming
+// attention kernel runs
 constexpr size_t kAttScratchBytes = size_t(2) << 30;
+
+// the scores and the causal softmax in one tcgen05 kernel (no FP32 score buffer)
+bool attn_fused(const pt_former* m) {
+    return m->cfg.attn_mode == 0 && m->tc_ready && attn_softmax_tc_supported(m->cfg.n_spins, m->cfg.d_model);
+}
 
 pt_status ensure_att(pt_former* m, Act& a, int B) {
     const size_t N = m->cfg.n_spins, H = m->cfg.n_heads, d = m->cfg.d_model;
@@ -523,7 +529,7 @@ pt_status ensure_att(pt_former* m, Act& a, int B) {
     a.att_elems = 0;
     const size_t rows = (size_t)B * N;
     FCK(cudaMalloc(&a.qkv16, rows * 3 * d * 2));
-    FCK(cudaMalloc(&a.S, elems * 4));
+    if (!attn_fused(m)) FCK(cudaMalloc(&a.S, elems * 4));
     FCK(cudaMalloc(&a.P, elems * 2));
     a.att_elems = elems;
     return PT_OK;
@@ -676,7 +682,7 @@ pt_status attention_tc(pt_former* m, Act& x, int B) {
     const long long cfg_stride = (long long)N * ld;     // one configuration's rows
     const long long nn = (long long)N * N;
     pt_status s = PT_OK;
-    if (m->cfg.attn_mode == 0 && m->tc_ready && attn_softmax_tc_supported(N, d)) {
+    if (attn_fused(m)) {
         // the scores and the causal softmax in one tcgen05 kernel, P written directly
         FCK(attn_softmax_tc(x.qkv16, x.P, B, N, H, d, m->num_sms, m->d_err, m->exec));
     } else {
@@ -941,7 +947,8 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
     Act& x = m->score;
     embed_score_kernel<<<(unsigned)M, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, x.h, N, d);
     FCK(cudaGetLastError());
-    const bool tc = m->cfg.attn_mode != 1 && (size_t)B * H * N * N * 6 <= kAttScratchBytes;
+    // the probabilities (2 bytes per entry), and the FP32 scores unless fused (4 more)
+    const bool tc = m->cfg.attn_mode != 1 && (size_t)B * H * N * N * (attn_fused(m) ? 2 : 6) <= kAttScratchBytes;
     if (tc) {
         s = ensure_att(m, x, B);
         if (s != PT_OK) return s;

@@ -205,12 +205,10 @@ __device__ void graph_sweep_t(const GraphInst& I, GraphSmem& S, const RunArgs& a
                                                   (kDomWord << 24) | (uint32_t)oct, iid), a);
             const uint32_t hw[4] = {rh.x, rh.y, rh.z, rh.w};
             uint32_t below = 0, tie = 0;   // u < thr on the high halves; undecided there
-            const uint32_t drawn = valid & ~forced;
+            // every walker draws, without a branch: a padding walker reads slot 0's row and a
+            // forced Metropolis move row + 0, both in the table; their results are masked
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                // Gibbs draws for every walker (a padding walker reads slot 0's row, always in
-                // the table, and its byte is masked below); Metropolis skips the forced moves
-                if (!GIBBS && !(drawn >> j & 1u)) continue;
                 const uint32_t t = S.thr[index(j)];
                 const uint32_t x = (j & 1) ? (hw[j >> 1] << 16) : (hw[j >> 1] & 0xFFFF0000u);
                 below |= (uint32_t)(x < t) << j;
