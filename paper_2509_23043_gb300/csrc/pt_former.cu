@@ -255,16 +255,10 @@ __global__ void causal_softmax_loop_kernel(const float* __restrict__ S, __nv_bfl
         pr[j] = __float2bfloat16_rn(j <= i ? expf(sr[j] - mx) * inv : 0.f);
 }
 
-// append the keys and values of step t to the cache [B][N][2d] of one layer
-__global__ void kv_append_kernel(const float* __restrict__ qkv, float* __restrict__ cache, int N, int d, int t) {
-    const int b = blockIdx.x;
-    for (int c = threadIdx.x; c < 2 * d; c += blockDim.x)
-        cache[((size_t)b * N + t) * 2 * d + c] = qkv[(size_t)b * 3 * d + d + c];
-}
-
-// Attention of the step-t query against the cached keys 0..t: block b, one warp per head;
-// lanes score keys lane, lane + 32, ..., then each lane sums two of the 64 output dimensions.
-__global__ void attention_step_kernel(const float* __restrict__ qkv, const float* __restrict__ cache,
+// Attention of the step-t query against the cached keys 0..t: block b, one warp per head. The
+// warp first appends step t's key and value of its head to the cache; lanes then score keys
+// lane, lane + 32, ..., and each lane sums two of the 64 output dimensions.
+__global__ void attention_step_kernel(const float* __restrict__ qkv, float* __restrict__ cache,
                                       __nv_bfloat16* __restrict__ out, int N, int d, int t) {
     extern __shared__ float sm[];              // per warp: q [64], p [N]
     const int hd = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.x;
@@ -273,6 +267,13 @@ __global__ void attention_step_kernel(const float* __restrict__ qkv, const float
     const float* qr = qkv + (size_t)b * 3 * d + hd * kDH;
     qs[lane] = qr[lane] * 0.125f;
     qs[lane + 32] = qr[lane + 32] * 0.125f;
+    // append this step's key and value of head hd to the cache (row t), read back below
+    float* crow = cache + ((size_t)b * N + t) * 2 * d + hd * kDH;
+#pragma unroll
+    for (int c = lane; c < kDH; c += 32) {
+        crow[c] = qr[d + c];
+        crow[d + c] = qr[2 * d + c];
+    }
     __syncwarp();
     const float* kb = cache + (size_t)b * N * 2 * d + hd * kDH;
     float mx = -INFINITY;
@@ -812,7 +813,6 @@ pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* 
         for (int l = 0; l < m->cfg.n_layers; ++l) {
             float* cl = m->cache + (size_t)l * B * N * 2 * d;
             pt_status s = block(m, m->step, (size_t)B, m->layers[l], false, [&]() -> pt_status {
-                kv_append_kernel<<<B, 256, 0, m->exec>>>(m->step.qkv, cl, N, d, t);
                 attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(m->step.qkv, cl, m->step.o, N, d, t);
                 FCK(cudaGetLastError());
                 return PT_OK;
