@@ -1064,7 +1064,8 @@ def isingformer_workload(stream, B=1024, reps=5):
                                             "attention's FP32 FLOPs are reported beside it"}},
              "sample": {"configs_per_s": B / (ms_s * 1e-3), "ms_per_call": ms_s, "prefix": npre,
                         "gpu_launches_per_call": "one CUDA graph of N steps",
-                        f"configs_per_s_B{8 * B}": Bl / (ms_sl * 1e-3), f"ms_per_call_B{8 * B}": ms_sl},
+                        f"configs_per_s_B{8 * B}": Bl / (ms_sl * 1e-3), f"ms_per_call_B{8 * B}": ms_sl,
+                        "roofline": sample_roofline(shp, Bl, ms_sl)},
              "e2e": {"value": B / (ms_e * 1e-3), "unit": "configs/s", "h2d_bytes_per_step": B * N,
                      "d2h_bytes_per_step": B * 4}}
     # the same pass with every projection on cuBLASLt (proj_mode 1) and with every suitable
@@ -1087,12 +1088,28 @@ def isingformer_workload(stream, B=1024, reps=5):
     return out_d
 
 
+def sample_roofline(shp, B, ms):
+    """HBM roofline of autoregressive sampling: at step t every layer reads the cached key and
+    value rows 0..t of each configuration (2 d FP32 values per row) and appends row t, so a call
+    moves L B 2d 4 (N(N+1)/2 + N) bytes of cache; the weights (a few MB, resident in L2) and
+    the per-step activations (B rows) are left out."""
+    N, d, L = shp.n_spins, shp.d_model, shp.n_layers
+    nbytes = L * B * 2 * d * 4.0 * (N * (N + 1) / 2 + N)
+    peak = _measured_peak("hbm_gbs")
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak if peak else None, "traffic": None, "configs_per_call": B,
+            "kernel": "the sampling call (one CUDA graph of N steps; the attention-step kernel "
+                      "streams the key/value cache)", "bytes_per_call": nbytes,
+            "note": "key/value cache bytes over the whole call's time"}
+
+
 def _measured_peak(key):
     p = ROOT / "MEASURED_PEAKS.json"
     try:
         return float(json.loads(p.read_text())[key])
     except (OSError, KeyError, ValueError):
-        return 1900.0 if key == "bf16_tflops" else None
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}.get(key)
 
 
 def _ev_pair():

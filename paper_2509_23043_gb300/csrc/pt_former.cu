@@ -256,56 +256,96 @@ __global__ void causal_softmax_loop_kernel(const float* __restrict__ S, __nv_bfl
 }
 
 // Attention of the step-t query against the cached keys 0..t: block b, one warp per head. The
-// warp first appends step t's key and value of its head to the cache; lanes then score keys
-// lane, lane + 32, ..., and each lane sums two of the 64 output dimensions.
-__global__ void attention_step_kernel(const float* __restrict__ qkv, float* __restrict__ cache,
-                                      __nv_bfloat16* __restrict__ out, int N, int d, int t) {
-    extern __shared__ float sm[];              // per warp: q [64], p [N]
+// warp first appends step t's key and value of its head to the cache. Each half-warp then takes
+// one cached row at a time (64 floats of this head, 256 contiguous bytes, a float4 per lane):
+// keys j = 2i + half for the scores, reduced over the half-warp's 16 lanes, then the value rows
+// in the same order for the weighted sum, the two halves added at the end. kStepRows rows per
+// half-warp are loaded before any is used, so every warp keeps kStepRows x 512 bytes in flight:
+// the kernel streams the cache, and its rate is set by the bytes in flight per SM.
+constexpr int kStepRows = 8;
+__global__ void __launch_bounds__(256) attention_step_kernel(const float* __restrict__ qkv,
+                                                             float* __restrict__ cache,
+                                                             __nv_bfloat16* __restrict__ out,
+                                                             int N, int d, int t) {
+    extern __shared__ float sm[];              // per warp: the t + 1 scores, then probabilities
     const int hd = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.x;
-    float* qs = sm + hd * (kDH + N);
-    float* ps = qs + kDH;
+    const int half = lane >> 4, c4 = 4 * (lane & 15);
+    float* ps = sm + hd * N;
     const float* qr = qkv + (size_t)b * 3 * d + hd * kDH;
-    qs[lane] = qr[lane] * 0.125f;
-    qs[lane + 32] = qr[lane + 32] * 0.125f;
-    // append this step's key and value of head hd to the cache (row t), read back below
+    float4 q = *reinterpret_cast<const float4*>(qr + c4);
+    q.x *= 0.125f; q.y *= 0.125f; q.z *= 0.125f; q.w *= 0.125f;
+    // append this step's key (lanes 0-15) and value (lanes 16-31) of head hd as row t
     float* crow = cache + ((size_t)b * N + t) * 2 * d + hd * kDH;
-#pragma unroll
-    for (int c = lane; c < kDH; c += 32) {
-        crow[c] = qr[d + c];
-        crow[d + c] = qr[2 * d + c];
-    }
+    *reinterpret_cast<float4*>(crow + half * d + c4) =
+        *reinterpret_cast<const float4*>(qr + (1 + half) * d + c4);
     __syncwarp();
-    const float* kb = cache + (size_t)b * N * 2 * d + hd * kDH;
+    const float* kb = cache + (size_t)b * N * 2 * d + hd * kDH + c4;
+    const size_t rs = 2 * (size_t)d;           // floats between consecutive cached rows
+    const int nk = t + 1;
     float mx = -INFINITY;
-    for (int j = lane; j <= t; j += 32) {
-        const float* kr = kb + (size_t)j * 2 * d;
-        float s = 0.f;
-#pragma unroll 16
-        for (int c = 0; c < kDH; ++c) s = fmaf(qs[c], kr[c], s);
-        ps[j] = s;
-        mx = fmaxf(mx, s);
+    for (int j0 = 0; j0 < nk; j0 += 2 * kStepRows) {
+        float s[kStepRows];
+#pragma unroll
+        for (int u = 0; u < kStepRows; ++u) {
+            const int j = j0 + 2 * u + half;
+            float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < nk) k = *reinterpret_cast<const float4*>(kb + j * rs);
+            s[u] = fmaf(q.x, k.x, fmaf(q.y, k.y, fmaf(q.z, k.z, q.w * k.w)));
+        }
+#pragma unroll
+        for (int u = 0; u < kStepRows; ++u) {
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+            const int j = j0 + 2 * u + half;
+            if (j < nk) {
+                if ((lane & 15) == 0) ps[j] = s[u];
+                mx = fmaxf(mx, s[u]);
+            }
+        }
     }
     mx = warp_max(mx);
+    __syncwarp();
     float sum = 0.f;
-    for (int j = lane; j <= t; j += 32) {
+    for (int j = lane; j < nk; j += 32) {
         const float p = expf(ps[j] - mx);
         ps[j] = p;
         sum += p;
     }
     sum = warp_sum(sum);
     __syncwarp();
-    float a0 = 0.f, a1 = 0.f;
     const float* vb = kb + d;
-    for (int j = 0; j <= t; ++j) {
-        const float p = ps[j];
-        const float* vr = vb + (size_t)j * 2 * d;
-        a0 = fmaf(p, vr[2 * lane], a0);
-        a1 = fmaf(p, vr[2 * lane + 1], a1);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j0 = 0; j0 < nk; j0 += 2 * kStepRows) {
+        float4 v[kStepRows];
+        float p[kStepRows];
+#pragma unroll
+        for (int u = 0; u < kStepRows; ++u) {
+            const int j = j0 + 2 * u + half;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            p[u] = 0.f;
+            if (j < nk) {
+                v[u] = *reinterpret_cast<const float4*>(vb + j * rs);
+                p[u] = ps[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStepRows; ++u) {
+            acc.x = fmaf(p[u], v[u].x, acc.x);
+            acc.y = fmaf(p[u], v[u].y, acc.y);
+            acc.z = fmaf(p[u], v[u].z, acc.z);
+            acc.w = fmaf(p[u], v[u].w, acc.w);
+        }
     }
-    const float inv = 1.f / sum;
-    __nv_bfloat16* o = out + (size_t)b * d + hd * kDH;
-    o[2 * lane] = __float2bfloat16_rn(a0 * inv);
-    o[2 * lane + 1] = __float2bfloat16_rn(a1 * inv);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 16);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 16);
+    if (half == 0) {
+        const float inv = 1.f / sum;
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (size_t)b * d + hd * kDH + c4);
+        o[0] = __floats2bfloat162_rn(acc.x * inv, acc.y * inv);
+        o[1] = __floats2bfloat162_rn(acc.z * inv, acc.w * inv);
+    }
 }
 
 // final layer norm and head of one row (one warp): the two logits and their log-softmax
@@ -806,7 +846,7 @@ pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, 
 pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* prefix, int npre,
                           int8_t* out, float* logq) {
     const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
-    const size_t smem = (size_t)H * (kDH + N) * 4;
+    const size_t smem = (size_t)H * N * 4;
     for (int t = 0; t < N; ++t) {
         embed_step_kernel<<<B, 256, 0, m->exec>>>(out, beta, m->tok, m->wb, m->bb, m->pe, m->step.h, N, d, t);
         FCK(cudaGetLastError());
@@ -982,7 +1022,7 @@ pt_status pt_former_sample(pt_former* m, int32_t B, const float* beta, const int
     if (B < 1) return ffail(PT_EINVAL, "B must be >= 1");
     if (n_prefix < 0 || n_prefix > N || (n_prefix > 0 && !prefix))
         return ffail(PT_EINVAL, "n_prefix must be in [0, N], with a prefix array when > 0");
-    if ((size_t)H * (kDH + N) * 4 > 48 * 1024)
+    if ((size_t)H * N * 4 > 48 * 1024)
         return ffail(PT_ENOTSUP, "sampling keeps per-head scores of N = %d positions in shared memory; N too large", N);
     pt_status s = ensure_act(m, m->step, (size_t)B);
     if (s != PT_OK) return s;
