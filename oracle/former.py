@@ -21,9 +21,11 @@ Readings where it is silent (each marked R below):
      a final layer norm, then a linear head to two logits;
   R3 GELU in its erf form between the two FFN maps;
   R4 sampling draws spin t = +1 iff u_t < P(+1 | prefix), u_t uniform in [0, 1).
-Parity unpinned: there are no trained weights, so no output of the paper's models can be
-compared; the pins are the model's structural facts (normalisation, causality, the start
-token, the positional code), checked in tests/test_former_oracle.py.
+There are no trained weights, so no output of the paper's models can be compared. The pins
+(tests/test_former_oracle.py) are the model's structural facts (normalisation, causality,
+the start token, the positional code, a layer-free closed form) and, for the decoder blocks,
+a library routine: PyTorch's nn.TransformerEncoderLayer with pre-layer-norm, exact GELU and
+a causal mask gives the same logits in float64.
 """
 from __future__ import annotations
 

@@ -120,3 +120,54 @@ def test_sampling_keeps_the_prefix():
     assert np.array_equal(S[:, :2], pre)
     _, lq_chk = F.score(W, SMALL, S, np.full(10, 1.1))
     assert np.allclose(lq, lq_chk, atol=1e-12)
+
+
+@pytest.mark.parametrize("shp", [SMALL, I.FormerShape(n_spins=9, d_model=64, n_heads=4, n_layers=3, d_ff=256)])
+def test_blocks_match_the_library_transformer_layer(shp):
+    # the pre-layer-norm decoder blocks (causal multi-head attention, GELU FFN, residuals,
+    # final layer norm and linear head) are PyTorch's nn.TransformerEncoderLayer with
+    # norm_first, exact GELU, no dropout and a causal mask: the oracle's logits equal the
+    # library stack's on the same embedded input, in float64. A transposed operand, a head
+    # split or scale, a residual or a layer norm in the wrong place each break the equality.
+    torch = pytest.importorskip("torch")
+    nn = torch.nn
+    W, _ = I.former_weights(shp, index=5)
+    d, H, F_ = shp.d_model, shp.n_heads, shp.d_ff
+    g = np.random.default_rng(9)
+    B, N = 3, shp.n_spins
+    X = np.where(g.random((B, N)) < 0.5, 1, -1).astype(np.int8)
+    beta = g.uniform(0.0, 4.0, B)
+    logits, _ = F.score(W, shp, X, beta)
+
+    tok = F.input_tokens(X)
+    h = (W["tok_emb"][tok] + (beta[:, None] * W["w_beta"] + W["b_beta"])[:, None, :]
+         + F.positional_encoding(N, d)[None])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).double()
+    layers = []
+    for l in range(shp.n_layers):
+        p = f"l{l}."
+        lay = nn.TransformerEncoderLayer(d, H, dim_feedforward=F_, dropout=0.0, activation="gelu",
+                                         layer_norm_eps=F.LN_EPS, batch_first=True, norm_first=True)
+        lay = lay.double().eval()
+        with torch.no_grad():
+            lay.self_attn.in_proj_weight.copy_(t(W[p + "w_qkv"].T))
+            lay.self_attn.in_proj_bias.copy_(t(W[p + "b_qkv"]))
+            lay.self_attn.out_proj.weight.copy_(t(W[p + "w_o"].T))
+            lay.self_attn.out_proj.bias.copy_(t(W[p + "b_o"]))
+            lay.linear1.weight.copy_(t(W[p + "w_1"].T))
+            lay.linear1.bias.copy_(t(W[p + "b_1"]))
+            lay.linear2.weight.copy_(t(W[p + "w_2"].T))
+            lay.linear2.bias.copy_(t(W[p + "b_2"]))
+            lay.norm1.weight.copy_(t(W[p + "ln1_g"]))
+            lay.norm1.bias.copy_(t(W[p + "ln1_b"]))
+            lay.norm2.weight.copy_(t(W[p + "ln2_g"]))
+            lay.norm2.bias.copy_(t(W[p + "ln2_b"]))
+        layers.append(lay)
+    mask = torch.triu(torch.ones(N, N, dtype=torch.bool), diagonal=1)
+    with torch.no_grad():
+        z = t(h)
+        for lay in layers:
+            z = lay(z, src_mask=mask)
+        z = torch.nn.functional.layer_norm(z, (d,), t(W["lnf_g"]), t(W["lnf_b"]), eps=F.LN_EPS)
+        ref = (z @ t(W["w_out"]) + t(W["b_out"])).numpy()
+    assert np.abs(logits - ref).max() < 1e-10
