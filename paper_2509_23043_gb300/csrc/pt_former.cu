@@ -70,17 +70,45 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // h[b N + t] = tok_emb[token] + (beta_b W_beta + b_beta) + PE[t]; token = start (2) at t = 0,
-// else the token of spin t - 1 (teacher forcing: the configurations scored).
+// else the token of spin t - 1 (teacher forcing: the configurations scored). One warp per
+// row; with y given, the row's layer norm (gain g, bias bt; the first block's, computed as
+// layernorm_kernel computes it) is written to y in the same pass, so h is not read back.
+template <int D>
 __global__ void embed_score_kernel(const int8_t* __restrict__ spins, const float* __restrict__ beta,
                                    const float* __restrict__ tok, const float* __restrict__ wb,
                                    const float* __restrict__ bb, const float* __restrict__ pe,
-                                   float* __restrict__ h, int N, int d) {
-    const size_t row = blockIdx.x;
+                                   const float* __restrict__ g, const float* __restrict__ bt,
+                                   float* __restrict__ h, __nv_bfloat16* __restrict__ y, size_t M,
+                                   int N) {
+    const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
     const int b = (int)(row / N), t = (int)(row - (size_t)b * N);
     const int k = t == 0 ? 2 : (spins[(size_t)b * N + t - 1] > 0 ? 1 : 0);
     const float be = beta[b];
-    for (int c = threadIdx.x; c < d; c += blockDim.x)
-        h[row * d + c] = tok[k * d + c] + (be * wb[c] + bb[c]) + pe[(size_t)t * d + c];
+    float v[D / 32];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        const int c = lane + 32 * i;
+        v[i] = tok[k * D + c] + (be * wb[c] + bb[c]) + pe[(size_t)t * D + c];
+        h[row * D + c] = v[i];
+        s += v[i];
+    }
+    if (!y) return;
+    const float mu = warp_sum(s) / D;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        v[i] -= mu;
+        q += v[i] * v[i];
+    }
+    const float rstd = rsqrtf(warp_sum(q) / D + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < D / 32; ++i) {
+        const int c = lane + 32 * i;
+        y[row * D + c] = __float2bfloat16_rn(v[i] * rstd * g[c] + bt[c]);
+    }
 }
 
 // one sampling step: h[b] for position t, the token of the spin drawn at t - 1
@@ -802,9 +830,11 @@ constexpr size_t kTcMinRows = 16384;
 // one pre-layer-norm block on rows [0, M) of `a` (attention by `attn`; query/key/value to
 // the bfloat16 buffer when qkv_bf16, the operand layout of the tensor-core attention). The
 // products run on this library's tcgen05 kernels (bias, GELU and residual in their
-// epilogues) or on cuBLASLt as proj_mode says (include/pt_former.h).
+// epilogues) or on cuBLASLt as proj_mode says (include/pt_former.h). ln1_done: the block's first
+// layer norm is already in x.a (written with the embedding).
 template <class AttnFn>
-pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, AttnFn attn) {
+pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, bool ln1_done,
+                AttnFn attn) {
     const int d = m->cfg.d_model, F = m->cfg.d_ff;
     const bool tc = m->cfg.proj_mode == 2;                        // every suitable projection
     const bool tc_ffn1 = tc || (m->cfg.proj_mode == 0 && M >= kTcMinRows);
@@ -813,7 +843,7 @@ pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, 
         FCK(gemm_tc(epi, A, Wt, b, C, (int)M, n, k, m->num_sms, m->d_err, m->exec));
         return PT_OK;
     };
-    pt_status s = layernorm(m, x.h, Ly.ln1_g, Ly.ln1_b, x.a, M);
+    pt_status s = ln1_done ? PT_OK : layernorm(m, x.h, Ly.ln1_g, Ly.ln1_b, x.a, M);
     if (s == PT_OK) {
         if (qkv_bf16 && tc && gemm_tc_supported(3 * d, d))
             s = tc_gemm(kEpiBias, x.a, Ly.w_qkvt, Ly.b_qkv16, x.qkv16, 3 * d, d);
@@ -852,7 +882,7 @@ pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* 
         FCK(cudaGetLastError());
         for (int l = 0; l < m->cfg.n_layers; ++l) {
             float* cl = m->cache + (size_t)l * B * N * 2 * d;
-            pt_status s = block(m, m->step, (size_t)B, m->layers[l], false, [&]() -> pt_status {
+            pt_status s = block(m, m->step, (size_t)B, m->layers[l], false, false, [&]() -> pt_status {
                 attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(m->step.qkv, cl, m->step.o, N, d, t);
                 FCK(cudaGetLastError());
                 return PT_OK;
@@ -985,7 +1015,18 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
     pt_status s = ensure_act(m, m->score, M);
     if (s != PT_OK) return s;
     Act& x = m->score;
-    embed_score_kernel<<<(unsigned)M, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, x.h, N, d);
+    // the embedding, with the first block's layer norm in the same pass
+    const bool ln1_fused = m->cfg.n_layers > 0;
+    const float* g0 = ln1_fused ? m->layers[0].ln1_g : nullptr;
+    const float* b0 = ln1_fused ? m->layers[0].ln1_b : nullptr;
+    __nv_bfloat16* y0 = ln1_fused ? x.a : nullptr;
+    const unsigned eg = (unsigned)((M + 7) / 8);
+    switch (d) {
+        case 64: embed_score_kernel<64><<<eg, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, g0, b0, x.h, y0, M, N); break;
+        case 128: embed_score_kernel<128><<<eg, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, g0, b0, x.h, y0, M, N); break;
+        case 256: embed_score_kernel<256><<<eg, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, g0, b0, x.h, y0, M, N); break;
+        case 512: embed_score_kernel<512><<<eg, 256, 0, m->exec>>>(spins, beta, m->tok, m->wb, m->bb, m->pe, g0, b0, x.h, y0, M, N); break;
+    }
     FCK(cudaGetLastError());
     // the probabilities (2 bytes per entry), and the FP32 scores unless fused (4 more)
     const bool tc = m->cfg.attn_mode != 1 && (size_t)B * H * N * N * (attn_fused(m) ? 2 : 6) <= kAttScratchBytes;
@@ -994,7 +1035,7 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
         if (s != PT_OK) return s;
     }
     for (int l = 0; l < m->cfg.n_layers && s == PT_OK; ++l) {
-        s = block(m, x, M, m->layers[l], tc, [&]() -> pt_status {
+        s = block(m, x, M, m->layers[l], tc, l == 0 && ln1_fused, [&]() -> pt_status {
             if (tc) return attention_tc(m, x, B);
             attention_kernel<<<dim3((N + kAQ - 1) / kAQ, H, B), kAQ, 0, m->exec>>>(x.qkv, x.o, N, d);
             FCK(cudaGetLastError());

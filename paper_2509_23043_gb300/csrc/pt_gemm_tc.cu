@@ -2,7 +2,7 @@
 // of the IsingFormer's blocks (Methods, "IsingFormer architecture and training"):
 //
 //     kEpiGelu:  C[M][N] = GELU(A[M][K] W[K][N] + b[N])   bfloat16 C and b (first FFN map),
-//                GELU(x) = x (1 + erf(x / sqrt 2)) / 2 (erf to 1.5e-7, see gelu_erf);
+//                GELU(x) = x (1 + erf(x / sqrt 2)) / 2 (erf to 1.5e-7, see gelu_erf2);
 //     kEpiBias:  C[M][N] = A W + b                         bfloat16 C and b (query/key/value);
 //     kEpiResid: C[M][N] += A W + b                        FP32 C and b (output map and second
 //                                                          FFN map into the residual stream).
@@ -155,23 +155,57 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// GELU(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from Abramowitz and Stegun, Handbook of
-// Mathematical Functions, formula 7.1.26: for a >= 0,
+// Paired FP32 arithmetic (sm_100 and later): one instruction applies an IEEE operation to both
+// halves of a 64-bit register pair, each half rounded as the scalar operation rounds it.
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t dup(float c) { return f2(c, c); }
+__device__ __forceinline__ void split2(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+constexpr uint64_t kNeg2 = 0x8000000080000000ull;     // both sign bits
+
+// GELU(x) = x (1 + erf(x / sqrt 2)) / 2 of two values, with erf from Abramowitz and Stegun,
+// Handbook of Mathematical Functions, formula 7.1.26: for a >= 0,
 //     erf(a) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-a^2) + eps,  t = 1 / (1 + p a),
 //     |eps| <= 1.5e-7,
-// with the handbook's p and a1..a5, and erf(-a) = -erf(a). A reciprocal, five multiply-adds
-// and an exponential: fewer instructions than erff in an epilogue that is bound by issue, and
-// an error far below the bfloat16 rounding of the result (2^-9 relative).
-__device__ __forceinline__ float gelu_erf(float x) {
-    const float a = fabsf(x) * 0.70710678118654752f;
-    const float t = __fdividef(1.f, fmaf(0.3275911f, a, 1.f));
-    float poly = fmaf(1.061405429f, t, -1.453152027f);
-    poly = fmaf(poly, t, 1.421413741f);
-    poly = fmaf(poly, t, -0.284496736f);
-    poly = fmaf(poly, t, 0.254829592f);
-    poly *= t;
-    const float e = fmaf(-poly, __expf(-a * a), 1.f);           // erf(a)
-    return 0.5f * x * (1.f + copysignf(e, x));
+// with the handbook's p and a1..a5, and erf(-a) = -erf(a). Per value a reciprocal, five
+// multiply-adds and an exponential, fewer instructions than erff in an epilogue that is bound
+// by issue, with an error far below the bfloat16 rounding of the result (2^-9 relative); the
+// multiply-adds run paired, two values per instruction.
+__device__ __forceinline__ void gelu_erf2(float& x0, float& x1) {
+    const uint64_t a = mul2(f2(fabsf(x0), fabsf(x1)), dup(0.70710678118654752f));
+    float d0, d1, a0, a1;
+    split2(fma2(dup(0.3275911f), a, dup(1.f)), d0, d1);
+    const uint64_t t = f2(__fdividef(1.f, d0), __fdividef(1.f, d1));
+    uint64_t poly = fma2(dup(1.061405429f), t, dup(-1.453152027f));
+    poly = fma2(poly, t, dup(1.421413741f));
+    poly = fma2(poly, t, dup(-0.284496736f));
+    poly = fma2(poly, t, dup(0.254829592f));
+    poly = mul2(poly, t);
+    split2(a, a0, a1);
+    float e0, e1;                                                // erf(a) = 1 - poly exp(-a^2)
+    split2(fma2(poly ^ kNeg2, f2(__expf(-a0 * a0), __expf(-a1 * a1)), dup(1.f)), e0, e1);
+    split2(mul2(mul2(dup(0.5f), f2(x0, x1)), add2(dup(1.f), f2(copysignf(e0, x0), copysignf(e1, x1)))), x0,
+           x1);
 }
 
 template <int EPI>
@@ -341,11 +375,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float2 bb = __bfloat1622float2(b2[i]);
-                        float x0 = __uint_as_float(v[2 * i]) + bb.x, x1 = __uint_as_float(v[2 * i + 1]) + bb.y;
-                        if (EPI == kEpiGelu) {
-                            x0 = gelu_erf(x0);
-                            x1 = gelu_erf(x1);
-                        }
+                        float x0, x1;
+                        split2(add2(f2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), f2(bb.x, bb.y)),
+                               x0, x1);
+                        if (EPI == kEpiGelu) gelu_erf2(x0, x1);
                         const __nv_bfloat162 r = __floats2bfloat162_rn(x0, x1);
                         ow[i] = *reinterpret_cast<const uint32_t*>(&r);
                     }

@@ -1,4 +1,4 @@
-"""The erf of the tcgen05 FFN kernel's GELU epilogue (csrc/pt_gemm_tc.cu, gelu_erf):
+"""The erf of the tcgen05 FFN kernel's GELU epilogue (csrc/pt_gemm_tc.cu, gelu_erf2):
 Abramowitz and Stegun, Handbook of Mathematical Functions, formula 7.1.26,
 erf(a) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-a^2), t = 1 / (1 + p a), a >= 0, with
 the handbook's error bound 1.5e-7. The coefficients below are read from the kernel's source, so a
@@ -15,7 +15,7 @@ SRC = Path(__file__).resolve().parents[1] / "paper_2509_23043_gb300" / "csrc" / 
 
 def _coefficients():
     body = SRC.read_text()
-    body = body[body.index("__device__ __forceinline__ float gelu_erf"):]
+    body = body[body.index("__device__ __forceinline__ void gelu_erf2"):]
     body = body[:body.index("\n}\n")]
     nums = [float(x) for x in re.findall(r"[-+]?\d+\.\d+(?:e[-+]?\d+)?", body)]
     # in order of appearance: 1/sqrt 2, p, then a5, a4, a3, a2, a1 (Horner order)
