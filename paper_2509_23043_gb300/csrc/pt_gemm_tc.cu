@@ -413,6 +413,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 
+// 2^x by the PTX ex2.approx instruction (an approximation; subnormal results flush to zero). The
+// attention tests bound its effect on the probabilities against the library path.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e8 = 1.4426950408889634f / 8.f;   // log2(e) / sqrt(64)
+
 // Causal attention probabilities of the scoring pass for sequences of at most 256 positions:
 // P[b][h][i][j] = softmax_j(Q_i . K_j / 8) over j <= i (bfloat16, zero for j > i), for every
 // configuration b and head h, Q and K read in place from the bfloat16 [B N][3d] QKV buffer
@@ -541,25 +550,44 @@ __global__ void __launch_bounds__(ATT_THREADS, 1)
             // the warp's last key (its last row's): tcgen05.ld is warp-collective, so every
             // lane runs the same chunks and masks its own keys
             const int jwarp = min(mt * BM + 32 * q + 31, N - 1);
-            // pass 1: running maximum and sum of exp over the row, 32 columns at a time
+            // pass 1: running maximum (of the raw scores: the scale 1/8 is positive) and sum of
+            // exp over the row, 32 columns at a time; exp((s - m) / 8) = 2^((s - m) kLog2e8), one
+            // multiply-add and one ex2 per score (the base-2 softmax of FlashAttention-2, Dao
+            // 2023). Chunks wholly inside the causal range take no per-key mask.
             float mx = -INFINITY, sum = 0.f;
 #pragma unroll 1
             for (int ch = 0; ch * 32 <= jwarp; ++ch) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(32 * ch), v);
+                const bool whole = 32 * ch + 31 <= jmax;
                 float cm = -INFINITY;
+                if (whole) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (32 * ch + c <= jmax) cm = fmaxf(cm, __uint_as_float(v[c]) * 0.125f);
+                    for (int c = 0; c < 32; ++c) cm = fmaxf(cm, __uint_as_float(v[c]));
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (32 * ch + c <= jmax) cm = fmaxf(cm, __uint_as_float(v[c]));
+                }
                 const float nm = fmaxf(mx, cm);
-                float cs = 0.f;
+                const float off = -nm * kLog2e8;
+                float cs0 = 0.f, cs1 = 0.f;
+                if (whole) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (32 * ch + c <= jmax) cs += __expf(__uint_as_float(v[c]) * 0.125f - nm);
-                sum = sum * __expf(mx - nm) + cs;
+                    for (int c = 0; c < 32; c += 2) {
+                        cs0 += ex2_approx(fmaf(__uint_as_float(v[c]), kLog2e8, off));
+                        cs1 += ex2_approx(fmaf(__uint_as_float(v[c + 1]), kLog2e8, off));
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (32 * ch + c <= jmax) cs0 += ex2_approx(fmaf(__uint_as_float(v[c]), kLog2e8, off));
+                }
+                sum = sum * ex2_approx((mx - nm) * kLog2e8) + (cs0 + cs1);
                 mx = nm;
             }
             const float inv = 1.f / sum;
+            const float off = -mx * kLog2e8;
             // pass 2: the probabilities, 32 keys (64 bytes) per row at a time through the
             // staging buffer; four lanes write a row's 64 bytes; rows and keys past N are not
             // written, keys j > i are zeros
@@ -569,15 +597,19 @@ __global__ void __launch_bounds__(ATT_THREADS, 1)
             for (int ch = 0; ch < nch; ++ch) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(32 * ch), v);
+                const bool whole = 32 * ch + 31 <= jmax;
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
                     uint32_t w[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int c = 8 * k4 + 2 * e;
-                        const float p0 = 32 * ch + c <= jmax ? __expf(__uint_as_float(v[c]) * 0.125f - mx) * inv : 0.f;
-                        const float p1 =
-                            32 * ch + c + 1 <= jmax ? __expf(__uint_as_float(v[c + 1]) * 0.125f - mx) * inv : 0.f;
+                        float p0 = ex2_approx(fmaf(__uint_as_float(v[c]), kLog2e8, off)) * inv;
+                        float p1 = ex2_approx(fmaf(__uint_as_float(v[c + 1]), kLog2e8, off)) * inv;
+                        if (!whole) {
+                            p0 = 32 * ch + c <= jmax ? p0 : 0.f;
+                            p1 = 32 * ch + c + 1 <= jmax ? p1 : 0.f;
+                        }
                         const __nv_bfloat162 r2 = __floats2bfloat162_rn(p0, p1);
                         w[e] = *reinterpret_cast<const uint32_t*>(&r2);
                     }
