@@ -578,14 +578,14 @@ void free_act(Act& a) {
     a = Act{};
 }
 
-// the probabilities of one layer's attention (B H N^2 entries of 2 bytes, and 4 more for the
-// FP32 scores of the unfused path) are kept when they fit this budget; else the streaming
-// attention kernel runs
+// the unfused tensor-core path keeps one layer's FP32 scores and bfloat16 probabilities (B H N^2
+// entries of 6 bytes) when they fit this budget; else the streaming attention kernel runs (the
+// fused kernel keeps neither)
 constexpr size_t kAttScratchBytes = size_t(2) << 30;
 
-// the scores and the causal softmax in one tcgen05 kernel (no FP32 score buffer)
+// the scores, the causal softmax and P V in one tcgen05 kernel (no score or probability buffer)
 bool attn_fused(const pt_former* m) {
-    return m->cfg.attn_mode == 0 && m->tc_ready && attn_softmax_tc_supported(m->cfg.n_spins, m->cfg.d_model);
+    return m->cfg.attn_mode == 0 && m->tc_ready && attn_tc_supported(m->cfg.n_spins, m->cfg.d_model);
 }
 
 pt_status ensure_att(pt_former* m, Act& a, int B) {
@@ -598,8 +598,10 @@ pt_status ensure_att(pt_former* m, Act& a, int B) {
     a.att_elems = 0;
     const size_t rows = (size_t)B * N;
     FCK(cudaMalloc(&a.qkv16, rows * 3 * d * 2));
-    if (!attn_fused(m)) FCK(cudaMalloc(&a.S, elems * 4));
-    FCK(cudaMalloc(&a.P, elems * 2));
+    if (!attn_fused(m)) {
+        FCK(cudaMalloc(&a.S, elems * 4));
+        FCK(cudaMalloc(&a.P, elems * 2));
+    }
     a.att_elems = elems;
     return PT_OK;
 }
@@ -741,10 +743,12 @@ pt_status gemm_batched(pt_former* m, cublasOperation_t ta, const __nv_bfloat16* 
 
 pt_status attention_scores_softmax(pt_former* m, Act& x, int B);
 
-// Causal attention of the scoring pass on the tensor cores, per head, batched over the B
-// configurations, reading the heads' columns of the bfloat16 [B N][3d] query/key/value in
-// place: S = Q K^T / 8 (row-major S [N][N] is the column-major S^T = K Q^T), the causal
-// softmax, then O = P V (O^T = V^T P^T, written into the head's columns of the [B N][d] output).
+// Causal attention of the scoring pass on the tensor cores, reading the heads' columns of the
+// bfloat16 [B N][3d] query/key/value in place and writing the head's columns of the [B N][d]
+// output. attn_mode 0 with N <= 256: one tcgen05 kernel (scores, softmax and P V on the SM).
+// Otherwise per head, batched over the B configurations on cuBLASLt: S = Q K^T / 8 (row-major
+// S [N][N] is the column-major S^T = K Q^T), the causal softmax kernel, then O = P V
+// (O^T = V^T P^T).
 pt_status attention_tc(pt_former* m, Act& x, int B) {
     const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
     const int ld = 3 * d;
@@ -752,12 +756,12 @@ pt_status attention_tc(pt_former* m, Act& x, int B) {
     const long long nn = (long long)N * N;
     pt_status s = PT_OK;
     if (attn_fused(m)) {
-        // the scores and the causal softmax in one tcgen05 kernel, P written directly
-        FCK(attn_softmax_tc(x.qkv16, x.P, B, N, H, d, m->num_sms, m->d_err, m->exec));
-    } else {
-        s = attention_scores_softmax(m, x, B);
-        if (s != PT_OK) return s;
+        // scores, causal softmax and P V in one tcgen05 kernel, O written directly
+        FCK(attn_tc(x.qkv16, x.o, B, N, H, d, m->num_sms, m->d_err, m->exec));
+        return PT_OK;
     }
+    s = attention_scores_softmax(m, x, B);
+    if (s != PT_OK) return s;
     for (int hd = 0; hd < H && s == PT_OK; ++hd)
         s = gemm_batched(m, CUBLAS_OP_N, x.qkv16 + 2 * d + hd * kDH, ld, cfg_stride, x.P + hd * nn, N, H * nn,
                          x.o + hd * kDH, CUDA_R_16BF, d, (long long)N * d, kDH, N, N, B, 1.f);
@@ -1029,7 +1033,7 @@ pt_status pt_former_score(pt_former* m, int32_t B, const int8_t* spins, const fl
     }
     FCK(cudaGetLastError());
     // the probabilities (2 bytes per entry), and the FP32 scores unless fused (4 more)
-    const bool tc = m->cfg.attn_mode != 1 && (size_t)B * H * N * N * (attn_fused(m) ? 2 : 6) <= kAttScratchBytes;
+    const bool tc = m->cfg.attn_mode != 1 && (attn_fused(m) || (size_t)B * H * N * N * 6 <= kAttScratchBytes);
     if (tc) {
         s = ensure_att(m, x, B);
         if (s != PT_OK) return s;

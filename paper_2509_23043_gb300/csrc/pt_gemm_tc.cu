@@ -422,54 +422,101 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 constexpr float kLog2e8 = 1.4426950408889634f / 8.f;   // log2(e) / sqrt(64)
 
-// Causal attention probabilities of the scoring pass for sequences of at most 256 positions:
-// P[b][h][i][j] = softmax_j(Q_i . K_j / 8) over j <= i (bfloat16, zero for j > i), for every
-// configuration b and head h, Q and K read in place from the bfloat16 [B N][3d] QKV buffer
-// (head h at columns 64 h and d + 64 h; head dimension 64). One tile per (b, h, block of 128
-// queries): S = Q K^T for the 128 queries against all N keys in one tcgen05.mma group (K 64,
-// N 256: the whole score row is in TMEM), so the scores never leave the SM. The epilogue is
-// two groups of four warps, one per TMEM accumulator, taking alternate tiles; a thread owns a
-// row: one pass over its 256 columns keeps the running maximum and sum, a second writes
-// exp(s - max) / sum (fast exponential: the probabilities are stored in bfloat16). Keys past
-// the configuration's N rows (the next configuration's, or zero fill past the buffer) fall
-// beyond every query's causal range.
+// Causal attention of the scoring pass for sequences of at most 256 positions, all of it on
+// the SM: O[b N + i][64 h ..] = sum_{j <= i} softmax_j(Q_i . K_j / 8) V_j for every configuration
+// b and head h, Q, K and V read in place from the bfloat16 [B N][3d] QKV buffer (head h at
+// columns 64 h, d + 64 h and 2d + 64 h; head dimension 64), O bfloat16 [B N][d]. One tile per
+// (b, h, block of 128 queries):
+//   - warp 0, one thread: TMA loads the 128 query rows and the configuration's 256 key and 256
+//     value rows (rows past its N belong to the next configuration or are zero fill past the
+//     buffer: they fall outside every query's causal range) into one of two stages;
+//   - warp 1, one thread: S = Q K^T (one tcgen05.mma group, K 64, N 256) into the tile's TMEM
+//     accumulator, so the whole score row of each query is in TMEM; later O = P V (M 128,
+//     N 64, K the keys rounded up to 16) into the first 64 columns of the same accumulator,
+//     with P from shared memory (K-major) and V from the stage as loaded (rows of 64 values:
+//     MN-major, the instruction's transposed-B form). S of the next tile is issued before P V
+//     of this one, so the products of one tile overlap the softmax of the other;
+//   - warps 2..9: two groups of four, one per accumulator, taking alternate tiles; a thread owns
+//     a row. Pass 1 reads its 256 columns 32 at a time and keeps the running maximum and sum of
+//     exp; pass 2 writes exp(s - max) (unnormalised, at most 1) in bfloat16 into the 64 KB P
+//     buffer in the 128-byte-swizzled K-major layout the tensor core reads (one buffer, used by
+//     the tiles in turn); then O / sum is read from TMEM and written out.
+// Each exponential is 2^((s - max) log2(e) / 8): one multiply-add and one ex2 per score (the
+// base-2 softmax of FlashAttention-2, Dao 2023). Every wait is bounded as in the products above.
 constexpr int ATT_EPI_WARPS = 8;
 constexpr int ATT_THREADS = 64 + 32 * ATT_EPI_WARPS;
-constexpr size_t ATT_SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + BAR_BYTES + (size_t)ATT_EPI_WARPS * STG_BYTES;
+constexpr int ATT_STAGES = 2;
+constexpr int ATT_Q_BYTES = BM * 64 * 2;                      // 16 KB
+constexpr int ATT_KV_BYTES = BN * 64 * 2;                     // 32 KB each
+constexpr int ATT_STAGE_BYTES = ATT_Q_BYTES + 2 * ATT_KV_BYTES;
+constexpr int ATT_P_BYTES = BM * BN * 2;                      // 64 KB: four 16 KB chunks of 64 keys
+// barriers: full, empty, sfull, ofull, tempty (one per stage or accumulator), pfull, pempty, done;
+// then the TMEM base address and the abort flag
+constexpr int ATT_NBAR = 5 * 2 + 3;
+constexpr int ATT_BAR_BYTES = 8 * ATT_NBAR + 8;
+constexpr size_t ATT_SMEM_BYTES = 1024 + (size_t)ATT_STAGES * ATT_STAGE_BYTES + ATT_P_BYTES + ATT_BAR_BYTES;
+static_assert(ATT_SMEM_BYTES <= 232448, "over the opt-in shared memory of a block");
+
+// Instruction descriptor of P V: FP32 accumulator, bfloat16 A and B, A K-major, B MN-major
+// (bit 16), N = 64, M = 128.
+constexpr uint32_t IDESC_PV = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(64 >> 3) << 17) |
+                              ((uint32_t)(BM >> 4) << 24);
+
+// Descriptor of an MN-major, 128-byte-swizzled bfloat16 tile of one 64-element atom along MN
+// (rows of 128 bytes, one per K index, as TMA writes them): 8-row K groups 1024 bytes apart.
+// The stride between MN atoms is not used at N = 64; both byte offsets are set to 1024.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_f16_pv(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC_PV), "r"(accumulate)
+        : "memory");
+}
 
 __global__ void __launch_bounds__(ATT_THREADS, 1)
-    attn_softmax_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmK,
-                        __nv_bfloat16* __restrict__ P, int B, int N, int H, int d, int* __restrict__ err) {
+    attn_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmK,
+                   __nv_bfloat16* __restrict__ O, int B, int N, int H, int d, int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t ring = (raw + 1023u) & ~1023u;
     uint8_t* ring_ptr = smem_raw + (ring - raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring_ptr + (size_t)STAGES * STAGE_BYTES);
+    const uint32_t pbuf = ring + (uint32_t)ATT_STAGES * ATT_STAGE_BYTES;          // 1024-aligned
+    uint8_t* pbuf_ptr = ring_ptr + (size_t)ATT_STAGES * ATT_STAGE_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(pbuf_ptr + ATT_P_BYTES);
     const uint32_t bar0 = smem_u32(bars);
     auto full = [&](int s) { return bar0 + 8u * s; };
-    auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto tfull = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
-    auto tempty = [&](int a) { return bar0 + 8u * (2 * STAGES + NUM_ACC + a); };
-    const uint32_t done = bar0 + 8u * (2 * STAGES + 2 * NUM_ACC);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 * NUM_ACC + 1);
+    auto empty = [&](int s) { return bar0 + 8u * (2 + s); };
+    auto sfull = [&](int a) { return bar0 + 8u * (4 + a); };
+    auto ofull = [&](int a) { return bar0 + 8u * (6 + a); };
+    auto tempty = [&](int a) { return bar0 + 8u * (8 + a); };
+    const uint32_t pfull = bar0 + 8u * 10, pempty = bar0 + 8u * 11, done = bar0 + 8u * 12;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + ATT_NBAR);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    uint8_t* staging = ring_ptr + (size_t)STAGES * STAGE_BYTES + BAR_BYTES;
-    auto sA = [&](int s) { return ring + (uint32_t)s * STAGE_BYTES; };
-    auto sB = [&](int s) { return ring + (uint32_t)s * STAGE_BYTES + A_BYTES; };
+    auto sQ = [&](int s) { return ring + (uint32_t)s * ATT_STAGE_BYTES; };
+    auto sK = [&](int s) { return ring + (uint32_t)s * ATT_STAGE_BYTES + ATT_Q_BYTES; };
+    auto sV = [&](int s) { return ring + (uint32_t)s * ATT_STAGE_BYTES + ATT_Q_BYTES + ATT_KV_BYTES; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m_tiles = (N + BM - 1) / BM;
     const int tiles = B * H * m_tiles;
+    const int kp16 = (N + 15) >> 4;                   // K16 steps of P V
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < 2; ++s) {
             bar_init(full(s), 1);
             bar_init(empty(s), 1);
+            bar_init(sfull(s), 1);
+            bar_init(ofull(s), 1);
+            bar_init(tempty(s), 32 * ATT_EPI_WARPS / 2);   // one group per accumulator
         }
-        for (int a = 0; a < NUM_ACC; ++a) {
-            bar_init(tfull(a), 1);
-            bar_init(tempty(a), 32 * ATT_EPI_WARPS / NUM_ACC);   // one group per accumulator
-        }
+        bar_init(pfull, 32 * ATT_EPI_WARPS / 2);           // the writing group
+        bar_init(pempty, 1);
         bar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -486,44 +533,69 @@ __global__ void __launch_bounds__(ATT_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0, armed = 0, armed_par = 0;
-            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            uint32_t armed = 0, armed_par = 0;
+            for (int u = 0;; ++u) {
+                const int t = blockIdx.x + u * gridDim.x;
+                if (t >= tiles) break;
+                const int s = u & 1;
+                const uint32_t ph = (uint32_t)(u >> 1) & 1u;
                 const int bh = t / m_tiles, mt = t - bh * m_tiles;
                 const int b = bh / H, h = bh - b * H;
-                if (!bar_wait(empty(stage), phase ^ 1u, abort_flag, err, 11)) {
-                    for (int s = 0; s < STAGES; ++s)
-                        if (armed >> s & 1u) {
+                if (!bar_wait(empty(s), ph ^ 1u, abort_flag, err, 21)) {
+                    for (int k = 0; k < 2; ++k)
+                        if (armed >> k & 1u) {
                             const unsigned long long t0 = now_ns();
-                            while (!bar_try(full(s), armed_par >> s & 1u) && now_ns() - t0 < WAIT_NS) {}
+                            while (!bar_try(full(k), armed_par >> k & 1u) && now_ns() - t0 < WAIT_NS) {}
                         }
                     break;
                 }
-                bar_expect_tx(full(stage), STAGE_BYTES);
-                tma_load_2d(sA(stage), &tmQ, h * 64, b * N + mt * BM, full(stage));   // 128 queries
-                tma_load_2d(sB(stage), &tmK, d + h * 64, b * N, full(stage));         // 256 keys
-                armed |= 1u << stage;
-                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                bar_expect_tx(full(s), ATT_STAGE_BYTES);
+                tma_load_2d(sQ(s), &tmQ, h * 64, b * N + mt * BM, full(s));          // 128 queries
+                tma_load_2d(sK(s), &tmK, d + h * 64, b * N, full(s));                // 256 keys
+                tma_load_2d(sV(s), &tmK, 2 * d + h * 64, b * N, full(s));            // 256 values
+                armed |= 1u << s;
+                armed_par = (armed_par & ~(1u << s)) | (ph << s);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int stage = 0, acc = 0;
-            uint32_t phase = 0, acc_phase = 0;
-            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-                if (!bar_wait(tempty(acc), acc_phase ^ 1u, abort_flag, err, 12)) break;
+            int n = 0;                                     // this block's tiles
+            while (blockIdx.x + n * gridDim.x < tiles) ++n;
+            // S of tile u into accumulator u & 1, once the tile's stage is loaded and the
+            // accumulator's previous tile has been read out
+            auto issue_s = [&](int u) -> bool {
+                const int a = u & 1;
+                const uint32_t ph = (uint32_t)(u >> 1) & 1u;
+                if (!bar_wait(tempty(a), ph ^ 1u, abort_flag, err, 22)) return false;
                 tc_fence_after();
-                if (!bar_wait(full(stage), phase, abort_flag, err, 13)) break;
+                if (!bar_wait(full(a), ph, abort_flag, err, 23)) return false;
                 tc_fence_after();
-                const uint32_t dcol = tmem + (uint32_t)(acc * BN);
-                const uint64_t ad = sw128_desc(sA(stage)), bd = sw128_desc(sB(stage));
+                const uint64_t qd = sw128_desc(sQ(a)), kd = sw128_desc(sK(a));
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) mma_f16(dcol, ad + 2u * k, bd + 2u * k, k != 0 ? 1u : 0u);
-                mma_commit(empty(stage));
-                mma_commit(tfull(acc));
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                if (++acc == NUM_ACC) { acc = 0; acc_phase ^= 1u; }
+                for (int k = 0; k < 4; ++k) mma_f16(tmem + (uint32_t)(a * BN), qd + 2u * k, kd + 2u * k, k != 0 ? 1u : 0u);
+                mma_commit(sfull(a));
+                return true;
+            };
+            // P V of tile u once its P is in the buffer; then the stage, the P buffer and the
+            // result are released
+            auto issue_pv = [&](int u) -> bool {
+                const int a = u & 1;
+                if (!bar_wait(pfull, (uint32_t)u & 1u, abort_flag, err, 24)) return false;
+                tc_fence_after();
+                for (int k = 0; k < kp16; ++k) {
+                    const uint64_t pd = sw128_desc(pbuf + (uint32_t)(k >> 2) * (BM * 128)) + 2u * (uint32_t)(k & 3);
+                    const uint64_t vd = sw128_mn_desc(sV(a) + (uint32_t)k * 2048u);
+                    mma_f16_pv(tmem + (uint32_t)(a * BN), pd, vd, k != 0 ? 1u : 0u);
+                }
+                mma_commit(empty(a));
+                mma_commit(pempty);
+                mma_commit(ofull(a));
+                return true;
+            };
+            bool ok = n == 0 || issue_s(0);
+            for (int u = 0; ok && u < n; ++u) {
+                if (u + 1 < n) ok = issue_s(u + 1);
+                if (ok) ok = issue_pv(u);
             }
             mma_commit(done);
             const unsigned long long t0 = now_ns();
@@ -532,28 +604,26 @@ __global__ void __launch_bounds__(ATT_THREADS, 1)
     } else {
         const int q = warp & 3;                   // TMEM lane quarter: rows 32 q .. 32 q + 31
         const int grp = (warp - 2) >> 2;          // accumulator (and tile parity) of this group
-        uint8_t* stg = staging + (size_t)(warp - 2) * STG_BYTES;
-        const int rr = lane >> 2, part = lane & 3;
         const int row = 32 * q + lane;            // the thread's row of the tile
         const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(grp * BN);
-        uint32_t ph = 0;
-        for (int t = blockIdx.x + grp * gridDim.x; t < tiles; t += NUM_ACC * gridDim.x) {
-            // a group's four warps leave together only through this wait: every one of them
+        uint8_t* prow = pbuf_ptr + (size_t)row * 128;
+        const int nchp = (kp16 * 16 + 31) / 32;   // chunks of 32 keys that P V reads
+        for (int u = grp;; u += 2) {
+            const int t = blockIdx.x + u * gridDim.x;
+            if (t >= tiles) break;
+            const uint32_t ph = (uint32_t)(u >> 1) & 1u;
+            // a group's four warps leave together only through these waits: every one of them
             // sees the same phase complete, or every one runs out of time or sees the abort
-            const bool ok = bar_wait(tfull(grp), ph, abort_flag, err, 14);
-            if (!__all_sync(0xFFFFFFFFu, ok)) break;
-            ph ^= 1u;
+            if (!__all_sync(0xFFFFFFFFu, bar_wait(sfull(grp), ph, abort_flag, err, 25))) break;
             tc_fence_after();
             const int bh = t / m_tiles, mt = t - bh * m_tiles;
+            const int b = bh / H, h = bh - b * H;
             const int i = mt * BM + row;                   // query position
             const int jmax = min(i, N - 1);                // keys 0 .. jmax
             // the warp's last key (its last row's): tcgen05.ld is warp-collective, so every
             // lane runs the same chunks and masks its own keys
             const int jwarp = min(mt * BM + 32 * q + 31, N - 1);
-            // pass 1: running maximum (of the raw scores: the scale 1/8 is positive) and sum of
-            // exp over the row, 32 columns at a time; exp((s - m) / 8) = 2^((s - m) kLog2e8), one
-            // multiply-add and one ex2 per score (the base-2 softmax of FlashAttention-2, Dao
-            // 2023). Chunks wholly inside the causal range take no per-key mask.
+            // pass 1: running maximum (of the raw scores: the scale 1/8 is positive) and sum
             float mx = -INFINITY, sum = 0.f;
 #pragma unroll 1
             for (int ch = 0; ch * 32 <= jwarp; ++ch) {
@@ -586,46 +656,64 @@ __global__ void __launch_bounds__(ATT_THREADS, 1)
                 sum = sum * ex2_approx((mx - nm) * kLog2e8) + (cs0 + cs1);
                 mx = nm;
             }
-            const float inv = 1.f / sum;
             const float off = -mx * kLog2e8;
-            // pass 2: the probabilities, 32 keys (64 bytes) per row at a time through the
-            // staging buffer; four lanes write a row's 64 bytes; rows and keys past N are not
-            // written, keys j > i are zeros
-            const size_t prow0 = ((size_t)bh * N + (size_t)mt * BM + 32 * q) * N;
-            const int nch = (N + 31) / 32;
+            // the P buffer is free once P V of the previous tile has read it
+            if (u > 0 && !__all_sync(0xFFFFFFFFu, bar_wait(pempty, (uint32_t)(u - 1) & 1u, abort_flag, err, 26)))
+                break;
+            // pass 2: exp(s - max) in bfloat16 into the P buffer (row `row`, keys in chunks of 64:
+            // 16-byte unit k of a 128-byte row stored at unit k ^ (row & 7)); zeros past jmax
 #pragma unroll 1
-            for (int ch = 0; ch < nch; ++ch) {
+            for (int ch = 0; ch < nchp; ++ch) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(32 * ch), v);
                 const bool whole = 32 * ch + 31 <= jmax;
+                uint32_t w[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = 2 * e;
+                    float p0 = ex2_approx(fmaf(__uint_as_float(v[c]), kLog2e8, off));
+                    float p1 = ex2_approx(fmaf(__uint_as_float(v[c + 1]), kLog2e8, off));
+                    if (!whole) {
+                        p0 = 32 * ch + c <= jmax ? p0 : 0.f;
+                        p1 = 32 * ch + c + 1 <= jmax ? p1 : 0.f;
+                    }
+                    const __nv_bfloat162 r2 = __floats2bfloat162_rn(p0, p1);
+                    w[e] = *reinterpret_cast<const uint32_t*>(&r2);
+                }
+                uint8_t* cbase = prow + (size_t)(ch >> 1) * (BM * 128);
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = 8 * k4 + 2 * e;
-                        float p0 = ex2_approx(fmaf(__uint_as_float(v[c]), kLog2e8, off)) * inv;
-                        float p1 = ex2_approx(fmaf(__uint_as_float(v[c + 1]), kLog2e8, off)) * inv;
-                        if (!whole) {
-                            p0 = 32 * ch + c <= jmax ? p0 : 0.f;
-                            p1 = 32 * ch + c + 1 <= jmax ? p1 : 0.f;
-                        }
-                        const __nv_bfloat162 r2 = __floats2bfloat162_rn(p0, p1);
-                        w[e] = *reinterpret_cast<const uint32_t*>(&r2);
-                    }
-                    *reinterpret_cast<uint4*>(stg + lane * STG_PITCH + 16 * k4) = make_uint4(w[0], w[1], w[2], w[3]);
+                    const int unit = ((ch & 1) * 4 + k4) ^ (row & 7);
+                    *reinterpret_cast<uint4*>(cbase + 16 * unit) =
+                        make_uint4(w[4 * k4], w[4 * k4 + 1], w[4 * k4 + 2], w[4 * k4 + 3]);
                 }
-                __syncwarp();
-                const int c0 = 32 * ch;
+            }
+            // the generic-proxy stores become visible to the tensor core, and the score reads
+            // are complete before P V overwrites the accumulator
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            bar_arrive(pfull);
+            if (!__all_sync(0xFFFFFFFFu, bar_wait(ofull(grp), ph, abort_flag, err, 27))) break;
+            tc_fence_after();
+            const float inv = 1.f / sum;
+            __nv_bfloat16* orow = O + ((size_t)b * N + i) * d + h * 64;
+#pragma unroll 1
+            for (int hc = 0; hc < 2; ++hc) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(32 * hc), v);
+                uint32_t w[16];
 #pragma unroll
-                for (int it = 0; it < 4; ++it) {
-                    const int r = rr + 8 * it;
-                    const int qi = mt * BM + 32 * q + r;
-                    if (qi < N && c0 + 8 * part < N)
-                        *reinterpret_cast<uint4*>(P + prow0 + (size_t)r * N + c0 + 8 * part) =
-                            *reinterpret_cast<const uint4*>(stg + r * STG_PITCH + 16 * part);
+                for (int e = 0; e < 16; ++e) {
+                    const __nv_bfloat162 r2 = __floats2bfloat162_rn(__uint_as_float(v[2 * e]) * inv,
+                                                                    __uint_as_float(v[2 * e + 1]) * inv);
+                    w[e] = *reinterpret_cast<const uint32_t*>(&r2);
                 }
-                __syncwarp();
+                if (i < N) {
+                    uint4* dst = reinterpret_cast<uint4*>(orow + 32 * hc);
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4)
+                        dst[k4] = make_uint4(w[4 * k4], w[4 * k4 + 1], w[4 * k4 + 2], w[4 * k4 + 3]);
+                }
             }
             tc_fence_before();
             bar_arrive(tempty(grp));
@@ -673,7 +761,7 @@ cudaError_t gemm_tc_setup() {
     cudaError_t e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiGelu>, at, (int)tcg::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiBias>, at, (int)tcg::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::gemm_tc_kernel<kEpiResid>, at, (int)tcg::SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::attn_softmax_kernel, at, (int)tcg::ATT_SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tcg::attn_tc_kernel, at, (int)tcg::ATT_SMEM_BYTES);
     return e;
 }
 
@@ -707,22 +795,22 @@ cudaError_t gemm_tc(int epi, const __nv_bfloat16* A, const __nv_bfloat16* Wt, co
     return cudaGetLastError();
 }
 
-bool attn_softmax_tc_supported(int N, int d) {
+bool attn_tc_supported(int N, int d) {
     return N >= 1 && N <= tcg::BN && N % 8 == 0 && d % 64 == 0;
 }
 
-cudaError_t attn_softmax_tc(const __nv_bfloat16* qkv, __nv_bfloat16* P, int B, int N, int H, int d, int num_sms,
-                            int* d_err, cudaStream_t stream) {
-    if (!g_encode || !attn_softmax_tc_supported(N, d) || B < 1) return cudaErrorInvalidValue;
-    if (((uintptr_t)qkv | (uintptr_t)P) & 15u) return cudaErrorMisalignedAddress;
-    // two maps over the same buffer: query tiles of 64 columns by 128 rows, key tiles of 64
-    // columns by 256 rows
+cudaError_t attn_tc(const __nv_bfloat16* qkv, __nv_bfloat16* O, int B, int N, int H, int d, int num_sms,
+                    int* d_err, cudaStream_t stream) {
+    if (!g_encode || !attn_tc_supported(N, d) || B < 1 || H * 64 != d) return cudaErrorInvalidValue;
+    if (((uintptr_t)qkv | (uintptr_t)O) & 15u) return cudaErrorMisalignedAddress;
+    // two maps over the same buffer: query tiles of 64 columns by 128 rows; key and value
+    // tiles of 64 columns by 256 rows
     CUtensorMap tq, tk;
     if (!encode_2d(&tq, qkv, (uint64_t)3 * d, (uint64_t)B * N, tcg::BK, tcg::BM) ||
         !encode_2d(&tk, qkv, (uint64_t)3 * d, (uint64_t)B * N, tcg::BK, tcg::BN))
         return cudaErrorInvalidValue;
     const int tiles = B * H * ((N + tcg::BM - 1) / tcg::BM);
     const int grid = tiles < num_sms ? tiles : num_sms;
-    tcg::attn_softmax_kernel<<<grid, tcg::ATT_THREADS, tcg::ATT_SMEM_BYTES, stream>>>(tq, tk, P, B, N, H, d, d_err);
+    tcg::attn_tc_kernel<<<grid, tcg::ATT_THREADS, tcg::ATT_SMEM_BYTES, stream>>>(tq, tk, O, B, N, H, d, d_err);
     return cudaGetLastError();
 }

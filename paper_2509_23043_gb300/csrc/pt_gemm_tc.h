@@ -21,13 +21,14 @@ bool gemm_tc_supported(int N, int K);
 cudaError_t gemm_tc(int epi, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const void* bias, void* C,
                     int M, int N, int K, int num_sms, int* d_err, cudaStream_t stream);
 
-// Whether the fused causal-softmax kernel takes sequences of N positions and model width d:
+// Whether the fused attention kernel takes sequences of N positions and model width d:
 // N <= 256 (one key tile), N a multiple of 8, d a multiple of 64 (head dimension 64).
-bool attn_softmax_tc_supported(int N, int d);
+bool attn_tc_supported(int N, int d);
 
-// P[b][h][i][j] = softmax over j <= i of Q_i . K_j / 8 (0 for j > i), bfloat16 [B][H][N][N],
+// O[b N + i][64 h + c] = sum over j <= i of softmax_j(Q_i . K_j / 8) V_j[c], bfloat16 [B N][d],
 // from the bfloat16 query/key/value buffer qkv [B N][3d] (head h: queries at columns 64 h,
-// keys at d + 64 h). One persistent block per SM; a wait that runs out records a nonzero code
-// in *d_err and the kernel returns.
-cudaError_t attn_softmax_tc(const __nv_bfloat16* qkv, __nv_bfloat16* P, int B, int N, int H, int d, int num_sms,
-                            int* d_err, cudaStream_t stream);
+// keys at d + 64 h, values at 2d + 64 h; H = d / 64). Scores, softmax and P V stay on the SM.
+// One persistent block per SM; a wait that runs out records a nonzero code in *d_err and the
+// kernel returns.
+cudaError_t attn_tc(const __nv_bfloat16* qkv, __nv_bfloat16* O, int B, int N, int H, int d, int num_sms,
+                    int* d_err, cudaStream_t stream);

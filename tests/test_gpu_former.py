@@ -76,13 +76,15 @@ def test_tcgen05_projections_match_library_products(N, B):
     assert np.all(np.abs(lg0 - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
 
 
-@pytest.mark.parametrize("N,B", [(8, 5), (64, 3), (136, 2), (200, 4), (256, 2)])
+@pytest.mark.parametrize("N,B", [(8, 5), (64, 3), (136, 2), (200, 4), (256, 2), (200, 160)])
 def test_fused_attention_matches_library_attention(N, B):
-    # attn_mode 0: the scores and the causal softmax in one tcgen05 kernel (one tile per 128
-    # queries, the whole score row in TMEM) against attn_mode 2 (cuBLASLt scores in FP32 and
-    # the softmax kernel): the same bfloat16 queries and keys and FP32 scores, so the
-    # probabilities differ only by the order of the exponential sums; N = 8 .. 256 covers one
-    # query tile, a ragged second tile (136 = 128 + 8) and the largest key tile; the logits
+    # attn_mode 0: scores, causal softmax and P V in one tcgen05 kernel (one tile per 128
+    # queries, the whole score row in TMEM, P through shared memory) against attn_mode 2
+    # (cuBLASLt scores in FP32, the softmax kernel, cuBLASLt P V): the same bfloat16 queries,
+    # keys and values and FP32 scores, the probabilities rounded to bfloat16 on both sides (the
+    # fused kernel before normalising); N = 8 .. 256 covers one query tile, a ragged second
+    # tile (136 = 128 + 8) and the largest key tile, and B = 160 at N = 200 gives every block
+    # about eight tiles (both stages, both accumulators and the P buffer in turn); the logits
     # also agree with the float64 oracle
     from paper_2509_23043_gb300.former import Former
     shp = I.FormerShape(n_spins=N)
@@ -101,8 +103,12 @@ def test_fused_attention_matches_library_attention(N, B):
         assert np.isfinite(lg0).all()
         d = np.abs(lg0 - lg1)
         print("fused attention vs library attention: max logit difference", d.max())
-        assert d.max() < 0.01, d.max()
+        # each side rounds the probabilities to bfloat16 (2^-9 relative) at its own point and
+        # sums in its own order: differences of order 1e-3, tails near 1e-2 over 64 000
+        # logits; the bound of the projections comparison above
+        assert d.max() < 0.02, d.max()
     lg_o, _ = F.score(W, shp, Xh, bh.astype(np.float64))
+    print("fused attention vs the float64 oracle: max logit error", np.abs(lg0 - lg_o).max())
     assert np.all(np.abs(lg0 - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
 
 
