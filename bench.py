@@ -1056,12 +1056,13 @@ def isingformer_workload(stream, B=1024, reps=5):
                                     "frac": gemm / (ms * 1e-3) / 1e12 / peak_tf if peak_tf else None,
                                     "traffic": None, "kernel": "the scoring pass (this library's "
                                     "tcgen05 kernels for the first FFN map with bias and GELU "
-                                    "fused and for the attention scores with the causal softmax "
-                                    "fused; the other projections and O = P V on cuBLASLt; norms, "
+                                    "fused and for the whole causal attention: scores, softmax "
+                                    "and P V; the other projections on cuBLASLt; norms, "
                                     "embedding and head in this library's kernels)",
                                     "flops_per_call": gemm, "attention_flops_per_call": attn,
-                                    "note": "matrix-product FLOPs over the whole pass's time; the "
-                                            "attention's FP32 FLOPs are reported beside it"}},
+                                    "note": "projection FLOPs over the whole pass's time; the "
+                                            "attention's causal products (Q K^T and P V below "
+                                            "the diagonal) are reported beside them"}},
              "sample": {"configs_per_s": B / (ms_s * 1e-3), "ms_per_call": ms_s, "prefix": npre,
                         "gpu_launches_per_call": "one CUDA graph of N steps",
                         f"configs_per_s_B{8 * B}": Bl / (ms_sl * 1e-3), f"ms_per_call_B{8 * B}": ms_sl,

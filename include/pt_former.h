@@ -41,13 +41,13 @@ typedef struct pt_former pt_former;
 /* Model shape (the paper's spin-glass and factorization model: d_model 256, 4 heads, 5
  * layers, FFN 1024). n_spins N >= 1 is the sequence length; d_model a multiple of 64 and of
  * n_heads with d_model / n_heads = 64; d_ff a multiple of 8; n_layers >= 0.
- * attn_mode selects the scoring pass's attention: 0 = automatic: the scores and the causal
- * softmax in one tcgen05 kernel when N <= 256 and N is a multiple of 8 (the probabilities
- * written in bfloat16 directly, the scores never leaving the SM), else as mode 2; then
- * O = P V as batched cuBLASLt products; while one layer's probabilities (2 B H N^2 bytes, plus
- * 4 B H N^2 for the FP32 scores of mode 2's path) fit 2 GiB, else the streaming kernel. 1 = always the
+ * attn_mode selects the scoring pass's attention: 0 = automatic: when N <= 256 and N is a
+ * multiple of 8, the whole attention in one tcgen05 kernel (scores, causal softmax and O = P V
+ * on the SM; no score or probability buffer); else as mode 2 while one layer's FP32 scores and
+ * bfloat16 probabilities (6 B H N^2 bytes) fit 2 GiB, else the streaming kernel. 1 = always the
  * streaming kernel (FP32, keys and values streamed through shared memory, softmax online).
- * 2 = the scores as batched cuBLASLt products (FP32), a causal-softmax kernel, then O = P V.
+ * 2 = the scores as batched cuBLASLt products (FP32), a causal-softmax kernel, then O = P V as
+ * batched cuBLASLt products.
  * proj_mode selects the projections' matrix products. This library's tcgen05 kernels
  * (TMA-fed, FP32 accumulators in tensor memory, the bias and GELU or the residual add in the
  * epilogue) take projections whose output width is a multiple of 256 and input width a

@@ -60,10 +60,10 @@ class Former:
     """One IsingFormer on the current CUDA device and stream."""
 
     def __init__(self, shape, packed_params: np.ndarray, stream=None, attn_mode: int = 0, proj_mode: int = 0):
-        """attn_mode 0: scoring attention on the tensor cores where its scores fit (scores and
-        causal softmax fused in one tcgen05 kernel for N <= 256, N a multiple of 8), else the
-        streaming kernel; 1: always the streaming kernel; 2: tensor-core attention with the
-        scores and the softmax as separate cuBLASLt products and kernel. proj_mode 0: the first FFN map by
+        """attn_mode 0: scoring attention on the tensor cores (for N <= 256, N a multiple of 8,
+        scores, causal softmax and P V in one tcgen05 kernel; else as mode 2 where its scores
+        fit, else the streaming kernel); 1: always the streaming kernel; 2: tensor-core
+        attention with the scores, the softmax and P V as separate cuBLASLt products and kernel. proj_mode 0: the first FFN map by
         this library's tcgen05 kernel (bias and GELU fused) from 16384 rows, cuBLASLt for the
         rest; 1: cuBLASLt products and a GELU kernel; 2: the tcgen05 kernels for every
         projection whose shape suits them (bias, GELU, residual fused), at any size."""
