@@ -1069,6 +1069,7 @@ def isingformer_workload(stream, B=1024, reps=5):
                         "roofline": sample_roofline(shp, Bl, ms_sl)},
              "e2e": {"value": B / (ms_e * 1e-3), "unit": "configs/s", "h2d_bytes_per_step": B * N,
                      "d2h_bytes_per_step": B * 4}}
+    out_d["score"]["hbm_view"] = score_hbm_view(shp, B, ms)
     # the same pass with every projection on cuBLASLt (proj_mode 1) and with every suitable
     # projection on the tcgen05 kernels (proj_mode 2)
     for mode in (1, 2):
@@ -1087,6 +1088,24 @@ def isingformer_workload(stream, B=1024, reps=5):
                              "numpy oracle (BLAS threads on the host cores)"}
     del m
     return out_d
+
+
+def score_hbm_view(shp, B, ms):
+    """The scoring pass against the copy bandwidth: the bytes its kernels hand to one another
+    through HBM, M = B N rows. Per layer: the first layer norm reads the FP32 residual stream
+    and writes bfloat16 (6 M d; folded into the embedding at layer 0), QKV reads it and writes
+    3 d columns (8 M d), the fused attention reads QKV and writes O (8 M d), the output map reads
+    O and reads and writes the stream (10 M d), the second layer norm (6 M d), the first FFN
+    map (2 M d + 2 M F), the second (2 M F + 8 M d): 48 M d + 4 M F. Plus the embedding's write
+    of the stream and the head's read of it."""
+    N, d, F, L = shp.n_spins, shp.d_model, shp.d_ff, shp.n_layers
+    M = B * N
+    nbytes = L * (48.0 * M * d + 4.0 * M * F) - (4.0 * M * d if L else 0.0) + 8.0 * M * d
+    peak = _measured_peak("hbm_gbs")
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak if peak else None, "bytes_per_call": nbytes,
+            "note": "activation bytes between the pass's kernels over the whole pass's time"}
 
 
 def sample_roofline(shp, B, ms):
