@@ -1066,7 +1066,7 @@ def isingformer_workload(stream, B=1024, reps=5):
              "sample": {"configs_per_s": B / (ms_s * 1e-3), "ms_per_call": ms_s, "prefix": npre,
                         "gpu_launches_per_call": "one CUDA graph of N steps",
                         f"configs_per_s_B{8 * B}": Bl / (ms_sl * 1e-3), f"ms_per_call_B{8 * B}": ms_sl,
-                        "roofline": sample_roofline(shp, Bl, ms_sl)},
+                        "roofline": sample_roofline(shp, Bl, ms_sl, elem_bytes=2)},
              "e2e": {"value": B / (ms_e * 1e-3), "unit": "configs/s", "h2d_bytes_per_step": B * N,
                      "d2h_bytes_per_step": B * 4}}
     out_d["score"]["hbm_view"] = score_hbm_view(shp, B, ms)
@@ -1108,19 +1108,19 @@ def score_hbm_view(shp, B, ms):
             "note": "activation bytes between the pass's kernels over the whole pass's time"}
 
 
-def sample_roofline(shp, B, ms):
+def sample_roofline(shp, B, ms, elem_bytes=2):
     """HBM roofline of autoregressive sampling: at step t every layer reads the cached key and
-    value rows 0..t of each configuration (2 d FP32 values per row) and appends row t, so a call
-    moves L B 2d 4 (N(N+1)/2 + N) bytes of cache; the weights (a few MB, resident in L2) and
-    the per-step activations (B rows) are left out."""
+    value rows 0..t of each configuration (2 d values per row, bfloat16 in the default mode)
+    and appends row t, so a call moves L B 2d e (N(N+1)/2 + N) bytes of cache; the weights (a
+    few MB, resident in L2) and the per-step activations (B rows) are left out."""
     N, d, L = shp.n_spins, shp.d_model, shp.n_layers
-    nbytes = L * B * 2 * d * 4.0 * (N * (N + 1) / 2 + N)
+    nbytes = L * B * 2 * d * float(elem_bytes) * (N * (N + 1) / 2 + N)
     peak = _measured_peak("hbm_gbs")
     ach = nbytes / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak if peak else None, "traffic": None, "configs_per_call": B,
             "kernel": "the sampling call (one CUDA graph of N steps; the attention-step kernel "
-                      "streams the key/value cache)", "bytes_per_call": nbytes,
+                      "streams the bfloat16 key/value cache)", "bytes_per_call": nbytes,
             "note": "key/value cache bytes over the whole call's time"}
 
 

@@ -99,7 +99,11 @@ pt_status pt_former_score(pt_former *m, int32_t B, const int8_t *spins, const fl
  * product and carry bits of the factorization order). beta float [B], prefix int8
  * [B][n_prefix] or NULL, out int8 [B][N], logq float [B] or NULL; all device. The launches
  * of one (B, n_prefix) are captured in a CUDA graph on first use and replayed afterwards
- * (seed and stream are read from device memory by the kernels). Stream ordered.
+ * (seed and stream are read from device memory by the kernels). Stream ordered. The
+ * key/value cache is bfloat16 with the arithmetic of the fused scoring attention (query, keys
+ * and values in bfloat16, unnormalised probabilities rounded to bfloat16 before P V), except
+ * with attn_mode 1, where it is FP32 like the streaming attention: log q of a sampled
+ * configuration is then the one the scoring pass of the same model gives it.
  * PT_ENOTSUP when n_heads x N x 4 bytes (the per-head scores of one configuration, kept in
  * shared memory) exceed 48 KiB. */
 pt_status pt_former_sample(pt_former *m, int32_t B, const float *beta, const int8_t *prefix,

@@ -8,8 +8,8 @@
 // products; query/key/value bfloat16 [M][3d] for the tensor-core attention of the scoring
 // pass, FP32 for the streaming kernel and the sampler. The matrix products run on the tensor
 // cores through cuBLASLt (bfloat16 inputs, FP32 accumulation, bias and residual in the
-// epilogue); the rest are the kernels below. Sampling keeps an FP32 key/value cache
-// [layer][B][N][2d].
+// epilogue); the rest are the kernels below. Sampling keeps a key/value cache
+// [layer][B][N][2d], bfloat16 (FP32 with the streaming attention, attn_mode 1).
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -376,6 +376,139 @@ __global__ void __launch_bounds__(256) attention_step_kernel(const float* __rest
     }
 }
 
+// 2^x by the PTX ex2.approx instruction (subnormal results flush to zero), and log2(e) / 8:
+// the exponential of the fused scoring kernel, 2^((s - max) log2(e) / 8) = exp((s - max) / 8)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e8 = 1.4426950408889634f / 8.f;
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// The sampling step with a bfloat16 cache (attn_mode 0 and 2), in the arithmetic of the fused
+// scoring kernel, so that the log q of a sampled configuration is the one scoring gives it:
+// query, keys and values rounded to bfloat16; scores s_j = q . k_j in FP32 (unscaled);
+// p_j = 2^((s_j - max) log2(e) / 8); the sum of the p_j in FP32; O = sum bf16(p_j) v_j / sum.
+// Block b, one warp per head; each quarter-warp reads one cached row of its head at a time (64
+// bfloat16 values, 128 contiguous bytes, 16 per lane), kStepRows16 rows per quarter in flight:
+// the same bytes per load instruction as the FP32 kernel, for half the bytes per row.
+constexpr int kStepRows16 = 8;
+__device__ __forceinline__ void bf16x8_to_float(uint4 r, float (&f)[8]) {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        f[2 * i] = __uint_as_float(w[i] << 16);
+        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+}
+__global__ void __launch_bounds__(256) attention_step16_kernel(const float* __restrict__ qkv,
+                                                               __nv_bfloat16* __restrict__ cache,
+                                                               __nv_bfloat16* __restrict__ out,
+                                                               int N, int d, int t) {
+    extern __shared__ float sm[];              // per warp: the t + 1 scores, then bf16(p)
+    const int hd = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.x;
+    const int qtr = lane >> 3, c8 = 8 * (lane & 7);
+    float* ps = sm + hd * N;
+    const float* qr = qkv + (size_t)b * 3 * d + hd * kDH;
+    float q[8];
+    {
+        const float4 q0 = *reinterpret_cast<const float4*>(qr + c8);
+        const float4 q1 = *reinterpret_cast<const float4*>(qr + c8 + 4);
+        q[0] = bf16_round(q0.x); q[1] = bf16_round(q0.y); q[2] = bf16_round(q0.z); q[3] = bf16_round(q0.w);
+        q[4] = bf16_round(q1.x); q[5] = bf16_round(q1.y); q[6] = bf16_round(q1.z); q[7] = bf16_round(q1.w);
+    }
+    // append this step's key (lanes 0-7) and value (lanes 8-15) of head hd as row t
+    __nv_bfloat16* crow = cache + ((size_t)b * N + t) * 2 * d + hd * kDH;
+    if (qtr < 2) {
+        const float4 a0 = *reinterpret_cast<const float4*>(qr + (1 + qtr) * d + c8);
+        const float4 a1 = *reinterpret_cast<const float4*>(qr + (1 + qtr) * d + c8 + 4);
+        const __nv_bfloat162 w0 = __floats2bfloat162_rn(a0.x, a0.y), w1 = __floats2bfloat162_rn(a0.z, a0.w);
+        const __nv_bfloat162 w2 = __floats2bfloat162_rn(a1.x, a1.y), w3 = __floats2bfloat162_rn(a1.z, a1.w);
+        *reinterpret_cast<uint4*>(crow + qtr * d + c8) =
+            make_uint4(*reinterpret_cast<const uint32_t*>(&w0), *reinterpret_cast<const uint32_t*>(&w1),
+                       *reinterpret_cast<const uint32_t*>(&w2), *reinterpret_cast<const uint32_t*>(&w3));
+    }
+    __syncwarp();
+    const __nv_bfloat16* kb = cache + (size_t)b * N * 2 * d + hd * kDH + c8;
+    const size_t rs = 2 * (size_t)d;           // elements between consecutive cached rows
+    const int nk = t + 1;
+    float mx = -INFINITY;
+    for (int j0 = 0; j0 < nk; j0 += 4 * kStepRows16) {
+        uint4 raw[kStepRows16];
+#pragma unroll
+        for (int u = 0; u < kStepRows16; ++u) {
+            const int j = j0 + 4 * u + qtr;
+            raw[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (j < nk) raw[u] = *reinterpret_cast<const uint4*>(kb + j * rs);
+        }
+#pragma unroll
+        for (int u = 0; u < kStepRows16; ++u) {
+            float k[8];
+            bf16x8_to_float(raw[u], k);
+            float sc = q[7] * k[7];
+#pragma unroll
+            for (int c = 6; c >= 0; --c) sc = fmaf(q[c], k[c], sc);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+            const int j = j0 + 4 * u + qtr;
+            if (j < nk) {
+                if ((lane & 7) == 0) ps[j] = sc;
+                mx = fmaxf(mx, sc);
+            }
+        }
+    }
+    mx = warp_max(mx);
+    __syncwarp();
+    const float off = -mx * kLog2e8;
+    float sum = 0.f;
+    for (int j = lane; j < nk; j += 32) {
+        const float p = ex2_approx(fmaf(ps[j], kLog2e8, off));
+        sum += p;
+        ps[j] = bf16_round(p);
+    }
+    sum = warp_sum(sum);
+    __syncwarp();
+    const __nv_bfloat16* vb = kb + d;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j0 = 0; j0 < nk; j0 += 4 * kStepRows16) {
+        uint4 raw[kStepRows16];
+        float p[kStepRows16];
+#pragma unroll
+        for (int u = 0; u < kStepRows16; ++u) {
+            const int j = j0 + 4 * u + qtr;
+            raw[u] = make_uint4(0u, 0u, 0u, 0u);
+            p[u] = 0.f;
+            if (j < nk) {
+                raw[u] = *reinterpret_cast<const uint4*>(vb + j * rs);
+                p[u] = ps[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStepRows16; ++u) {
+            float v[8];
+            bf16x8_to_float(raw[u], v);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = fmaf(p[u], v[c], acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 8);
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+    }
+    if (qtr == 0) {
+        const float inv = 1.f / sum;
+        const __nv_bfloat162 w0 = __floats2bfloat162_rn(acc[0] * inv, acc[1] * inv);
+        const __nv_bfloat162 w1 = __floats2bfloat162_rn(acc[2] * inv, acc[3] * inv);
+        const __nv_bfloat162 w2 = __floats2bfloat162_rn(acc[4] * inv, acc[5] * inv);
+        const __nv_bfloat162 w3 = __floats2bfloat162_rn(acc[6] * inv, acc[7] * inv);
+        *reinterpret_cast<uint4*>(out + (size_t)b * d + hd * kDH + c8) =
+            make_uint4(*reinterpret_cast<const uint32_t*>(&w0), *reinterpret_cast<const uint32_t*>(&w1),
+                       *reinterpret_cast<const uint32_t*>(&w2), *reinterpret_cast<const uint32_t*>(&w3));
+    }
+}
+
 // final layer norm and head of one row (one warp): the two logits and their log-softmax
 template <int D>
 __device__ __forceinline__ void head_row(const float* xr, const float* g, const float* bt,
@@ -524,7 +657,7 @@ struct pt_former {
     float *lnf_g = nullptr, *lnf_b = nullptr, *wout = nullptr, *bout = nullptr;
     std::vector<Layer> layers;
     Act score, step;
-    float* cache = nullptr;        // sampling: [L][B][N][2d]
+    void* cache = nullptr;         // sampling: [L][B][N][2d], bfloat16 (attn_mode 0, 2) or FP32 (1)
     int cache_B = 0;
     SampleArgs* d_sargs = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -877,6 +1010,10 @@ pt_status block(pt_former* m, Act& x, size_t M, const Layer& Ly, bool qkv_bf16, 
     return s;
 }
 
+// the sampler's key/value cache: bfloat16 unless the scoring attention is the FP32 streaming
+// kernel (attn_mode 1), so that sampler and scorer share their arithmetic
+bool cache16(const pt_former* m) { return m->cfg.attn_mode != 1; }
+
 pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* prefix, int npre,
                           int8_t* out, float* logq) {
     const int N = m->cfg.n_spins, d = m->cfg.d_model, H = m->cfg.n_heads;
@@ -885,9 +1022,14 @@ pt_status sample_launches(pt_former* m, int B, const float* beta, const int8_t* 
         embed_step_kernel<<<B, 256, 0, m->exec>>>(out, beta, m->tok, m->wb, m->bb, m->pe, m->step.h, N, d, t);
         FCK(cudaGetLastError());
         for (int l = 0; l < m->cfg.n_layers; ++l) {
-            float* cl = m->cache + (size_t)l * B * N * 2 * d;
+            const size_t off = (size_t)l * B * N * 2 * d;       // elements
             pt_status s = block(m, m->step, (size_t)B, m->layers[l], false, false, [&]() -> pt_status {
-                attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(m->step.qkv, cl, m->step.o, N, d, t);
+                if (cache16(m))
+                    attention_step16_kernel<<<B, 32 * H, smem, m->exec>>>(
+                        m->step.qkv, static_cast<__nv_bfloat16*>(m->cache) + off, m->step.o, N, d, t);
+                else
+                    attention_step_kernel<<<B, 32 * H, smem, m->exec>>>(
+                        m->step.qkv, static_cast<float*>(m->cache) + off, m->step.o, N, d, t);
                 FCK(cudaGetLastError());
                 return PT_OK;
             });
@@ -1075,7 +1217,7 @@ pt_status pt_former_sample(pt_former* m, int32_t B, const float* beta, const int
         if (m->cache) cudaFree(m->cache);
         m->cache = nullptr;
         m->cache_B = 0;
-        FCK(cudaMalloc(&m->cache, (size_t)std::max(m->cfg.n_layers, 1) * B * N * 2 * d * 4));
+        FCK(cudaMalloc(&m->cache, (size_t)std::max(m->cfg.n_layers, 1) * B * N * 2 * d * (cache16(m) ? 2 : 4)));
         m->cache_B = B;
         if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
     }

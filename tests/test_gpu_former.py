@@ -183,6 +183,43 @@ def test_sampling_matches_the_oracle_decisions():
     assert not np.array_equal(out.cpu().numpy(), S)
 
 
+@pytest.mark.parametrize("N,B", [(40, 24), (200, 16)])
+def test_bfloat16_cache_sampling_matches_scoring(N, B):
+    # attn_mode 0: the sampler's bfloat16 key/value cache takes the fused scoring kernel's
+    # arithmetic (bfloat16 query, keys and values, FP32 scores, the same exponential, the
+    # unnormalised probabilities rounded to bfloat16 before P V), so the log q it reports is
+    # the scoring pass's up to summation order; every drawn spin is the oracle's threshold
+    # decision at the GPU's own prefix except within 0.02 of a tie
+    npre, seed, sid = 5, 0x2468_ACE0_1357, 3
+    shp, W, m = _model(N, index=N + 9, attn_mode=0)
+    g = np.random.default_rng(N + 21)
+    beta = g.uniform(0.2, 2.5, B).astype(np.float32)
+    pre = np.where(g.random((B, npre)) < 0.5, 1, -1).astype(np.int8)
+    bt, pt_ = torch.from_numpy(beta).cuda(), torch.from_numpy(pre).cuda()
+    out = torch.empty((B, N), dtype=torch.int8, device="cuda")
+    lq = torch.empty(B, dtype=torch.float32, device="cuda")
+    m.sample(bt, seed, sid, prefix=pt_, out=out, logq=lq)
+    m.check()
+    S = out.cpu().numpy()
+    assert np.array_equal(S[:, :npre], pre)
+    lq_gpu = lq.cpu().numpy().astype(np.float64)
+    lq_s = m.score(torch.from_numpy(S).cuda(), bt).cpu().numpy().astype(np.float64)
+    print("bfloat16-cache sampler vs scoring: max log q difference", np.abs(lq_gpu - lq_s).max())
+    assert np.allclose(lq_gpu, lq_s, atol=1e-3 * np.sqrt(N), rtol=1e-4), (lq_gpu, lq_s)
+    lg_o, lq_o = F.score(W, shp, S, beta.astype(np.float64))
+    assert np.all(np.abs(lq_gpu - lq_o) <= 0.02 * np.sqrt(N) + 0.01 * np.abs(lq_o))
+    p_plus = np.exp(F.log_softmax2(lg_o)[..., 1])
+    near = 0
+    for b in range(B):
+        for t in range(npre, N):
+            u = _philox_u(seed, t, b, sid)
+            if abs(u - p_plus[b, t]) < 0.02:
+                near += 1
+                continue
+            assert S[b, t] == (1 if u < p_plus[b, t] else -1), (b, t, u, p_plus[b, t])
+    assert near < 0.05 * B * (N - npre)
+
+
 def test_sampled_frequencies_follow_q():
     # a small model (d 64, one head, 2 layers) over N = 6 spins: the frequencies of 40000
     # GPU draws follow the exact q(x | beta) of the oracle over all 64 configurations, within
