@@ -87,7 +87,7 @@ def parse():
     p.add_argument("--serve-pool-gap", type=int, default=100)
     p.add_argument("--serve-hbm-frac", type=float, default=0.5,
                    help="device-memory budget of admitted requests, as a fraction of all slots")
-    p.add_argument("--profile-case", choices=("lattice", "lattice-gibbs", "graph", "former"),
+    p.add_argument("--profile-case", choices=("lattice", "lattice-gibbs", "graph", "former", "former-sample"),
                    help="run one small case for a profiler capture and exit (no timing, no JSON)")
     p.add_argument("--cpu-sample-instances", type=int, default=16)
     p.add_argument("--cpu-sample-sweeps", type=int, default=60)
@@ -1223,7 +1223,9 @@ def profile_case(kind):
     pools of 1024 entries (1 GB, larger than L2), one launch at creation then four of 100
     cycles. graph: 1000 clamped 8x8 multipliers, Gibbs, colour classes of at most 32 free
     sites, pools of 16, one launch at creation then three of 1000 cycles. former: three IsingFormer scoring passes over 1024
-    configurations of N = 200."""
+    configurations of N = 200. former-sample: one IsingFormer sampling call of 1024
+    configurations of N = 200 with the product and carry-in bits as the prefix (direct
+    launches: 200 steps; a 1 GB bfloat16 key/value cache)."""
     import torch
     import instances as I
     import paper_2509_23043_gb300 as pt
@@ -1261,6 +1263,19 @@ def profile_case(kind):
         for _ in range(3):
             pt.run_cycles(ctx, 1000)
         out = pt.energies(ctx)[:4]
+    elif kind == "former-sample":
+        from paper_2509_23043_gb300.former import Former
+        mult = I.multiplier(8)
+        shp = I.FormerShape(n_spins=mult.n_spins)
+        _, packed = I.former_weights(shp)
+        m = Former(shp, packed)
+        inst = mult.instance(251 * 241)
+        npre = int((inst.clamp != 0).sum())
+        pre = torch.from_numpy(np.tile(inst.clamp[:npre], (1024, 1)).astype(np.int8)).cuda()
+        beta = torch.full((1024,), 1.0, dtype=torch.float32, device="cuda")
+        S, lq = m.sample(beta, 1, 0, prefix=pre)
+        m.check()
+        out = lq[:4].cpu().numpy()
     else:
         from paper_2509_23043_gb300.former import Former
         shp = I.FormerShape(n_spins=200)
