@@ -1,5 +1,7 @@
-// Hand-written Blackwell (sm_103a) matrix products with fused epilogues, for the projections
-// of the IsingFormer's blocks (Methods, "IsingFormer architecture and training"):
+// Hand-written Blackwell (sm_103a) tcgen05 kernels of the IsingFormer's blocks (Methods,
+// "IsingFormer architecture and training"): the fused causal attention of the scoring pass
+// (attn_tc_kernel, described where it is defined) and the projections' matrix products with
+// fused epilogues:
 //
 //     kEpiGelu:  C[M][N] = GELU(A[M][K] W[K][N] + b[N])   bfloat16 C and b (first FFN map),
 //                GELU(x) = x (1 + erf(x / sqrt 2)) / 2 (erf to 1.5e-7, see gelu_erf2);

@@ -1,5 +1,5 @@
-// Host interface of the hand-written tcgen05 products with fused epilogues (pt_gemm_tc.cu),
-// used by the IsingFormer's projections.
+// Host interface of the hand-written tcgen05 kernels (pt_gemm_tc.cu) of the IsingFormer: the
+// projections' products with fused epilogues, and the scoring pass's fused causal attention.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
