@@ -7,9 +7,11 @@
 // and the first FFN map (GELU applied in place) bfloat16, the inputs of the next matrix
 // products; query/key/value bfloat16 [M][3d] for the tensor-core attention of the scoring
 // pass, FP32 for the streaming kernel and the sampler. The matrix products run on the tensor
-// cores through cuBLASLt (bfloat16 inputs, FP32 accumulation, bias and residual in the
-// epilogue); the rest are the kernels below. Sampling keeps a key/value cache
-// [layer][B][N][2d], bfloat16 (FP32 with the streaming attention, attn_mode 1).
+// cores (bfloat16 inputs, FP32 accumulation, bias, GELU or residual in the epilogue), through
+// this library's tcgen05 kernels (pt_gemm_tc.cu: the first FFN map, and the whole attention of
+// the scoring pass) or cuBLASLt as proj_mode and attn_mode say; the rest are the kernels
+// below. Sampling keeps a key/value cache [layer][B][N][2d], bfloat16 (FP32 with the streaming
+// attention, attn_mode 1).
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
