@@ -103,7 +103,9 @@ pt_status pt_former_score(pt_former *m, int32_t B, const int8_t *spins, const fl
  * key/value cache is bfloat16 with the arithmetic of the fused scoring attention (query, keys
  * and values in bfloat16, unnormalised probabilities rounded to bfloat16 before P V), except
  * with attn_mode 1, where it is FP32 like the streaming attention: log q of a sampled
- * configuration is then the one the scoring pass of the same model gives it.
+ * configuration is then the one the scoring pass of the same model gives it, up to summation
+ * order (for attn_mode 0 where the fused attention runs, N <= 256 and a multiple of 8; for
+ * other N the scoring attention normalises before rounding, a difference of bfloat16 size).
  * PT_ENOTSUP when n_heads x N x 4 bytes (the per-head scores of one configuration, kept in
  * shared memory) exceed 48 KiB. */
 pt_status pt_former_sample(pt_former *m, int32_t B, const float *beta, const int8_t *prefix,
