@@ -237,3 +237,61 @@ def test_sampled_frequencies_follow_q():
     emp = np.bincount(code, minlength=64) / n
     tv = 0.5 * np.abs(emp - q).sum()
     assert tv < 5 * 0.5 * np.sum(np.sqrt(q * (1 - q) / n)) + 0.01, tv
+
+
+@pytest.mark.parametrize("shape", [
+    I.FormerShape(n_spins=1),                                            # one spin: one key
+    I.FormerShape(n_spins=9, d_model=64, n_heads=1, n_layers=0, d_ff=128),  # no blocks at all
+    I.FormerShape(n_spins=16, d_model=64, n_heads=1, n_layers=1, d_ff=64),  # one block of width 64
+])
+def test_degenerate_shapes_score_and_sample(shape):
+    # B = 1: a single spin (the start token alone, attention over one key), a model without
+    # blocks (embedding, final layer norm and head) and one block of width 64 (one head, the
+    # fused attention with H = 1); scoring against the float64 oracle, and the sampler's log q
+    # against the scoring pass
+    N = shape.n_spins
+    shp, W, m = _model(N, index=77, shape=shape)
+    X = np.ones((1, N), np.int8)
+    X[0, ::2] = -1
+    beta = np.array([1.3], np.float32)
+    bt = torch.from_numpy(beta).cuda()
+    lq, lg = m.score(torch.from_numpy(X).cuda(), bt, logits=True)
+    lg_o, lq_o = F.score(W, shp, X, beta.astype(np.float64))
+    assert np.all(np.abs(lg.cpu().numpy() - lg_o) <= 0.05 + 0.02 * np.abs(lg_o))
+    assert abs(float(lq.cpu()[0]) - lq_o[0]) <= 0.02 * np.sqrt(N) + 0.01 * abs(lq_o[0])
+    S, lqs = m.sample(bt, 5, 1)
+    m.check()
+    S = S.cpu().numpy()
+    assert S.shape == (1, N) and set(np.unique(S)) <= {-1, 1}
+    lq_s = m.score(torch.from_numpy(S).cuda(), bt).cpu().numpy()
+    assert abs(float(lqs.cpu()[0]) - lq_s[0]) <= 1e-3 * np.sqrt(N) + 1e-4 * abs(lq_s[0])
+
+
+def test_invalid_calls_are_rejected():
+    # a width that is not 64 per head, an empty batch, a prefix longer than N and a sequence
+    # whose per-head scores exceed the sampler's shared memory are refused with a status; the
+    # model answers normally afterwards
+    from paper_2509_23043_gb300 import PT_EINVAL, PT_ENOTSUP, PTError
+    from paper_2509_23043_gb300.former import Former
+    bad = I.FormerShape(n_spins=8, d_model=96, n_heads=1, n_layers=1, d_ff=64)
+    _, packed = I.former_weights(bad)
+    with pytest.raises(PTError) as e:
+        Former(bad, packed)
+    assert e.value.status == PT_EINVAL
+    shp, W, m = _model(8, index=1, shape=I.FormerShape(n_spins=8, d_model=64, n_heads=1, n_layers=1, d_ff=64))
+    beta = torch.ones(2, dtype=torch.float32, device="cuda")
+    with pytest.raises(PTError) as e:
+        m.score(torch.empty((0, 8), dtype=torch.int8, device="cuda"), beta[:0])
+    assert e.value.status == PT_EINVAL
+    with pytest.raises(PTError) as e:
+        m.sample(beta, 1, 0, prefix=torch.ones((2, 9), dtype=torch.int8, device="cuda"))
+    assert e.value.status == PT_EINVAL
+    big = I.FormerShape(n_spins=4096, d_model=256, n_heads=4, n_layers=1, d_ff=64)
+    _, _, mb = _model(4096, index=2, shape=big)
+    with pytest.raises(PTError) as e:
+        mb.sample(torch.ones(1, dtype=torch.float32, device="cuda"), 1, 0)
+    assert e.value.status == PT_ENOTSUP
+    X = np.where(np.arange(16).reshape(2, 8) % 3 == 0, 1, -1).astype(np.int8)
+    lq = m.score(torch.from_numpy(X).cuda(), beta).cpu().numpy()
+    _, lq_o = F.score(W, shp, X, np.ones(2))
+    assert np.all(np.abs(lq - lq_o) <= 0.02 * np.sqrt(8) + 0.01 * np.abs(lq_o))
