@@ -23,7 +23,7 @@ FORMER_LIB = OUT_DIR / "libptformer.so"
 FORMER_SOURCES = ["pt_former.cu", "pt_gemm_tc.cu"]
 CUDA_LIB_DIR = "/usr/local/cuda/lib64"
 SOURCES = ["pt_api.cu", "pt_lattice.cu", "pt_lattice_gibbs.cu", "pt_lattice_big.cu", "pt_graph.cu", "pt_calib.cu"]
-HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh", "pt_lattice.cuh", "pt_gemm_tc.h"]
+HEADERS = ["pt_device.cuh", "pt_layout.h", "pt_graph.cuh", "pt_lattice.cuh", "pt_gemm_tc.h", "pt_softmax2.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ffp-contract=off on the host: FP64 threshold tables are evaluated exactly as written.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -30,6 +30,7 @@
 #include "../../include/pt_former.h"
 #include "pt_device.cuh"
 #include "pt_gemm_tc.h"
+#include "pt_softmax2.cuh"
 
 namespace {
 
@@ -378,14 +379,9 @@ __global__ void __launch_bounds__(256) attention_step_kernel(const float* __rest
     }
 }
 
-// 2^x by the PTX ex2.approx instruction (subnormal results flush to zero), and log2(e) / 8:
-// the exponential of the fused scoring kernel, 2^((s - max) log2(e) / 8) = exp((s - max) / 8)
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-constexpr float kLog2e8 = 1.4426950408889634f / 8.f;
+// the exponential of the fused scoring kernel (pt_softmax2.cuh)
+using ptsm::ex2_approx;
+using ptsm::kLog2e8;
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // The sampling step with a bfloat16 cache (attn_mode 0 and 2), in the arithmetic of the fused

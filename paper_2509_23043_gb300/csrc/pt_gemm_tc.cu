@@ -35,6 +35,7 @@
 #include <cstdint>
 
 #include "pt_gemm_tc.h"
+#include "pt_softmax2.cuh"
 
 namespace tcg {
 
@@ -414,15 +415,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-
-// 2^x by the PTX ex2.approx instruction (an approximation; subnormal results flush to zero). The
-// attention tests bound its effect on the probabilities against the library path.
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-constexpr float kLog2e8 = 1.4426950408889634f / 8.f;   // log2(e) / sqrt(64)
+using ptsm::ex2_approx;
+using ptsm::kLog2e8;
 
 // Causal attention of the scoring pass for sequences of at most 256 positions, all of it on
 // the SM: O[b N + i][64 h ..] = sum_{j <= i} softmax_j(Q_i . K_j / 8) V_j for every configuration
